@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the spectral-filtering generator (generate + threshold + S(k)).
+
+Prints ONE JSON line (rank 0).  Default workload: the 2D 4096^2 ensemble of 64
+fields (p = 4, semi-axes 2:1 rotated 30 degrees, band 0.15 k_Nyq, width 0.03,
+s = 4, levels 0 and +-0.5 sigma, 64 x 36 radial x angular bins); one step is
+the whole ensemble.  Metric: voxels per second of the whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun each rank runs its own ensemble (field indices offset by rank,
+no data-path collective: weak scaling); timing is max over ranks.  The
+reference arm (--impl reference) times the FP64 CPU oracle on a bounded sample
+of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # 2D 4096^2 FP32 ensemble of 64 seeds, anisotropic, angularly resolved S(k)
+    "ensemble-2d-4096": dict(shape=(4096, 4096), nfields=64, p=4.0, axes=(1.0, 0.5), rot=math.radians(30.0),
+                             k0=0.15, width=0.03, supp=4.0, levels=(0.0, 0.5, -0.5), nr=64, ntheta=36),
+    # 3D 512^3 single field, superellipsoid p = 6, semi-axes 1:1:0.5
+    "3d-512": dict(shape=(512, 512, 512), nfields=1, p=6.0, axes=(1.0, 1.0, 0.5), rot=0.0, k0=0.2, width=0.04,
+                   supp=2.0, levels=(0.0,), nr=256, ntheta=1),
+    "3d-1024": dict(shape=(1024, 1024, 1024), nfields=1, p=6.0, axes=(1.0, 1.0, 0.5), rot=0.0, k0=0.2, width=0.04,
+                    supp=2.0, levels=(0.0,), nr=256, ntheta=1),
+    # 2D 256^2 isotropic single field (the small oracle case)
+    "2d-256": dict(shape=(256, 256), nfields=1, p=2.0, axes=(1.0, 1.0), rot=0.0, k0=0.25, width=0.05, supp=2.0,
+                   levels=(0.0,), nr=128, ntheta=1),
+}
+METRIC = "voxels/s for gen+threshold+S(k)"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def algorithmic_bytes(shape, nlev, field_bytes=4):
+    """Bytes each pass kind must move per launch (one field), by the pass plan:
+    r2c writes the half spectrum (4 B/voxel); a strided pass reads and writes it
+    (8 B/voxel per spectrum); c2r reads it, writes the field, nlev sign maps and
+    nlev map spectra; the bins pass reads the nlev map spectra."""
+    N = math.prod(shape)
+    h = 4 * N  # half spectrum bytes
+    return {
+        "r2c": h,
+        "cols_mid_fwd": 2 * h,
+        "cols_filter": 2 * h,
+        "cols_mid_inv": 2 * h,
+        "c2r": h + field_bytes * N + nlev * N + nlev * h,
+        "cols_mid_maps": 2 * h * nlev,
+        "cols_bins": h * nlev,
+        "counts": 0,
+        "misc": 0,
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, out_path=None):
+        self.proc = None
+        self.path = out_path or os.path.join("/tmp", f"hufield_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, bus_id=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if bus_id and parts[1].lower()[-12:] != bus_id.lower()[-12:]:
+                continue
+            rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(wl, nfields_total):
+    """The FP64 oracle on one field of the workload (a bounded sample)."""
+    import oracle
+
+    of = oracle.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
+    t0 = time.perf_counter()
+    oracle.pipeline(wl["shape"], of, 0, 0, levels=wl["levels"], nr=wl["nr"], ntheta=wl["ntheta"])
+    dt = time.perf_counter() - t0
+    N = math.prod(wl["shape"])
+    return {"value": N / dt, "unit": "voxels/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"1 field of {'x'.join(map(str, wl['shape']))} (of {nfields_total} per step), "
+                      f"full FP64 pipeline, {dt:.2f} s"}
+
+
+def run_reference(args, wl, name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    N = math.prod(wl["shape"])
+    times = []
+    for i in range(args.warmup + args.steps):
+        of = oracle.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"],
+                           supp=wl["supp"])
+        t0 = time.perf_counter()
+        oracle.pipeline(wl["shape"], of, i, 0, levels=wl["levels"], nr=wl["nr"], ntheta=wl["ntheta"])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = N * len(times) / tot
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "shape": list(wl["shape"]), "step_sample": "1 field per step"},
+            "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
+                             "sample": f"1 field of {'x'.join(map(str, wl['shape']))} per step"},
+            "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="ensemble-2d-4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl, args.workload)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2509_08675_gb300 import builder
+
+    if rank == 0 or world == 1:
+        builder.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2509_08675_gb300 import hufield as hf
+
+    shape, nf, levels = wl["shape"], wl["nfields"], wl["levels"]
+    nlev, nr, nt = len(levels), wl["nr"], wl["ntheta"]
+    nb = nr * nt
+    N = math.prod(shape)
+    fdt = torch.float32 if args.dtype == "f32" else torch.bfloat16
+    filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
+    plan = hf.Plan(shape, profile=True)
+    ws = plan.workspace(nlev, nb)
+    out_f = torch.empty((nf,) + tuple(shape), dtype=fdt, device="cuda")
+    maps = torch.empty((nf, nlev) + tuple(shape), dtype=torch.int8, device="cuda")
+    sf = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    cf = torch.zeros(nb, dtype=torch.int64, device="cuda")
+    sm = torch.zeros(nlev * nb, dtype=torch.float64, device="cuda")
+    cm = torch.zeros(nlev * nb, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    field0 = rank * nf
+
+    def step(i):
+        hf.hufield_ensemble(plan, filt, 1000 + i, field0, nf, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, ws,
+                            stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    hf.hufield_profile_read(plan)  # drop warm-up records
+
+    clocks = ClockSampler()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
+        ev[i][0].record(stream)
+        step(args.warmup + i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        pr = torch.cuda.get_device_properties(local)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+    except Exception:
+        bus = None
+    clk = clocks.stop(bus)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    prof = hf.hufield_profile_read(plan)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps * nf * N / (tot_ms / 1e3)
+
+    # roofline of the dominant pass (live per-launch CUDA-event times of the timed steps)
+    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2)
+    peak, peak_kind = peaks()
+    passes = {}
+    for k, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        per = ms / cnt
+        gbs = algo.get(k, 0) / (per / 1e3) / 1e9 if algo.get(k, 0) else None
+        passes[k] = {"launches": cnt, "ms_total": round(ms, 4), "ms_per_launch": round(per, 5),
+                     "GBps": round(gbs, 1) if gbs else None, "frac": round(gbs / peak, 4) if gbs else None}
+    dom = max((k for k in passes if algo.get(k, 0)), key=lambda k: passes[k]["ms_total"])
+    per_step_bytes = nf * sum(algo[k] * passes[k]["launches"] / (args.steps * nf) for k in passes if algo.get(k))
+    pipe_gbs = per_step_bytes / (tot_ms / args.steps / 1e3) / 1e9
+    traffic = None
+    roof = {"bound": "hbm", "achieved": passes[dom]["GBps"], "peak": peak, "unit": "GB/s",
+            "frac": passes[dom]["frac"], "traffic": traffic, "kernel": dom, "peak_source": peak_kind}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws, field0, dist, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl, nf)
+
+    launches = sum(p["launches"] for p in passes.values()) // args.steps
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": args.workload, "shape": list(shape), "fields_per_step": nf,
+                           "levels": list(levels), "bins": [nr, nt], "l2": "flushed between timed steps",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof,
+                "pipeline": {"bytes_per_voxel": round(per_step_bytes / (nf * N), 2), "GBps": round(pipe_gbs, 1),
+                             "frac": round(pipe_gbs / peak, 4)},
+                "passes": passes,
+                "gpu_launches": launches * args.steps,
+                "clocks": clk,
+                "e2e": e2e,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws, field0, dist, world):
+    """The same step through the public per-field call, with every output (fields,
+    sign maps, bins) copied to pinned host memory on a second stream that
+    overlaps the next field's compute."""
+    shape, nf, levels = wl["shape"], wl["nfields"], wl["levels"]
+    nlev, nr, nt = len(levels), wl["nr"], wl["ntheta"]
+    N = math.prod(shape)
+    try:
+        host_f = torch.empty(out_f.shape, dtype=out_f.dtype, pin_memory=True)
+        host_m = torch.empty(maps.shape, dtype=maps.dtype, pin_memory=True)
+    except RuntimeError:
+        return None
+    host_bins = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (sf, cf, sm, cm)]
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    done = [torch.cuda.Event() for _ in range(nf)]
+
+    def step(i):
+        for e in range(nf):
+            hf.hufield_pipeline(plan, filt, 2000 + i, field0 + e, out_f[e], levels, maps[e], nr, nt, e > 0, sf, cf,
+                                sm, cm, ws, stream=comp)
+            done[e].record(comp)
+            with torch.cuda.stream(copy):
+                copy.wait_event(done[e])
+                host_f[e].copy_(out_f[e], non_blocking=True)
+                host_m[e].copy_(maps[e], non_blocking=True)
+        comp.wait_stream(copy)
+        for h, d in zip(host_bins, (sf, cf, sm, cm)):
+            h.copy_(d, non_blocking=True)
+
+    steps, warm = max(1, min(args.steps, 3)), 1
+    for i in range(warm):
+        step(i)
+    torch.cuda.synchronize()
+    hf.hufield_profile_read(plan)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        step(warm + i)
+        comp.synchronize()
+    dt = time.perf_counter() - t0
+    hf.hufield_profile_read(plan)
+    if dist is not None:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    d2h = (out_f.numel() * out_f.element_size() + maps.numel() + sum(t.numel() * t.element_size()
+                                                                      for t in (sf, cf, sm, cm)))
+    return {"value": world * steps * nf * N / dt, "unit": "voxels/s", "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "note": "inputs are seeds and filter parameters passed by value; every output copied to pinned host"}
+
+
+if __name__ == "__main__":
+    main()

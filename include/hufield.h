@@ -1,0 +1,180 @@
+/*
+ * hufield.h -- C ABI of the GB300 (sm_103a) spectral-filtering generator of
+ * hyperuniform random fields (Zhong & Mao, arXiv 2509.08675, Sec. II.B).
+ *
+ * Pipeline (Sec. II.B): seeded white noise -> forward real FFT -> multiply by
+ * A(k) = sqrt(chi(k)) (Eq. 8) with chi from the generalized superellipse norm
+ * (Eq. 12) and the band envelope (Eq. 13) -> inverse FFT (Eq. 9) ->
+ * normalisation to zero mean and variance sigma_f^2 (Eq. 15) -> sign maps at
+ * given levels (Sec. II.B, last paragraph) -> binned spectral density S(k) of
+ * the field and of every map (the log S panels of Figs. 1-5).
+ *
+ * Conventions shared by every call
+ *   - Lattice: ndim = 2 or 3, C order, axis ndim-1 contiguous; every n[i] is a
+ *     power of two with 8 <= n[i] <= 4096, and N = prod n[i] <= 2^31.
+ *   - Signed index n_i in [-n[i]/2, n[i]/2); wavevector in units of the
+ *     Nyquist wavenumber, kappa_i = 2 n_i / n[i] (kappa_i = +-1 is Nyquist).
+ *     A physical k_i is kappa_i * pi n[i] / L.
+ *   - Noise: Philox4x32-10 (Salmon et al., SC'11) with key = (seed lo, seed hi)
+ *     and counter = (j lo, j hi, field_idx, 0) for the block j = voxel >> 2;
+ *     its four words x0..x3 give voxels 4j..4j+3 by Box-Muller,
+ *     u = (x + 1/2) 2^-32, z0 = sqrt(-2 ln u0) cos(2 pi u1),
+ *     z1 = sqrt(-2 ln u0) sin(2 pi u1), z2/z3 likewise from (x2, x3).
+ *   - Filter: K = (sum_i |kappa'_i / axes[i]|^p)^(1/p), kappa' = kappa rotated
+ *     by -rot in the 0-1 plane; chi = C K^supp exp(-(K-k0)^2 / (2 width^2))
+ *     with C putting the analytic maximum at 1; A = 0 at K = 0 and on every
+ *     Nyquist plane.  form = 1 sets k0 = 0, which is the paper's Eq. (13)
+ *     with alpha = supp and sigma = width.
+ *   - Spectrum: S(n) = |DFT(y)(n)|^2 / N over the full lattice.  Radial bin b
+ *     holds modes with b <= nr |kappa| < b + 1 (exact integer test); modes
+ *     with |kappa| >= 1 are dropped.  In 2D, ntheta > 1 splits the folded
+ *     angle atan2(kappa_1, kappa_0) in [0, pi) into ntheta half-open sectors
+ *     whose edges are the directions round(2^30 (cos, sin)(j pi / ntheta)).
+ *     Bin index = b * ntheta + sector.  sums[bin] += sum of S over its modes,
+ *     counts[bin] += number of modes; the bin mean is sums / counts.
+ *
+ * Memory and execution
+ *   - Every buffer argument named out_*, ws, sums, counts, f or y is a DEVICE
+ *     pointer owned by the caller; levels is a HOST pointer.  Device buffers
+ *     must be 256-byte aligned.  The library allocates device memory only in
+ *     hufield_plan_create (a 32 KB twiddle table) and never on a hot call.
+ *   - All hot calls are asynchronous on the given CUDA stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream) and return after
+ *     enqueueing the work.  A stream-ordered caller may reuse ws once the call
+ *     has completed on that stream.
+ *   - Return value: HUFIELD_OK or an error code; arguments are validated before
+ *     anything is enqueued, so an error return leaves every buffer untouched,
+ *     except HUFIELD_ERR_CUDA (a launch failed; the stream state is that of
+ *     the CUDA runtime).  No exception crosses this interface.
+ *   - A plan may be used from one host thread at a time; distinct plans are
+ *     independent.
+ */
+#ifndef HUFIELD_H
+#define HUFIELD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum hufield_status {
+    HUFIELD_OK = 0,
+    HUFIELD_ERR_INVALID_ARG = 1,      /* NULL pointer, NaN/out-of-range parameter, bad dtype */
+    HUFIELD_ERR_UNSUPPORTED_DIMS = 2, /* ndim or n[i] outside the supported set */
+    HUFIELD_ERR_WS_TOO_SMALL = 3,     /* ws_bytes below hufield_workspace_bytes() */
+    HUFIELD_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed */
+    HUFIELD_ERR_TIMEOUT = 5           /* reserved for bounded device-side waits */
+};
+
+enum hufield_dtype { HUFIELD_F32 = 0, HUFIELD_BF16 = 1, HUFIELD_I8 = 2 };
+
+typedef struct hufield_plan hufield_plan;
+
+/* Plan flag: record CUDA events around every kernel launch of the plan's
+ * calls (per-pass device times for profiling; see hufield_profile_read). */
+#define HUFIELD_PLAN_PROFILE 1u
+
+typedef struct {
+    int32_t ndim;   /* 2 or 3 */
+    int32_t reserved;
+    int64_t n[3];   /* lattice extent per axis; n[2] ignored in 2D */
+} hufield_dims;
+
+typedef struct {
+    float p;        /* superellipse exponent, Eq. (12); p > 0 */
+    float axes[3];  /* semi-axes a, b, c of Eq. (12); > 0 (axes[2] ignored in 2D) */
+    float rot;      /* rotation of the semi-axes in the 0-1 plane, radians */
+    float k0;       /* band centre in units of k_Nyquist (ignored when form = 1) */
+    float width;    /* Gaussian width w (sigma of Eq. 13) in units of k_Nyquist; > 0 */
+    float supp;     /* small-k exponent s (alpha of Eq. 13); >= 0 */
+    float sigma_f;  /* target standard deviation of the field, Eq. (15); > 0 */
+    int32_t form;   /* 0 generalised band at k0, 1 paper form (k0 = 0) */
+    int32_t nyquist;/* must be 0: the filter is zero on Nyquist planes */
+} hufield_filter;
+
+/* Plan for one lattice.  Allocates the twiddle table on the current CUDA
+ * device and chooses launch shapes; the plan must be used on that device.
+ * flags is 0 or HUFIELD_PLAN_PROFILE.  Returns HUFIELD_ERR_UNSUPPORTED_DIMS
+ * for a lattice outside the set above. */
+int hufield_plan_create(hufield_plan **plan, const hufield_dims *dims, uint32_t flags);
+int hufield_plan_destroy(hufield_plan *plan);
+
+/* Bytes of device workspace a call needs: nlev sign maps (0 for
+ * hufield_generate, 1 for hufield_spectrum) and nbins = nr * ntheta bins
+ * (0 when no spectrum is taken).  Returns 0 for invalid arguments. */
+size_t hufield_workspace_bytes(const hufield_plan *plan, int32_t nlev, int32_t nbins);
+
+/* Noise of field (seed, field_idx), Sec. II.B: bits (N uint32 words, word i =
+ * Philox word i & 3 of block i >> 2) and/or z (N floats, Box-Muller).  Either
+ * output may be NULL. */
+int hufield_noise(hufield_plan *plan, uint64_t seed, uint32_t field_idx, uint32_t *bits, float *z,
+                  void *stream);
+
+/* Forward r2c DFT of the noise (diagnostic): X(n) = sum_x z(x) e^{-2 pi i n.x/N}
+ * into ws as complex64 [n0][n1]...[n_last/2], i.e. the half spectrum without
+ * its Nyquist plane along the last axis (k_last = 0 .. n_last/2 - 1). */
+int hufield_forward(hufield_plan *plan, uint64_t seed, uint32_t field_idx, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/* Steps noise -> r2c -> filter -> c2r -> normalise (Sec. II.B, Eqs. 8-15):
+ * writes the field f (N values of out_dtype, HUFIELD_F32 or HUFIELD_BF16). */
+int hufield_generate(hufield_plan *plan, const hufield_filter *filt, uint64_t seed, uint32_t field_idx,
+                     int32_t out_dtype, void *out_f, void *ws, size_t ws_bytes, void *stream);
+
+/* Sign maps of a field (Sec. II.B, last paragraph): out_maps[t * N + i] =
+ * f[i] >= levels[t] ? +1 : -1 for t < nlev (1 <= nlev <= 8).  dtype of f is
+ * HUFIELD_F32 or HUFIELD_BF16. */
+int hufield_threshold(hufield_plan *plan, const void *f, int32_t dtype, const float *levels, int32_t nlev,
+                      int8_t *out_maps, void *stream);
+
+/* Binned spectral density of a real field y (dtype F32, BF16 or I8):
+ * S(n) = |DFT(y)(n)|^2 / N.  nr in [1, 4096], ntheta in [1, 64] (2D only for
+ * ntheta > 1), nr * ntheta <= 4096.  accumulate = 0 overwrites sums/counts,
+ * 1 adds to them (ensembles). */
+int hufield_spectrum(hufield_plan *plan, const void *y, int32_t dtype, int32_t nr, int32_t ntheta,
+                     int32_t accumulate, double *sums, int64_t *counts, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/* Whole path, fused: generate (as hufield_generate), then for each of nlev
+ * (0..8) levels the sign map (as hufield_threshold), and the binned S of the
+ * field (sums_f/counts_f) and of each map (sums_m/counts_m, nlev blocks of
+ * nr * ntheta).  out_f and out_maps may be NULL (not stored).  The field's S
+ * is taken from the filtered spectrum (S_f(n) = N |G(n)|^2 / sum |G|^2), which
+ * equals the spectrum of the stored FP32 field up to rounding. */
+int hufield_pipeline(hufield_plan *plan, const hufield_filter *filt, uint64_t seed, uint32_t field_idx,
+                     int32_t out_dtype, void *out_f, const float *levels, int32_t nlev, int8_t *out_maps,
+                     int32_t nr, int32_t ntheta, int32_t accumulate, double *sums_f, int64_t *counts_f,
+                     double *sums_m, int64_t *counts_m, void *ws, size_t ws_bytes, void *stream);
+
+/* Ensemble: hufield_pipeline for field_idx = field0 .. field0 + nfields - 1
+ * with the same seed and filter, bins accumulated over the ensemble.  Field e
+ * is written at out_f + e * N elements and its maps at out_maps + e * nlev * N
+ * (either may be NULL).  accumulate applies to the first field. */
+int hufield_ensemble(hufield_plan *plan, const hufield_filter *filt, uint64_t seed, uint32_t field0,
+                     int32_t nfields, int32_t out_dtype, void *out_f, const float *levels, int32_t nlev,
+                     int8_t *out_maps, int32_t nr, int32_t ntheta, int32_t accumulate, double *sums_f,
+                     int64_t *counts_f, double *sums_m, int64_t *counts_m, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
+int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,
+                      void *stream);
+
+/* Profiling (plans created with HUFIELD_PLAN_PROFILE): waits for the events
+ * recorded since the previous read and adds, per pass kind, the device time
+ * in ms and the number of launches into ms[i] and launches[i] for
+ * i < min(n, number of kinds).  Kind names, comma separated, in that order:
+ * hufield_profile_names(). */
+int hufield_profile_read(hufield_plan *plan, double *ms, int64_t *launches, int32_t n);
+const char *hufield_profile_names(void);
+
+/* Name of a status code. */
+const char *hufield_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUFIELD_H */

@@ -1,0 +1,242 @@
+// fft.cuh -- in-CTA FFT engine for power-of-two lengths L <= 4096.
+//
+// Each CTA transforms TB independent lines of length L.  A thread holds E
+// complex values in registers; a stage of radix R makes every thread run E/R
+// radix-R butterflies in registers, and between stages the values are
+// exchanged through shared memory (Stockham autosort: natural order in and
+// out, no bit reversal).  Stage s with radix R, after sub-transforms of size
+// Ns have been formed, takes butterfly j's inputs at j + r L/R, multiplies
+// input r by W_{Ns R}^{(j mod Ns) r}, and writes output r at
+// (j / Ns) Ns R + (j mod Ns) + r Ns.
+//
+// Two thread layouts:
+//   COL  line b = g mod TB, butterfly j = g / TB  (lines are adjacent columns
+//        of a strided axis; lanes run over b so global loads are coalesced)
+//   ROW  butterfly j = g mod (L/R), line b = g / (L/R) (lines are contiguous
+//        rows; lanes run over j)
+// with g = t + T i for the thread's i-th butterfly.
+#pragma once
+
+#include "common.cuh"
+
+namespace hf {
+
+// ---------------------------------------------------------------------------
+// Radix-R DFT in registers, natural order, sign DIR (-1 forward, +1 inverse).
+// ---------------------------------------------------------------------------
+// v * exp(DIR 2 pi i k / R) for compile-time R and k in [0, R/2)
+template <int R, int DIR, int K>
+__device__ __forceinline__ float2 rot_const(float2 v) {
+    constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
+    constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
+    constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
+    if constexpr (K == 0) {
+        return v;
+    } else if constexpr (4 * K == R) {
+        return cmul_i<DIR>(v);
+    } else if constexpr (R == 8) {
+        // K = 1: (1 + DIR i)/sqrt2 ; K = 3: (-1 + DIR i)/sqrt2
+        if constexpr (K == 1) {
+            return DIR < 0 ? make_float2((v.x + v.y) * kC8, (v.y - v.x) * kC8)
+                           : make_float2((v.x - v.y) * kC8, (v.y + v.x) * kC8);
+        } else {
+            return DIR < 0 ? make_float2((v.y - v.x) * kC8, -(v.x + v.y) * kC8)
+                           : make_float2(-(v.x + v.y) * kC8, (v.x - v.y) * kC8);
+        }
+    } else {
+        static_assert(R == 16, "radix");
+        constexpr float c = K == 1 ? kC16 : K == 2 ? kC8 : K == 3 ? kS16 : K == 5 ? -kS16 : K == 6 ? -kC8 : -kC16;
+        constexpr float s = K == 1 ? kS16 : K == 2 ? kC8 : K == 3 ? kC16 : K == 5 ? kC16 : K == 6 ? kC8 : kS16;
+        return cmul(v, make_float2(c, DIR * s));
+    }
+}
+
+template <int R, int DIR>
+struct Dft {
+    template <int K>
+    __device__ __forceinline__ static void combine(float2* v, const float2* e, const float2* o) {
+        if constexpr (K < R / 2) {
+            const float2 t = rot_const<R, DIR, K>(o[K]);
+            v[K] = cadd(e[K], t);
+            v[K + R / 2] = csub(e[K], t);
+            combine<K + 1>(v, e, o);
+        }
+    }
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        Dft<R / 2, DIR>::run(e);
+        Dft<R / 2, DIR>::run(o);
+        combine<0>(v, e, o);
+    }
+};
+
+template <int DIR>
+struct Dft<2, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <int DIR>
+struct Dft<4, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        const float2 a2 = cadd(v[1], v[3]), a3 = cmul_i<DIR>(csub(v[1], v[3]));
+        v[0] = cadd(a0, a2);
+        v[1] = cadd(a1, a3);
+        v[2] = csub(a0, a2);
+        v[3] = csub(a1, a3);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Stage plan of a length 2^LOG2L: ceil(LOG2L / 4) stages of radix <= 16,
+// bits spread evenly with the larger radices last; REV reverses the order
+// (the inverse transform runs the forward plan backwards so that its input
+// positions are the forward transform's output positions).
+// ---------------------------------------------------------------------------
+template <int LOG2L, bool REV>
+struct Plan {
+    static constexpr int L = 1 << LOG2L;
+    static constexpr int NS = (LOG2L + 3) / 4;
+    static constexpr int bits_fwd(int s) {
+        return LOG2L / NS + (s >= NS - LOG2L % NS ? 1 : 0);
+    }
+    static constexpr int bits(int s) { return REV ? bits_fwd(NS - 1 - s) : bits_fwd(s); }
+    static constexpr int radix(int s) { return 1 << bits(s); }
+    static constexpr int log2_before(int s) { return s == 0 ? 0 : log2_before(s - 1) + bits(s - 1); }
+    static constexpr int max_radix() {
+        int m = 1;
+        for (int s = 0; s < NS; ++s) m = radix(s) > m ? radix(s) : m;
+        return m;
+    }
+    static constexpr int first_radix() { return radix(0); }
+    static constexpr int last_radix() { return radix(NS - 1); }
+};
+
+// Thread context for the butterfly mapping.
+struct Ctx {
+    int t;      // thread index
+    int T;      // threads in the CTA
+    int logTB;  // log2 of lines per CTA (TB)
+};
+
+// Butterfly (line b, index j) of a thread's i-th radix-2^LR butterfly.
+template <int LOG2L, bool ROW, int LR>
+__device__ __forceinline__ void butterfly_of(const Ctx& c, int i, int& b, int& j) {
+    const int g = c.t + c.T * i;
+    if constexpr (ROW) {
+        j = g & ((1 << (LOG2L - LR)) - 1);
+        b = g >> (LOG2L - LR);
+    } else {
+        b = g & ((1 << c.logTB) - 1);
+        j = g >> c.logTB;
+    }
+}
+
+// Shared-memory slot of element l of line b.  ROW lines are contiguous
+// with the low four bits of l XOR-ed by the next four (bank spread for the
+// stride patterns of the exchanges); COL tiles are [l][b].
+template <int LOG2L, bool ROW>
+__device__ __forceinline__ int smem_slot(const Ctx& c, int l, int b) {
+    if constexpr (ROW) {
+        return (b << LOG2L) + (l ^ ((l >> 4) & 15));
+    } else {
+        return (l << c.logTB) + b;
+    }
+}
+
+// Element positions of the data a thread holds before stage 0 (IN) or after
+// the last stage (OUT) of a plan: the i-th butterfly of radix R holds
+// elements j + r L/R, r = 0..R-1, in v[i R + r].
+template <int LOG2L, bool ROW, int R, int E, class F>
+__device__ __forceinline__ void for_each_element(const Ctx& c, F&& f) {
+    constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 0);
+    static_assert((1 << LR) == R, "radix");
+#pragma unroll
+    for (int i = 0; i < E / R; ++i) {
+        int b, j;
+        butterfly_of<LOG2L, ROW, LR>(c, i, b, j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) f(i * R + r, b, j + r * ((1 << LOG2L) / R));
+    }
+}
+
+template <int LOG2L, int E, int DIR, bool REV, bool ROW, int S>
+struct Stages {
+    using P = Plan<LOG2L, REV>;
+    static constexpr int R = P::radix(S);
+    static constexpr int LR = P::bits(S);
+    static constexpr int LNS = P::log2_before(S);  // log2 Ns
+    static_assert(E % R == 0, "E must be a multiple of every radix");
+
+    __device__ __forceinline__ static void run(float2 (&v)[E], float2* sm, const float2* __restrict__ tw,
+                                               const Ctx& c) {
+        constexpr int L = 1 << LOG2L;
+        constexpr int NB = E / R;
+        if constexpr (LNS > 0) {
+            // twiddles W_{Ns R}^{k r}, k = j mod Ns
+            constexpr int shift = kTwLog2 - (LNS + LR);
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                int b, j;
+                butterfly_of<LOG2L, ROW, LR>(c, i, b, j);
+                const int k = j & ((1 << LNS) - 1);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float2 w = __ldg(tw + ((k * r) << shift));
+                    v[i * R + r] = DIR < 0 ? cmul(v[i * R + r], w) : cmulc(v[i * R + r], w);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) Dft<R, DIR>::run(&v[i * R]);
+        if constexpr (S + 1 < P::NS) {
+            __syncthreads();  // every thread is done reading the previous exchange
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                int b, j;
+                butterfly_of<LOG2L, ROW, LR>(c, i, b, j);
+                const int k = j & ((1 << LNS) - 1);
+                const int base = ((j >> LNS) << (LNS + LR)) + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[smem_slot<LOG2L, ROW>(c, base + (r << LNS), b)] = v[i * R + r];
+            }
+            __syncthreads();
+            constexpr int R2 = P::radix(S + 1);
+            for_each_element<LOG2L, ROW, R2, E>(c, [&](int e, int b, int l) {
+                v[e] = sm[smem_slot<LOG2L, ROW>(c, l, b)];
+            });
+            (void)L;
+            Stages<LOG2L, E, DIR, REV, ROW, S + 1>::run(v, sm, tw, c);
+        }
+    }
+};
+
+// Full transform.  On entry v holds the plan's IN positions, on exit its OUT
+// positions.  Uses sm (TB * L slots) for the exchanges; contains
+// __syncthreads(), so every thread of the CTA must call it.
+template <int LOG2L, int E, int DIR, bool REV, bool ROW>
+__device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const float2* __restrict__ tw, const Ctx& c) {
+    Stages<LOG2L, E, DIR, REV, ROW, 0>::run(v, sm, tw, c);
+}
+
+// Elements per thread for a line length: 16 (32 for the long strided lines),
+// never more than the line itself.
+template <int LOG2L>
+struct ColShape {
+    static constexpr int E = LOG2L >= 11 ? 32 : (LOG2L >= 4 ? 16 : (1 << LOG2L));
+};
+template <int LOG2L>
+struct RowShape {
+    static constexpr int E = LOG2L >= 4 ? 16 : (1 << LOG2L);
+};
+
+}  // namespace hf

@@ -1,0 +1,751 @@
+// hufield.cu -- C ABI (include/hufield.h): plans, argument checks, workspace
+// layout and the launch sequence of the passes, plus the small kernels
+// (twiddle table, noise, sign maps, bin counts, bin finalisation).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/hufield.h"
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace hf {
+const void* cols_plain_kernel(int log2l, int mode, int dir);
+const void* cols_acc_kernel(int log2l, int mode, int dir);
+
+const void* cols_kernel(int log2l, int mode, int dir) {
+    return mode == kModePlain ? cols_plain_kernel(log2l, mode, dir) : cols_acc_kernel(log2l, mode, dir);
+}
+int col_elems(int log2l) { return log2l >= 11 ? 32 : (log2l >= 4 ? 16 : (1 << log2l)); }
+
+// ---------------------------------------------------------------------------
+// Small kernels.
+// ---------------------------------------------------------------------------
+// tw[q] = exp(-2 pi i q / 4096), FP64 then rounded once.
+__global__ void k_twiddles(float2* tw) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < kTwN) {
+        double s, c;
+        sincospi(-(double)q / (double)(kTwN / 2), &s, &c);
+        tw[q] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void k_noise(long long nblk, unsigned long long seed, unsigned int field_idx, uint4* bits, float4* z) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nblk;
+         j += (long long)gridDim.x * blockDim.x) {
+        const uint4 x = noise_block(seed, field_idx, (unsigned long long)j);
+        if (bits) bits[j] = x;
+        if (z) z[j] = box_muller(x);
+    }
+}
+
+struct Levels {
+    float t[kMaxLevels];
+};
+
+template <int DT>
+__global__ void k_threshold(long long nblk, const void* f, Levels lv, int nlev, long long N, char4* maps) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nblk;
+         j += (long long)gridDim.x * blockDim.x) {
+        float4 x;
+        if constexpr (DT == 0) {
+            x = __ldg(reinterpret_cast<const float4*>(f) + j);
+        } else {
+            const uint2 raw = __ldg(reinterpret_cast<const uint2*>(f) + j);
+            const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+            const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+            x = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+        for (int l = 0; l < nlev; ++l) {
+            const float t = lv.t[l];
+            char4 m;
+            m.x = x.x >= t ? 1 : -1;
+            m.y = x.y >= t ? 1 : -1;
+            m.z = x.z >= t ? 1 : -1;
+            m.w = x.w >= t ? 1 : -1;
+            maps[(long long)l * (N / 4) + j] = m;
+        }
+    }
+}
+
+// Number of full-lattice modes per bin, from the half spectrum (weights 1 at
+// k_last = 0, 2 elsewhere), added times `mult` to each of ndst arrays.
+struct CountArgs {
+    int ndim;
+    int log2n[3];
+    long long nmodes;  // N / 2
+    long long mult;
+    int ndst;
+    unsigned long long* dst[kMaxLevels + 1];
+    BinParams bp;
+};
+
+__global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ CountArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem_raw);
+    long long* ang = reinterpret_cast<long long*>(cnt + a.bp.nbins);
+    for (int i = threadIdx.x; i < a.bp.nbins; i += blockDim.x) cnt[i] = 0;
+    for (int i = threadIdx.x; i < a.bp.ntheta; i += blockDim.x) {
+        ang[i] = a.bp.ang_c[i];
+        ang[a.bp.ntheta + i] = a.bp.ang_s[i];
+    }
+    __syncthreads();
+    const int logM = a.log2n[a.ndim - 1] - 1;
+    const int M = 1 << logM;
+    // each thread walks runs of RL consecutive k_last of one row
+    const int RL = M < 8 ? M : 8;
+    const int logRL = M < 8 ? logM : 3;
+    const long long nruns = a.nmodes >> logRL;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nruns;
+         r += (long long)gridDim.x * blockDim.x) {
+        const long long m0 = r << logRL;
+        const int k0 = (int)(m0 & (M - 1));
+        const long long row = m0 >> logM;
+        int n0, n1;
+        if (a.ndim == 3) {
+            n1 = signed_index((int)(row & ((1 << a.log2n[1]) - 1)), a.log2n[1]);
+            n0 = signed_index((int)(row >> a.log2n[1]), a.log2n[0]);
+        } else {
+            n0 = signed_index((int)row, a.log2n[0]);
+            n1 = 0;
+        }
+        int run_bin = -1;
+        unsigned long long run = 0;
+        for (int k = k0; k < k0 + RL; ++k) {
+            int bin;
+            if (a.ndim == 3) {
+                bin = bin_index(a.bp, ang, n0, n1, k, 3);
+            } else {
+                bin = bin_index(a.bp, ang, n0, k, 0, 2);
+            }
+            const unsigned long long w = k == 0 ? 1 : 2;
+            if (bin != run_bin) {
+                if (run_bin >= 0) atomicAdd(cnt + run_bin, run);
+                run_bin = bin;
+                run = 0;
+            }
+            run += w;
+        }
+        if (run_bin >= 0) atomicAdd(cnt + run_bin, run);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.bp.nbins; i += blockDim.x) {
+        if (cnt[i] == 0) continue;
+        for (int d = 0; d < a.ndst; ++d) atomicAdd(a.dst[d] + i, cnt[i] * (unsigned long long)a.mult);
+    }
+}
+
+// sums_f[b] += raw[b] * N / P  (S_f(n) = N |G(n)|^2 / sum |G|^2)
+__global__ void k_finalize_field(const double* raw, const double* P, int nbins, double N, double* sums) {
+    const double s = N / *P;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sums[b] += raw[b] * s;
+}
+
+__global__ void k_bins_mean(const double* sums, const long long* counts, int nbins, double* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbins) out[b] = counts[b] ? sums[b] / (double)counts[b] : 0.0;
+}
+
+}  // namespace hf
+
+using namespace hf;
+
+// ---------------------------------------------------------------------------
+// Plan.
+// ---------------------------------------------------------------------------
+// Pass kinds for the profiling records.
+enum PassKind { kPassR2C = 0, kPassMidFwd, kPassFilter, kPassMidInv, kPassC2R, kPassMidMaps, kPassBins,
+                kPassCounts, kPassMisc, kPassCount };
+static const char* kPassNames = "r2c,cols_mid_fwd,cols_filter,cols_mid_inv,c2r,cols_mid_maps,cols_bins,counts,misc";
+
+struct ProfRecord {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+struct hufield_plan {
+    bool profile = false;
+    std::vector<ProfRecord> records;
+    std::vector<cudaEvent_t> pool;
+    int ndim;
+    long long n[3];
+    int log2n[3];
+    long long N;      // voxels
+    long long half;   // N / 2 half-spectrum modes
+    int logM;         // log2 (n_last / 2)
+    int device;
+    int nsm;
+    float2* tw;
+};
+
+namespace {
+
+struct Launch {
+    int grid = 0, block = 0;
+    size_t smem = 0;
+};
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+    int r = 0;
+    while ((1ll << r) < v) ++r;
+    return r;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int occupancy_grid(const void* fn, int block, size_t smem, long long work, int nsm) {
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess) return 0;
+    if (per_sm <= 0) return 0;
+    long long g = (long long)per_sm * nsm;
+    if (g > work) g = work;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Rows of length M = 2^log2m: TR rows per CTA with 256 threads at most.
+bool row_launch(const hufield_plan* p, const void* fn, long long nrows, int& logTR, Launch& L) {
+    const int log2m = p->logM;
+    const int E = row_elems(log2m);
+    long long TR = (256ll * E) >> log2m;
+    if (TR < 1) TR = 1;
+    if (TR > nrows) TR = nrows;
+    logTR = ilog2(TR);
+    L.block = (int)((TR << log2m) / E);
+    L.smem = (size_t)(TR << log2m) * sizeof(float2);
+    L.grid = occupancy_grid(fn, L.block, L.smem, nrows >> logTR, p->nsm);
+    return fn != nullptr && L.grid > 0;
+}
+
+// Columns of a strided axis of length 2^log2l: TB columns per CTA.
+bool col_launch(const hufield_plan* p, const void* fn, int log2l, long long B, long long A, size_t extra_smem,
+                int& logTB, Launch& L) {
+    const int E = col_elems(log2l);
+    const long long tmax = log2l >= 11 ? 512 : 256;
+    long long TB = (tmax * E) >> log2l;
+    if (TB < 1) TB = 1;
+    if (TB > B) TB = B;
+    logTB = ilog2(TB);
+    L.block = (int)((TB << log2l) / E);
+    L.smem = (size_t)(TB << log2l) * sizeof(float2) + extra_smem;
+    L.grid = occupancy_grid(fn, L.block, L.smem, A * (B >> logTB), p->nsm);
+    return fn != nullptr && L.grid > 0;
+}
+
+cudaEvent_t pool_event(hufield_plan* p) {
+    cudaEvent_t e = nullptr;
+    if (!p->pool.empty()) {
+        e = p->pool.back();
+        p->pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+// Runs `body` (which enqueues one kernel on s); with profiling on, brackets it
+// with two events on the same stream.
+template <class F>
+cudaError_t profiled(hufield_plan* p, int kind, cudaStream_t s, F&& body) {
+    if (!p->profile) return body();
+    ProfRecord r{kind, pool_event(p), pool_event(p)};
+    if (r.start) cudaEventRecord(r.start, s);
+    const cudaError_t e = body();
+    if (r.stop) cudaEventRecord(r.stop, s);
+    if (r.start && r.stop) p->records.push_back(r);
+    return e;
+}
+
+cudaError_t launch(hufield_plan* p, int kind, const void* fn, const Launch& L, void* arg, cudaStream_t s) {
+    void* args[] = {arg};
+    return profiled(p, kind, s, [&] { return cudaLaunchKernel(fn, dim3(L.grid), dim3(L.block), args, L.smem, s); });
+}
+
+bool finite(float v) { return isfinite(v) != 0; }
+
+int check_filter(const hufield_plan* p, const hufield_filter* f) {
+    if (!f) return HUFIELD_ERR_INVALID_ARG;
+    const float vals[] = {f->p, f->axes[0], f->axes[1], f->axes[2], f->rot, f->k0, f->width, f->supp, f->sigma_f};
+    for (float v : vals)
+        if (!finite(v)) return HUFIELD_ERR_INVALID_ARG;
+    if (!(f->p > 0.0f) || !(f->width > 0.0f) || !(f->supp >= 0.0f) || !(f->sigma_f > 0.0f))
+        return HUFIELD_ERR_INVALID_ARG;
+    for (int d = 0; d < p->ndim; ++d)
+        if (!(f->axes[d] > 0.0f)) return HUFIELD_ERR_INVALID_ARG;
+    if (f->form != 0 && f->form != 1) return HUFIELD_ERR_INVALID_ARG;
+    if (f->nyquist != 0) return HUFIELD_ERR_INVALID_ARG;
+    return HUFIELD_OK;
+}
+
+FilterParams make_filter(const hufield_plan* p, const hufield_filter* f) {
+    FilterParams fp{};
+    for (int d = 0; d < 3; ++d) fp.inv_a[d] = (float)(1.0 / (double)(d < p->ndim ? f->axes[d] : 1.0f));
+    fp.p = f->p;
+    fp.inv_p = (float)(1.0 / (double)f->p);
+    fp.rotated = f->rot != 0.0f;
+    fp.cr = (float)cos((double)f->rot);
+    fp.sr = (float)sin((double)f->rot);
+    const double k0 = f->form == 1 ? 0.0 : (double)f->k0;
+    const double w = f->width, s = f->supp;
+    const double ks = 0.5 * (k0 + sqrt(k0 * k0 + 4.0 * s * w * w));  // maximiser: s w^2 = K (K - k0)
+    fp.k0 = (float)k0;
+    fp.kstar = (float)ks;
+    fp.log2_kstar = (float)log2(ks);
+    fp.two_k0 = (float)(2.0 * k0);
+    fp.inv_2w2 = (float)(1.0 / (2.0 * w * w));
+    fp.half_s_ln2 = (float)(0.5 * s * log(2.0));
+    fp.half = 0.5f;
+    return fp;
+}
+
+int make_bins(const hufield_plan* p, int nr, int ntheta, BinParams& bp) {
+    if (nr < 1 || nr > kMaxBins || ntheta < 1 || ntheta > kMaxTheta) return HUFIELD_ERR_INVALID_ARG;
+    if ((long long)nr * ntheta > kMaxBins) return HUFIELD_ERR_INVALID_ARG;
+    if (ntheta > 1 && p->ndim != 2) return HUFIELD_ERR_INVALID_ARG;
+    memset(&bp, 0, sizeof(bp));
+    bp.nr = nr;
+    bp.ntheta = ntheta;
+    bp.nbins = nr * ntheta;
+    int lmax = 0;
+    for (int d = 0; d < p->ndim; ++d) lmax = p->log2n[d] > lmax ? p->log2n[d] : lmax;
+    bp.log2nmax = lmax;
+    for (int d = 0; d < 3; ++d) bp.shift[d] = d < p->ndim ? lmax - p->log2n[d] : 0;
+    // sector edges at angles j pi / ntheta, directions rounded to 2^30
+    for (int j = 0; j < ntheta; ++j) {
+        const double th = 3.14159265358979323846 * (double)j / (double)ntheta;
+        bp.ang_c[j] = llround(ldexp(cos(th), 30));
+        bp.ang_s[j] = llround(ldexp(sin(th), 30));
+    }
+    return HUFIELD_OK;
+}
+
+// Workspace: [spectrum: max(nlev,1) * N/2 complex64][P: double][raw field bins: nbins doubles]
+struct Workspace {
+    float2* spec;
+    double* P;
+    double* raw;
+};
+
+size_t ws_bytes(const hufield_plan* p, int nlev, int nbins) {
+    const size_t spec = align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
+    return spec + align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0)));
+}
+
+int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Workspace& w) {
+    if (!ws) return HUFIELD_ERR_INVALID_ARG;
+    if (((uintptr_t)ws & 255) != 0) return HUFIELD_ERR_INVALID_ARG;
+    if (bytes < ws_bytes(p, nlev, nbins)) return HUFIELD_ERR_WS_TOO_SMALL;
+    const size_t spec = align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
+    w.spec = reinterpret_cast<float2*>(ws);
+    w.P = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + spec);
+    w.raw = w.P + 1;
+    return HUFIELD_OK;
+}
+
+bool aligned(const void* ptr) { return ((uintptr_t)ptr & 255) == 0; }
+
+#define HF_CUDA(expr)                              \
+    do {                                           \
+        if ((expr) != cudaSuccess) return HUFIELD_ERR_CUDA; \
+    } while (0)
+
+// r2c rows of the noise (src == kSrcNoise) or of a stored field into w.spec,
+// then the forward FFT along axis 1 for 3D.
+int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed, uint32_t field_idx,
+                         float2* spec, cudaStream_t s) {
+    const long long nrows = p->N >> (p->logM + 1);
+    RowArgs ra{};
+    ra.src = y;
+    ra.out = spec;
+    ra.nrows = nrows;
+    ra.seed = seed;
+    ra.field_idx = field_idx;
+    ra.tw = p->tw;
+    Launch L;
+    const void* fn = r2c_kernel(p->logM, src);
+    if (!row_launch(p, fn, nrows, ra.logTR, L)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassR2C, fn, L, &ra, s));
+    if (p->ndim == 3) {
+        ColArgs ca{};
+        ca.data = spec;
+        ca.B = 1ll << p->logM;
+        ca.A = p->n[0];
+        ca.bstride = p->n[1] << p->logM;
+        ca.tw = p->tw;
+        const void* cf = cols_kernel(p->log2n[1], kModePlain, -1);
+        if (!col_launch(p, cf, p->log2n[1], ca.B, ca.A, 0, ca.logTB, L)) return HUFIELD_ERR_CUDA;
+        ca.ntiles = ca.A * (ca.B >> ca.logTB);
+        HF_CUDA(launch(p, kPassMidFwd, cf, L, &ca, s));
+    }
+    return HUFIELD_OK;
+}
+
+// Strided pass along axis 0 over `nbatch` spectra of N/2 modes each.
+int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const FilterParams* fp,
+               const BinParams& bp, double* gbins, double* gP, cudaStream_t s) {
+    ColArgs ca{};
+    ca.data = data;
+    ca.B = p->half >> p->log2n[0];
+    ca.A = nbatch;
+    ca.bstride = p->half;
+    ca.tw = p->tw;
+    ca.ndim = p->ndim;
+    ca.logM = p->logM;
+    for (int d = 0; d < 3; ++d) ca.log2n[d] = p->log2n[d];
+    if (fp) ca.fp = *fp;
+    ca.bp = bp;
+    ca.gbins = gbins;
+    ca.gP = gP;
+    ca.scale = (float)(1.0 / (double)p->N);
+    const size_t extra = mode == kModePlain ? 0
+                                            : (size_t)(bp.nbins + 1) * (sizeof(double) + sizeof(float)) +
+                                                  (size_t)2 * bp.ntheta * sizeof(long long);
+    Launch L;
+    const void* fn = cols_kernel(p->log2n[0], mode, -1);
+    if (!col_launch(p, fn, p->log2n[0], ca.B, ca.A, extra, ca.logTB, L)) return HUFIELD_ERR_CUDA;
+    ca.ntiles = ca.A * (ca.B >> ca.logTB);
+    const int kind = mode == kModeFilter ? kPassFilter : mode == kModeBins ? kPassBins : kPassMidFwd;
+    HF_CUDA(launch(p, kind, fn, L, &ca, s));
+    return HUFIELD_OK;
+}
+
+int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind, cudaStream_t s) {
+    ColArgs ca{};
+    ca.data = data;
+    ca.B = 1ll << p->logM;
+    ca.A = nbatch * p->n[0];
+    ca.bstride = p->n[1] << p->logM;
+    ca.tw = p->tw;
+    Launch L;
+    const void* fn = cols_kernel(p->log2n[1], kModePlain, dir);
+    if (!col_launch(p, fn, p->log2n[1], ca.B, ca.A, 0, ca.logTB, L)) return HUFIELD_ERR_CUDA;
+    ca.ntiles = ca.A * (ca.B >> ca.logTB);
+    HF_CUDA(launch(p, kind, fn, L, &ca, s));
+    return HUFIELD_OK;
+}
+
+int bin_counts(hufield_plan* p, const BinParams& bp, long long mult, int ndst, long long** dst,
+               cudaStream_t s) {
+    CountArgs ca{};
+    ca.ndim = p->ndim;
+    for (int d = 0; d < 3; ++d) ca.log2n[d] = p->log2n[d];
+    ca.nmodes = p->half;
+    ca.mult = mult;
+    ca.ndst = ndst;
+    for (int d = 0; d < ndst; ++d) ca.dst[d] = reinterpret_cast<unsigned long long*>(dst[d]);
+    ca.bp = bp;
+    Launch L;
+    L.block = 256;
+    L.smem = (size_t)bp.nbins * sizeof(unsigned long long) + (size_t)2 * bp.ntheta * sizeof(long long);
+    L.grid = occupancy_grid(reinterpret_cast<const void*>(&k_bin_counts), L.block, L.smem,
+                            ((p->half >> 3) + L.block - 1) / L.block, p->nsm);
+    if (L.grid <= 0) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassCounts, reinterpret_cast<const void*>(&k_bin_counts), L, &ca, s));
+    return HUFIELD_OK;
+}
+
+// The whole path for one field; bins are added to the (already prepared)
+// sums/counts.  nbins == 0 skips every spectrum.
+int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx, int out_dtype,
+              void* out_f, const float* levels, int nlev, int8_t* out_maps, const BinParams* bp, double* sums_f,
+              double* sums_m, const Workspace& w, cudaStream_t s) {
+    const FilterParams fp = make_filter(p, f);
+    BinParams none{};
+    none.ntheta = 1;
+    const BinParams& b = bp ? *bp : none;
+    HF_CUDA(cudaMemsetAsync(w.P, 0, sizeof(double) * (size_t)(1 + b.nbins), s));
+    int rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, s);
+    if (rc) return rc;
+    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, w.raw, w.P, s);
+    if (rc) return rc;
+    if (p->ndim == 3) {
+        rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, s);
+        if (rc) return rc;
+    }
+    if (bp && sums_f) {
+        HF_CUDA(profiled(p, kPassMisc, s, [&] {
+            k_finalize_field<<<1, 256, 0, s>>>(w.raw, w.P, b.nbins, (double)p->N, sums_f);
+            return cudaGetLastError();
+        }));
+    }
+    C2RArgs ca{};
+    ca.spec = w.spec;
+    ca.nrows = p->N >> (p->logM + 1);
+    ca.half = p->half;
+    ca.N = p->N;
+    ca.out_f = out_f;
+    ca.out_maps = reinterpret_cast<signed char*>(out_maps);
+    ca.nlev = nlev;
+    for (int t = 0; t < nlev; ++t) ca.levels[t] = levels[t];
+    ca.P = w.P;
+    ca.sigma_f = f->sigma_f;
+    ca.tw = p->tw;
+    Launch L;
+    const void* fn = c2r_kernel(p->logM, out_dtype == HUFIELD_BF16 ? 1 : 0);
+    if (!row_launch(p, fn, ca.nrows, ca.logTR, L)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassC2R, fn, L, &ca, s));
+    if (bp && nlev > 0 && sums_m) {
+        if (p->ndim == 3) {
+            rc = mid_pass(p, -1, w.spec, nlev, kPassMidMaps, s);
+            if (rc) return rc;
+        }
+        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, sums_m, nullptr, s);
+        if (rc) return rc;
+    }
+    return HUFIELD_OK;
+}
+
+int check_levels(const float* levels, int nlev) {
+    if (nlev < 0 || nlev > kMaxLevels) return HUFIELD_ERR_INVALID_ARG;
+    if (nlev > 0 && !levels) return HUFIELD_ERR_INVALID_ARG;
+    for (int t = 0; t < nlev; ++t)
+        if (!finite(levels[t])) return HUFIELD_ERR_INVALID_ARG;
+    return HUFIELD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hufield_status_string(int status) {
+    switch (status) {
+        case HUFIELD_OK: return "ok";
+        case HUFIELD_ERR_INVALID_ARG: return "invalid argument";
+        case HUFIELD_ERR_UNSUPPORTED_DIMS: return "unsupported lattice dimensions";
+        case HUFIELD_ERR_WS_TOO_SMALL: return "workspace too small";
+        case HUFIELD_ERR_CUDA: return "CUDA error";
+        case HUFIELD_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int hufield_plan_create(hufield_plan** out, const hufield_dims* dims, uint32_t flags) {
+    if (!out || !dims || (flags & ~HUFIELD_PLAN_PROFILE) != 0) return HUFIELD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (dims->ndim != 2 && dims->ndim != 3) return HUFIELD_ERR_UNSUPPORTED_DIMS;
+    long long N = 1;
+    for (int d = 0; d < dims->ndim; ++d) {
+        const long long n = dims->n[d];
+        if (!is_pow2(n) || n < 8 || n > 4096) return HUFIELD_ERR_UNSUPPORTED_DIMS;
+        N *= n;
+    }
+    if (N > (1ll << 31)) return HUFIELD_ERR_UNSUPPORTED_DIMS;
+    hufield_plan* p = new (std::nothrow) hufield_plan();
+    if (!p) return HUFIELD_ERR_CUDA;
+    p->profile = (flags & HUFIELD_PLAN_PROFILE) != 0;
+    p->ndim = dims->ndim;
+    for (int d = 0; d < 3; ++d) {
+        p->n[d] = d < dims->ndim ? dims->n[d] : 1;
+        p->log2n[d] = ilog2(p->n[d]);
+    }
+    p->N = N;
+    p->half = N / 2;
+    p->logM = p->log2n[p->ndim - 1] - 1;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+        cudaMalloc(&p->tw, sizeof(float2) * kTwN) != cudaSuccess) {
+        delete p;
+        return HUFIELD_ERR_CUDA;
+    }
+    k_twiddles<<<kTwN / 256, 256>>>(p->tw);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(p->tw);
+        delete p;
+        return HUFIELD_ERR_CUDA;
+    }
+    *out = p;
+    return HUFIELD_OK;
+}
+
+int hufield_plan_destroy(hufield_plan* p) {
+    if (!p) return HUFIELD_ERR_INVALID_ARG;
+    for (auto& r : p->records) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : p->pool) cudaEventDestroy(e);
+    cudaFree(p->tw);
+    delete p;
+    return HUFIELD_OK;
+}
+
+size_t hufield_workspace_bytes(const hufield_plan* p, int32_t nlev, int32_t nbins) {
+    if (!p || nlev < 0 || nlev > kMaxLevels || nbins < 0 || nbins > kMaxBins) return 0;
+    return ws_bytes(p, nlev, nbins);
+}
+
+int hufield_noise(hufield_plan* p, uint64_t seed, uint32_t field_idx, uint32_t* bits, float* z, void* stream) {
+    if (!p || (!bits && !z)) return HUFIELD_ERR_INVALID_ARG;
+    if ((bits && !aligned(bits)) || (z && !aligned(z))) return HUFIELD_ERR_INVALID_ARG;
+    const long long nblk = p->N / 4;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_noise, 256, 0);
+    long long g = (long long)(per_sm > 0 ? per_sm : 1) * p->nsm;
+    const long long need = (nblk + 255) / 256;
+    if (g > need) g = need;
+    k_noise<<<(int)g, 256, 0, (cudaStream_t)stream>>>(nblk, seed, field_idx, reinterpret_cast<uint4*>(bits),
+                                                       reinterpret_cast<float4*>(z));
+    HF_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
+int hufield_forward(hufield_plan* p, uint64_t seed, uint32_t field_idx, void* ws, size_t bytes, void* stream) {
+    if (!p) return HUFIELD_ERR_INVALID_ARG;
+    Workspace w;
+    int rc = carve(p, ws, bytes, 0, 0, w);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, s);
+    if (rc) return rc;
+    BinParams none{};
+    none.ntheta = 1;
+    return axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, s);
+}
+
+int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx,
+                     int32_t out_dtype, void* out_f, void* ws, size_t bytes, void* stream) {
+    if (!p) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_filter(p, f);
+    if (rc) return rc;
+    if (!out_f || !aligned(out_f) || (out_dtype != HUFIELD_F32 && out_dtype != HUFIELD_BF16))
+        return HUFIELD_ERR_INVALID_ARG;
+    Workspace w;
+    rc = carve(p, ws, bytes, 0, 0, w);
+    if (rc) return rc;
+    return run_field(p, f, seed, field_idx, out_dtype, out_f, nullptr, 0, nullptr, nullptr, nullptr, nullptr, w,
+                     (cudaStream_t)stream);
+}
+
+int hufield_threshold(hufield_plan* p, const void* f, int32_t dtype, const float* levels, int32_t nlev,
+                      int8_t* out_maps, void* stream) {
+    if (!p || !f || !out_maps || !aligned(f) || !aligned(out_maps)) return HUFIELD_ERR_INVALID_ARG;
+    if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16) return HUFIELD_ERR_INVALID_ARG;
+    if (nlev < 1) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_levels(levels, nlev);
+    if (rc) return rc;
+    Levels lv{};
+    for (int t = 0; t < nlev; ++t) lv.t[t] = levels[t];
+    const long long nblk = p->N / 4;
+    const long long g = (nblk + 255) / 256 < (long long)p->nsm * 8 ? (nblk + 255) / 256 : (long long)p->nsm * 8;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HUFIELD_F32)
+        k_threshold<0><<<(int)g, 256, 0, s>>>(nblk, f, lv, nlev, p->N, reinterpret_cast<char4*>(out_maps));
+    else
+        k_threshold<1><<<(int)g, 256, 0, s>>>(nblk, f, lv, nlev, p->N, reinterpret_cast<char4*>(out_maps));
+    HF_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
+int hufield_spectrum(hufield_plan* p, const void* y, int32_t dtype, int32_t nr, int32_t ntheta, int32_t accumulate,
+                     double* sums, int64_t* counts, void* ws, size_t bytes, void* stream) {
+    if (!p || !y || !sums || !counts || !aligned(y)) return HUFIELD_ERR_INVALID_ARG;
+    if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16 && dtype != HUFIELD_I8) return HUFIELD_ERR_INVALID_ARG;
+    if (accumulate != 0 && accumulate != 1) return HUFIELD_ERR_INVALID_ARG;
+    BinParams bp;
+    int rc = make_bins(p, nr, ntheta, bp);
+    if (rc) return rc;
+    Workspace w;
+    rc = carve(p, ws, bytes, 1, bp.nbins, w);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!accumulate) {
+        HF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * bp.nbins, s));
+        HF_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * bp.nbins, s));
+    }
+    long long* dst[1] = {reinterpret_cast<long long*>(counts)};
+    rc = bin_counts(p, bp, 1, 1, dst, s);
+    if (rc) return rc;
+    const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
+    rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, s);
+    if (rc) return rc;
+    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, sums, nullptr, s);
+}
+
+int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field0, int32_t nfields,
+                     int32_t out_dtype, void* out_f, const float* levels, int32_t nlev, int8_t* out_maps,
+                     int32_t nr, int32_t ntheta, int32_t accumulate, double* sums_f, int64_t* counts_f,
+                     double* sums_m, int64_t* counts_m, void* ws, size_t bytes, void* stream) {
+    if (!p || nfields < 1) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_filter(p, f);
+    if (rc) return rc;
+    rc = check_levels(levels, nlev);
+    if (rc) return rc;
+    if (out_dtype != HUFIELD_F32 && out_dtype != HUFIELD_BF16) return HUFIELD_ERR_INVALID_ARG;
+    if ((out_f && !aligned(out_f)) || (out_maps && !aligned(out_maps))) return HUFIELD_ERR_INVALID_ARG;
+    if (accumulate != 0 && accumulate != 1) return HUFIELD_ERR_INVALID_ARG;
+    if (!sums_f || !counts_f || (nlev > 0 && (!sums_m || !counts_m))) return HUFIELD_ERR_INVALID_ARG;
+    BinParams bp;
+    rc = make_bins(p, nr, ntheta, bp);
+    if (rc) return rc;
+    Workspace w;
+    rc = carve(p, ws, bytes, nlev, bp.nbins, w);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!accumulate) {
+        HF_CUDA(cudaMemsetAsync(sums_f, 0, sizeof(double) * bp.nbins, s));
+        HF_CUDA(cudaMemsetAsync(counts_f, 0, sizeof(int64_t) * bp.nbins, s));
+        if (nlev > 0) {
+            HF_CUDA(cudaMemsetAsync(sums_m, 0, sizeof(double) * bp.nbins * nlev, s));
+            HF_CUDA(cudaMemsetAsync(counts_m, 0, sizeof(int64_t) * bp.nbins * nlev, s));
+        }
+    }
+    long long* dst[kMaxLevels + 1];
+    dst[0] = reinterpret_cast<long long*>(counts_f);
+    for (int t = 0; t < nlev; ++t) dst[1 + t] = reinterpret_cast<long long*>(counts_m) + (long long)t * bp.nbins;
+    rc = bin_counts(p, bp, nfields, 1 + nlev, dst, s);
+    if (rc) return rc;
+    const size_t esize = out_dtype == HUFIELD_BF16 ? 2 : 4;
+    for (int e = 0; e < nfields; ++e) {
+        void* fo = out_f ? reinterpret_cast<char*>(out_f) + (size_t)e * (size_t)p->N * esize : nullptr;
+        int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * (size_t)p->N : nullptr;
+        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, w, s);
+        if (rc) return rc;
+    }
+    return HUFIELD_OK;
+}
+
+int hufield_pipeline(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx, int32_t out_dtype,
+                     void* out_f, const float* levels, int32_t nlev, int8_t* out_maps, int32_t nr, int32_t ntheta,
+                     int32_t accumulate, double* sums_f, int64_t* counts_f, double* sums_m, int64_t* counts_m,
+                     void* ws, size_t bytes, void* stream) {
+    return hufield_ensemble(p, f, seed, field_idx, 1, out_dtype, out_f, levels, nlev, out_maps, nr, ntheta,
+                            accumulate, sums_f, counts_f, sums_m, counts_m, ws, bytes, stream);
+}
+
+int hufield_profile_read(hufield_plan* p, double* ms, int64_t* launches, int32_t n) {
+    if (!p || (n > 0 && (!ms || !launches))) return HUFIELD_ERR_INVALID_ARG;
+    int rc = HUFIELD_OK;
+    for (auto& r : p->records) {
+        float t = 0.0f;
+        if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess)
+            rc = HUFIELD_ERR_CUDA;
+        if (r.kind < n) {
+            ms[r.kind] += (double)t;
+            launches[r.kind] += 1;
+        }
+        p->pool.push_back(r.start);
+        p->pool.push_back(r.stop);
+    }
+    p->records.clear();
+    return rc;
+}
+
+const char* hufield_profile_names(void) { return kPassNames; }
+
+int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, double* out, void* stream) {
+    if (!sums || !counts || !out || nbins < 1) return HUFIELD_ERR_INVALID_ARG;
+    k_bins_mean<<<(nbins + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        sums, reinterpret_cast<const long long*>(counts), nbins, out);
+    HF_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of the C ABI in include/hufield.h.
+
+Argument marshalling only: every step of the generator runs in the CUDA
+kernels of libhufield.  Tensors are torch CUDA tensors (device memory and
+streams come from PyTorch); the functions keep the C names.  A missing
+library raises at import time: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import platform
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, f"libhufield_{platform.machine()}.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEOUT = range(6)
+F32, BF16, I8 = 0, 1, 2
+PLAN_PROFILE = 1
+MAX_LEVELS = 8
+
+_DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.int8: I8}
+
+
+class HufieldError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class _Dims(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("reserved", C.c_int32), ("n", C.c_int64 * 3)]
+
+
+class _Filter(C.Structure):
+    _fields_ = [("p", C.c_float), ("axes", C.c_float * 3), ("rot", C.c_float), ("k0", C.c_float),
+                ("width", C.c_float), ("supp", C.c_float), ("sigma_f", C.c_float), ("form", C.c_int32),
+                ("nyquist", C.c_int32)]
+
+
+@dataclass
+class Filter:
+    """hufield_filter: wavenumbers in units of the Nyquist wavenumber."""
+
+    p: float = 2.0
+    axes: tuple = (1.0, 1.0, 1.0)
+    rot: float = 0.0
+    k0: float = 0.25
+    width: float = 0.05
+    supp: float = 2.0
+    sigma_f: float = 1.0
+    form: int = 0
+    nyquist: int = 0
+
+    def _c(self) -> _Filter:
+        ax = tuple(float(a) for a in self.axes) + (1.0,) * (3 - len(self.axes))
+        return _Filter(self.p, (C.c_float * 3)(*ax[:3]), self.rot, self.k0, self.width, self.supp, self.sigma_f,
+                       int(self.form), int(self.nyquist))
+
+
+def paper_filter(alpha: float, sigma: float, p: float, axes, n: int, L: float, sigma_f: float = 1.0) -> Filter:
+    """The paper's parameters (Eq. 13 with physical sigma on a cube of side L, n points
+    per axis) in Nyquist units: width = sigma / k_Nyq with k_Nyq = pi n / L."""
+    knyq = math.pi * n / L
+    return Filter(p=p, axes=tuple(axes), rot=0.0, k0=0.0, width=sigma / knyq, supp=alpha, sigma_f=sigma_f, form=1)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2509_08675_gb300.build() "
+                          "(the CUDA library is required, there is no fallback)")
+    lib = C.CDLL(LIB_PATH)
+    vp, sz, i32, u32, u64 = C.c_void_p, C.c_size_t, C.c_int32, C.c_uint32, C.c_uint64
+    fptr = C.POINTER(_Filter)
+    lib.hufield_plan_create.argtypes = [C.POINTER(vp), C.POINTER(_Dims), u32]
+    lib.hufield_plan_destroy.argtypes = [vp]
+    lib.hufield_workspace_bytes.argtypes = [vp, i32, i32]
+    lib.hufield_workspace_bytes.restype = sz
+    lib.hufield_noise.argtypes = [vp, u64, u32, vp, vp, vp]
+    lib.hufield_forward.argtypes = [vp, u64, u32, vp, sz, vp]
+    lib.hufield_generate.argtypes = [vp, fptr, u64, u32, i32, vp, vp, sz, vp]
+    lib.hufield_threshold.argtypes = [vp, vp, i32, C.POINTER(C.c_float), i32, vp, vp]
+    lib.hufield_spectrum.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]
+    lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
+                                     vp, vp, vp, vp, vp, sz, vp]
+    lib.hufield_ensemble.argtypes = [vp, fptr, u64, u32, i32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32,
+                                     i32, vp, vp, vp, vp, vp, sz, vp]
+    lib.hufield_bins_mean.argtypes = [vp, vp, i32, vp, vp]
+    lib.hufield_status_string.argtypes = [C.c_int]
+    lib.hufield_status_string.restype = C.c_char_p
+    lib.hufield_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+    lib.hufield_profile_names.argtypes = []
+    lib.hufield_profile_names.restype = C.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def status_string(status: int) -> str:
+    return _lib.hufield_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise HufieldError(rc, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _levels(levels):
+    levels = [float(x) for x in levels]
+    return (C.c_float * max(len(levels), 1))(*levels), len(levels)
+
+
+class Plan:
+    """hufield_plan for one lattice shape (2D or 3D), created on the current device."""
+
+    def __init__(self, shape, profile: bool = False):
+        self.shape = tuple(int(s) for s in shape)
+        if len(self.shape) not in (2, 3):
+            raise HufieldError(ERR_UNSUPPORTED_DIMS, "hufield_plan_create")
+        dims = _Dims(len(self.shape), 0, (C.c_int64 * 3)(*(self.shape + (1,) * (3 - len(self.shape)))))
+        h = C.c_void_p()
+        _check(_lib.hufield_plan_create(C.byref(h), C.byref(dims), PLAN_PROFILE if profile else 0),
+               "hufield_plan_create")
+        self._h = h
+        self.N = math.prod(self.shape)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.hufield_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, nlev: int = 0, nbins: int = 0, device=None) -> torch.Tensor:
+        n = hufield_workspace_bytes(self, nlev, nbins)
+        return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+def hufield_plan_create(shape, profile: bool = False) -> Plan:
+    return Plan(shape, profile)
+
+
+def hufield_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def hufield_workspace_bytes(plan: Plan, nlev: int, nbins: int) -> int:
+    n = _lib.hufield_workspace_bytes(plan.handle, nlev, nbins)
+    if n == 0:
+        raise HufieldError(ERR_INVALID_ARG, "hufield_workspace_bytes")
+    return int(n)
+
+
+def hufield_noise(plan: Plan, seed: int, field_idx: int, bits=None, z=None, stream=None):
+    _check(_lib.hufield_noise(plan.handle, seed, field_idx, _ptr(bits), _ptr(z), _stream(stream)), "hufield_noise")
+
+
+def hufield_forward(plan: Plan, seed: int, field_idx: int, ws: torch.Tensor, stream=None):
+    _check(_lib.hufield_forward(plan.handle, seed, field_idx, _ptr(ws), ws.numel(), _stream(stream)),
+           "hufield_forward")
+
+
+def hufield_generate(plan: Plan, filt: Filter, seed: int, field_idx: int, out_f: torch.Tensor, ws: torch.Tensor,
+                     stream=None):
+    fc = filt._c()
+    _check(_lib.hufield_generate(plan.handle, C.byref(fc), seed, field_idx, _DTYPES[out_f.dtype], _ptr(out_f),
+                                 _ptr(ws), ws.numel(), _stream(stream)), "hufield_generate")
+
+
+def hufield_threshold(plan: Plan, f: torch.Tensor, levels, out_maps: torch.Tensor, stream=None):
+    lv, n = _levels(levels)
+    _check(_lib.hufield_threshold(plan.handle, _ptr(f), _DTYPES[f.dtype], lv, n, _ptr(out_maps), _stream(stream)),
+           "hufield_threshold")
+
+
+def hufield_spectrum(plan: Plan, y: torch.Tensor, nr: int, ntheta: int, accumulate: bool, sums: torch.Tensor,
+                     counts: torch.Tensor, ws: torch.Tensor, stream=None):
+    _check(_lib.hufield_spectrum(plan.handle, _ptr(y), _DTYPES[y.dtype], nr, ntheta, int(accumulate), _ptr(sums),
+                                 _ptr(counts), _ptr(ws), ws.numel(), _stream(stream)), "hufield_spectrum")
+
+
+def hufield_pipeline(plan: Plan, filt: Filter, seed: int, field_idx: int, out_f, levels, out_maps, nr: int,
+                     ntheta: int, accumulate: bool, sums_f, counts_f, sums_m, counts_m, ws, stream=None,
+                     out_dtype=None):
+    fc = filt._c()
+    lv, n = _levels(levels)
+    dt = _DTYPES[out_f.dtype] if out_f is not None else (out_dtype if out_dtype is not None else F32)
+    _check(_lib.hufield_pipeline(plan.handle, C.byref(fc), seed, field_idx, dt, _ptr(out_f), lv, n, _ptr(out_maps),
+                                 nr, ntheta, int(accumulate), _ptr(sums_f), _ptr(counts_f), _ptr(sums_m),
+                                 _ptr(counts_m), _ptr(ws), ws.numel(), _stream(stream)), "hufield_pipeline")
+
+
+def hufield_ensemble(plan: Plan, filt: Filter, seed: int, field0: int, nfields: int, out_f, levels, out_maps,
+                     nr: int, ntheta: int, accumulate: bool, sums_f, counts_f, sums_m, counts_m, ws, stream=None,
+                     out_dtype=None):
+    fc = filt._c()
+    lv, n = _levels(levels)
+    dt = _DTYPES[out_f.dtype] if out_f is not None else (out_dtype if out_dtype is not None else F32)
+    _check(_lib.hufield_ensemble(plan.handle, C.byref(fc), seed, field0, nfields, dt, _ptr(out_f), lv, n,
+                                 _ptr(out_maps), nr, ntheta, int(accumulate), _ptr(sums_f), _ptr(counts_f),
+                                 _ptr(sums_m), _ptr(counts_m), _ptr(ws), ws.numel(), _stream(stream)),
+           "hufield_ensemble")
+
+
+def hufield_bins_mean(sums: torch.Tensor, counts: torch.Tensor, out_mean: torch.Tensor, stream=None):
+    _check(_lib.hufield_bins_mean(_ptr(sums), _ptr(counts), sums.numel(), _ptr(out_mean), _stream(stream)),
+           "hufield_bins_mean")
+
+
+def hufield_profile_read(plan: Plan):
+    """Per-pass device time (ms) and launch counts recorded since the last read
+    (plans created with profile=True); synchronises on the recorded events."""
+    names = _lib.hufield_profile_names().decode().split(",")
+    ms = (C.c_double * len(names))()
+    cnt = (C.c_int64 * len(names))()
+    _check(_lib.hufield_profile_read(plan.handle, ms, cnt, len(names)), "hufield_profile_read")
+    return {nm: (ms[i], cnt[i]) for i, nm in enumerate(names)}

@@ -11,3 +11,18 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built extension")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
+
+
+@pytest.fixture(scope="session")
+def hf():
+    """The CUDA library's binding, built in-tree if needed (GPU tests only)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    from paper_2509_08675_gb300 import builder
+
+    builder.build()
+    from paper_2509_08675_gb300 import hufield
+
+    return hufield

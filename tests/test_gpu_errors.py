@@ -1,0 +1,66 @@
+"""Argument checks of the C ABI: error codes, nothing enqueued."""
+import math
+
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_unsupported_dims(hf):
+    for shape in [(4, 8), (8, 8192), (12, 16), (8,), (8, 8, 8, 8), (2048, 2048, 1024)]:
+        with pytest.raises(hf.HufieldError) as e:
+            hf.Plan(shape)
+        assert e.value.status in (hf.ERR_UNSUPPORTED_DIMS, hf.ERR_INVALID_ARG)
+
+
+def test_bad_filters_rejected(hf):
+    plan = hf.Plan((32, 32))
+    ws = plan.workspace(0, 0)
+    out = torch.empty((32, 32), device="cuda")
+    bad = [dict(p=0.0), dict(p=float("nan")), dict(width=0.0), dict(supp=-1.0), dict(axes=(1.0, 0.0)),
+           dict(sigma_f=0.0), dict(k0=float("inf")), dict(form=2), dict(nyquist=1), dict(rot=float("nan"))]
+    for kw in bad:
+        with pytest.raises(hf.HufieldError) as e:
+            hf.hufield_generate(plan, hf.Filter(**kw), 0, 0, out, ws)
+        assert e.value.status == hf.ERR_INVALID_ARG, kw
+
+
+def test_workspace_checks(hf):
+    plan = hf.Plan((64, 64))
+    out = torch.empty((64, 64), device="cuda")
+    ws = plan.workspace(0, 0)
+    with pytest.raises(hf.HufieldError) as e:
+        hf.hufield_generate(plan, hf.Filter(), 0, 0, out, ws[: ws.numel() - 256])
+    assert e.value.status == hf.ERR_WS_TOO_SMALL
+    with pytest.raises(hf.HufieldError) as e:
+        hf.hufield_generate(plan, hf.Filter(), 0, 0, out, ws[8:])
+    assert e.value.status == hf.ERR_INVALID_ARG  # misaligned
+
+
+def test_bins_and_levels_checks(hf):
+    plan = hf.Plan((16, 16, 16))
+    ws = plan.workspace(8, 4096)
+    f = torch.empty((16, 16, 16), device="cuda")
+    maps = torch.empty((9, 16, 16, 16), dtype=torch.int8, device="cuda")
+    s = torch.zeros(4096 * 9, dtype=torch.float64, device="cuda")
+    c = torch.zeros(4096 * 9, dtype=torch.int64, device="cuda")
+    cases = [dict(levels=[0.0] * 9, nr=8, nt=1), dict(levels=[math.nan], nr=8, nt=1), dict(levels=[0.0], nr=0, nt=1),
+             dict(levels=[0.0], nr=8, nt=2), dict(levels=[0.0], nr=4097, nt=1)]
+    for cs in cases:
+        with pytest.raises(hf.HufieldError) as e:
+            hf.hufield_pipeline(plan, hf.Filter(axes=(1, 1, 1)), 0, 0, f, cs["levels"], maps, cs["nr"], cs["nt"],
+                                False, s, c, s, c, ws)
+        assert e.value.status == hf.ERR_INVALID_ARG, cs
+    with pytest.raises(hf.HufieldError):
+        hf.hufield_threshold(plan, f, [], maps)
+
+
+def test_error_leaves_outputs_untouched(hf):
+    plan = hf.Plan((32, 32))
+    ws = plan.workspace(0, 0)
+    out = torch.full((32, 32), 7.0, device="cuda")
+    with pytest.raises(hf.HufieldError):
+        hf.hufield_generate(plan, hf.Filter(p=-1.0), 0, 0, out, ws)
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all())

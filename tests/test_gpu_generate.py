@@ -1,0 +1,78 @@
+"""Generated field (noise -> r2c -> filter -> c2r -> normalise) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests import inputs
+from tests.gpu_common import check_field, filters, np_, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ((256, 256), inputs.filter_kwargs(inputs.C0)),
+    ((8, 8), dict(p=2.0, axes=(1.0, 1.0), k0=0.4, width=0.2, supp=2.0)),
+    ((16, 64), dict(p=3.0, axes=(1.0, 0.5), rot=0.7, k0=0.3, width=0.1, supp=4.0)),
+    ((64, 32), dict(p=1.0, axes=(1.0, 0.5), width=0.3, supp=2.0, form=1)),
+    ((512, 512), inputs.filter_kwargs(inputs.C1)),
+    ((4096, 8), dict(p=2.0, axes=(1.0, 1.0), k0=0.3, width=0.1, supp=2.0)),
+    ((8, 4096), dict(p=2.0, axes=(1.0, 1.0), k0=0.3, width=0.1, supp=2.0)),
+    ((8, 8, 8), dict(p=6.0, axes=(1.0, 1.0, 0.5), k0=0.4, width=0.2, supp=2.0)),
+    ((16, 32, 8), dict(p=6.0, axes=(1.0, 1.0, 0.5), k0=0.2, width=0.1, supp=2.0)),
+    ((32, 16, 64), dict(p=2.5, axes=(1.0, 0.7, 1.3), rot=1.1, k0=0.25, width=0.08, supp=6.0)),
+    ((64, 64, 64), inputs.filter_kwargs(inputs.C2)),
+]
+
+
+@pytest.mark.parametrize("shape,fk", CASES, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else None)
+def test_generate_parity(hf, shape, fk):
+    gf, of = filters(hf, **fk)
+    plan = hf.Plan(shape)
+    ws = plan.workspace(0, 0)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    hf.hufield_generate(plan, gf, 0, 3, out, ws)
+    torch.cuda.synchronize()
+    want = oracle.generate(shape, of, 0, 3)
+    check_field(np_(out), want)
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (32, 16, 64)])
+def test_generate_sigma_f_and_seeds(hf, shape):
+    gf, of = filters(hf, p=3.0, axes=(1.0, 0.8, 1.2), k0=0.3, width=0.1, supp=2.0)
+    gf.sigma_f = 2.5
+    plan = hf.Plan(shape)
+    ws = plan.workspace(0, 0)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    for seed, field in [(1, 0), (2**40 + 3, 9)]:
+        hf.hufield_generate(plan, gf, seed, field, out, ws)
+        torch.cuda.synchronize()
+        check_field(np_(out), oracle.generate(shape, of, seed, field, sigma_f=2.5))
+
+
+def test_generate_bf16_storage_error(hf):
+    # BF16 storage: expected relative L2 ~ 2^-9 / sqrt(3) ~ 1.1e-3 (round to nearest, 8-bit significand)
+    shape = (256, 256)
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
+    plan = hf.Plan(shape)
+    ws = plan.workspace(0, 0)
+    out = torch.empty(shape, dtype=torch.bfloat16, device="cuda")
+    hf.hufield_generate(plan, gf, 0, 0, out, ws)
+    torch.cuda.synchronize()
+    r = rel_l2(np_(out.float()).astype(np.float64), oracle.generate(shape, of, 0, 0))
+    assert 3e-4 < r < 2e-3
+
+
+def test_forward_spectrum(hf):
+    for shape in [(64, 32), (16, 8, 32), (8, 4096)]:
+        plan = hf.Plan(shape)
+        ws = plan.workspace(0, 0)
+        hf.hufield_forward(plan, 11, 2, ws)
+        torch.cuda.synchronize()
+        M = shape[-1] // 2
+        half = int(np.prod(shape)) // 2
+        got = np_(ws[: half * 8].view(torch.complex64)).reshape(shape[:-1] + (M,))
+        X = np.fft.fftn(oracle.noise(shape, 11, 2))[..., :M]
+        assert np.abs(got - X).max() < 2e-6 * math.sqrt(np.prod(shape)) * 4
+        assert rel_l2(got.astype(np.complex128), X) < 1e-6

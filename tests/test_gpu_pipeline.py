@@ -1,0 +1,121 @@
+"""Whole path (field, sign maps, binned S of field and maps) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests import inputs
+from tests.gpu_common import check_bins, check_field, check_maps, dev_zeros, filters, np_
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pipeline(hf, plan, gf, shape, seed, field, levels, nr, ntheta, out_dtype=torch.float32, nfields=1):
+    N = int(np.prod(shape))
+    nb = nr * ntheta
+    nlev = len(levels)
+    ws = plan.workspace(nlev, nb)
+    out_f = torch.empty((nfields,) + tuple(shape), dtype=out_dtype, device="cuda")
+    maps = torch.empty((nfields, max(nlev, 1)) + tuple(shape), dtype=torch.int8, device="cuda")
+    sf, cf = dev_zeros(nb, torch.float64), dev_zeros(nb, torch.int64)
+    sm, cm = dev_zeros(max(nlev, 1) * nb, torch.float64), dev_zeros(max(nlev, 1) * nb, torch.int64)
+    if nfields == 1:
+        hf.hufield_pipeline(plan, gf, seed, field, out_f, levels, maps, nr, ntheta, False, sf, cf, sm, cm, ws)
+    else:
+        hf.hufield_ensemble(plan, gf, seed, field, nfields, out_f, levels, maps, nr, ntheta, False, sf, cf, sm, cm,
+                            ws)
+    torch.cuda.synchronize()
+    return {"f": np_(out_f.float()), "maps": np_(maps), "sums_f": np_(sf), "counts_f": np_(cf),
+            "sums_m": np_(sm).reshape(-1, nb)[:nlev], "counts_m": np_(cm).reshape(-1, nb)[:nlev]}
+
+
+def compare(got, want, levels, N, e=0):
+    check_field(got["f"][e], want["f"])
+    flips = check_maps(got["maps"][e][: len(levels)], want["maps"], want["f"], levels) if levels else []
+    check_bins(got["sums_f"], want["sums_f"], got["counts_f"], want["counts_f"])
+    for t in range(len(levels)):
+        check_bins(got["sums_m"][t], want["sums_m"][t], got["counts_m"][t], want["counts_m"][t], flips=flips[t], N=N)
+
+
+CASES = [
+    ("C0-256^2", (256, 256), inputs.filter_kwargs(inputs.C0), (0.0,), 128, 1),
+    ("2d-aniso-16x64", (16, 64), dict(p=3.0, axes=(1.0, 0.5), rot=0.7, k0=0.3, width=0.1, supp=4.0),
+     (0.0, 0.5, -0.5), 8, 6),
+    ("2d-paper-64x32", (64, 32), dict(p=1.0, axes=(1.0, 0.5), width=0.3, supp=2.0, form=1), (0.0,), 16, 1),
+    ("C1-like-512^2", (512, 512), inputs.filter_kwargs(inputs.C1), (0.0, 0.5, -0.5), 64, 36),
+    ("2d-8x8", (8, 8), dict(p=2.0, axes=(1.0, 1.0), k0=0.4, width=0.3, supp=2.0), (0.0, 0.25), 4, 3),
+    ("2d-4096x8", (4096, 8), dict(p=2.0, axes=(1.0, 1.0), k0=0.3, width=0.1, supp=2.0), (0.0,), 32, 1),
+    ("2d-8x4096", (8, 4096), dict(p=2.0, axes=(1.0, 1.0), k0=0.3, width=0.1, supp=2.0), (0.0,), 32, 4),
+    ("3d-8^3", (8, 8, 8), dict(p=6.0, axes=(1.0, 1.0, 0.5), k0=0.4, width=0.2, supp=2.0), (0.0,), 4, 1),
+    ("3d-16x32x8", (16, 32, 8), dict(p=6.0, axes=(1.0, 1.0, 0.5), k0=0.2, width=0.1, supp=2.0), (0.0, 0.5), 16, 1),
+    ("3d-rot-32x16x64", (32, 16, 64), dict(p=2.5, axes=(1.0, 0.7, 1.3), rot=1.1, k0=0.25, width=0.08, supp=6.0),
+     (0.0,), 32, 1),
+    ("C2-like-64^3", (64, 64, 64), inputs.filter_kwargs(inputs.C2), (0.0,), 32, 1),
+]
+
+
+@pytest.mark.parametrize("name,shape,fk,levels,nr,nt", CASES, ids=[c[0] for c in CASES])
+def test_pipeline_parity(hf, name, shape, fk, levels, nr, nt):
+    gf, of = filters(hf, **fk)
+    plan = hf.Plan(shape)
+    got = run_pipeline(hf, plan, gf, shape, 0, 0, levels, nr, nt)
+    want = oracle.pipeline(shape, of, 0, 0, levels=levels, nr=nr, ntheta=nt)
+    compare(got, want, levels, int(np.prod(shape)))
+
+
+def test_pipeline_no_levels(hf):
+    shape = (64, 64)
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
+    plan = hf.Plan(shape)
+    got = run_pipeline(hf, plan, gf, shape, 4, 1, (), 16, 1)
+    want = oracle.pipeline(shape, of, 4, 1, levels=(), nr=16, ntheta=1)
+    check_field(got["f"][0], want["f"])
+    check_bins(got["sums_f"], want["sums_f"], got["counts_f"], want["counts_f"])
+
+
+def test_ensemble_accumulates(hf):
+    shape, levels, nr, nt = (64, 128), (0.0, 0.5, -0.5), 16, 6
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C1))
+    plan = hf.Plan(shape)
+    got = run_pipeline(hf, plan, gf, shape, 0, 5, levels, nr, nt, nfields=3)
+    sf = np.zeros(nr * nt)
+    cf = np.zeros(nr * nt, np.int64)
+    sm = np.zeros((len(levels), nr * nt))
+    cm = np.zeros((len(levels), nr * nt), np.int64)
+    for e in range(3):
+        w = oracle.pipeline(shape, of, 0, 5 + e, levels=levels, nr=nr, ntheta=nt)
+        check_field(got["f"][e], w["f"])
+        check_maps(got["maps"][e], w["maps"], w["f"], levels)
+        sf += w["sums_f"]
+        cf += w["counts_f"]
+        sm += w["sums_m"]
+        cm += w["counts_m"]
+    check_bins(got["sums_f"], sf, got["counts_f"], cf)
+    for t in range(len(levels)):
+        check_bins(got["sums_m"][t], sm[t], got["counts_m"][t], cm[t], flips=2, N=int(np.prod(shape)))
+
+
+def test_pipeline_bf16_maps_from_fp32(hf):
+    shape, levels = (128, 128), (0.0, 0.5)
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
+    plan = hf.Plan(shape)
+    a = run_pipeline(hf, plan, gf, shape, 1, 0, levels, 32, 1)
+    b = run_pipeline(hf, plan, gf, shape, 1, 0, levels, 32, 1, out_dtype=torch.bfloat16)
+    np.testing.assert_array_equal(a["maps"], b["maps"])
+    np.testing.assert_array_equal(a["sums_m"], b["sums_m"])
+    assert 3e-4 < np.linalg.norm(b["f"] - a["f"]) / np.linalg.norm(a["f"]) < 2e-3
+
+
+def test_field_bins_equal_spectrum_of_stored_field(hf):
+    # S_f from the filtered spectrum equals the spectrum call on the stored FP32 field
+    shape, nr = (32, 32, 32), 16
+    gf, _ = filters(hf, **inputs.filter_kwargs(inputs.C2))
+    plan = hf.Plan(shape)
+    got = run_pipeline(hf, plan, gf, shape, 2, 0, (0.0,), nr, 1)
+    f = torch.from_numpy(got["f"][0].astype(np.float32)).cuda()
+    s, c = dev_zeros(nr, torch.float64), dev_zeros(nr, torch.int64)
+    ws = plan.workspace(1, nr)
+    hf.hufield_spectrum(plan, f, nr, 1, False, s, c, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(np_(c), got["counts_f"])
+    np.testing.assert_allclose(np_(s), got["sums_f"], rtol=2e-5, atol=1e-9 * got["sums_f"].max())
