@@ -173,8 +173,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.fields > 0:
+        wl["nfields"] = args.fields
     if args.impl == "reference":
         return run_reference(args, wl, args.workload)
 

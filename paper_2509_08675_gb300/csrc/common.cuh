@@ -109,7 +109,7 @@ struct FilterParams {
     float inv_a[3];     // 1 / semi-axis
     float p, inv_p;     // superellipse exponent
     float cr, sr;       // cos, sin of the rotation
-    int rotated;        // 0: skip the rotation
+    int rotated;        // 0: no rotation, the norm is separable per axis
     float k0;           // band centre
     float kstar;        // analytic maximiser of K^s exp(-(K-k0)^2/(2w^2))
     float log2_kstar;

@@ -88,11 +88,13 @@ __global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ Coun
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem_raw);
     long long* ang = reinterpret_cast<long long*>(cnt + a.bp.nbins);
+    int* thr = reinterpret_cast<int*>(ang + 2 * a.bp.ntheta);
     for (int i = threadIdx.x; i < a.bp.nbins; i += blockDim.x) cnt[i] = 0;
     for (int i = threadIdx.x; i < a.bp.ntheta; i += blockDim.x) {
         ang[i] = a.bp.ang_c[i];
         ang[a.bp.ntheta + i] = a.bp.ang_s[i];
     }
+    fill_thresholds(a.bp, thr, threadIdx.x, blockDim.x);
     __syncthreads();
     const int logM = a.log2n[a.ndim - 1] - 1;
     const int M = 1 << logM;
@@ -118,9 +120,9 @@ __global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ Coun
         for (int k = k0; k < k0 + RL; ++k) {
             int bin;
             if (a.ndim == 3) {
-                bin = bin_index(a.bp, ang, n0, n1, k, 3);
+                bin = bin_index(a.bp, thr, ang, n0, n1, k, 3);
             } else {
-                bin = bin_index(a.bp, ang, n0, k, 0, 2);
+                bin = bin_index(a.bp, thr, ang, n0, k, 0, 2);
             }
             const unsigned long long w = k == 0 ? 1 : 2;
             if (bin != run_bin) {
@@ -407,7 +409,9 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     ca.scale = (float)(1.0 / (double)p->N);
     const size_t extra = mode == kModePlain ? 0
                                             : (size_t)(bp.nbins + 1) * (sizeof(double) + sizeof(float)) +
-                                                  (size_t)2 * bp.ntheta * sizeof(long long);
+                                                  (size_t)2 * bp.ntheta * sizeof(long long) +
+                                                  (size_t)(bp.nr + 1) * sizeof(int) +
+                                                  (mode == kModeFilter ? sizeof(float) << p->log2n[0] : 0);
     Launch L;
     const void* fn = cols_kernel(p->log2n[0], mode, -1);
     if (!col_launch(p, fn, p->log2n[0], ca.B, ca.A, extra, ca.logTB, L)) return HUFIELD_ERR_CUDA;
@@ -444,7 +448,8 @@ int bin_counts(hufield_plan* p, const BinParams& bp, long long mult, int ndst, l
     ca.bp = bp;
     Launch L;
     L.block = 256;
-    L.smem = (size_t)bp.nbins * sizeof(unsigned long long) + (size_t)2 * bp.ntheta * sizeof(long long);
+    L.smem = (size_t)bp.nbins * sizeof(unsigned long long) + (size_t)2 * bp.ntheta * sizeof(long long) +
+             (size_t)(bp.nr + 1) * sizeof(int);
     L.grid = occupancy_grid(reinterpret_cast<const void*>(&k_bin_counts), L.block, L.smem,
                             ((p->half >> 3) + L.block - 1) / L.block, p->nsm);
     if (L.grid <= 0) return HUFIELD_ERR_CUDA;
@@ -749,3 +754,4 @@ int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, 
 }
 
 }  // extern "C"
+

@@ -74,16 +74,11 @@ __device__ __forceinline__ int signed_index(int i, int log2n) {
     return i < (1 << (log2n - 1)) ? i : i - (1 << log2n);
 }
 
-// A(kappa) = sqrt(chi), Eqs. (8), (12), (13): zero at K = 0.
-__device__ __forceinline__ float filter_amplitude(const FilterParams& fp, float x, float y, float z, int ndim) {
-    if (fp.rotated) {
-        const float xr = fmaf(fp.cr, x, fp.sr * y);
-        const float yr = fmaf(fp.cr, y, -fp.sr * x);
-        x = xr;
-        y = yr;
-    }
-    float S = powf(fabsf(x) * fp.inv_a[0], fp.p) + powf(fabsf(y) * fp.inv_a[1], fp.p);
-    if (ndim == 3) S += powf(fabsf(z) * fp.inv_a[2], fp.p);
+// |t|^p for t >= 0 (one term of the superellipse sum, Eq. 12).
+__device__ __forceinline__ float pow_term(float t, float p) { return t > 0.0f ? exp2f(p * log2f(t)) : 0.0f; }
+
+// A = sqrt(chi) from S = K^p (Eqs. 8, 12, 13): zero at K = 0.
+__device__ __forceinline__ float amplitude_from_sum(const FilterParams& fp, float S) {
     if (!(S > 0.0f)) return 0.0f;
     const float log2K = log2f(S) * fp.inv_p;
     const float K = exp2f(log2K);
@@ -93,43 +88,77 @@ __device__ __forceinline__ float filter_amplitude(const FilterParams& fp, float 
     return expf(half_lnchi);
 }
 
-// Bin of a mode (signed indices), -1 when |kappa| >= 1.  Radial bin b holds
-// b^2 nmax^2 <= nr^2 Q < (b+1)^2 nmax^2 with Q = |kappa|^2 nmax^2 an integer;
-// the angular sector (2D) counts the sector edges the folded vector has
-// passed, from exact 64-bit cross products.
-__device__ __forceinline__ int bin_index(const BinParams& bp, const long long* ang, int n0, int n1, int n2,
-                                         int ndim) {
-    const long long v0 = (long long)n0 << bp.shift[0];
-    const long long v1 = (long long)n1 << bp.shift[1];
-    const long long v2 = ndim == 3 ? ((long long)n2 << bp.shift[2]) : 0;
-    const unsigned long long Q = 4ull * (unsigned long long)(v0 * v0 + v1 * v1 + v2 * v2);
-    const unsigned long long nm2 = 1ull << (2 * bp.log2nmax);
-    if (Q >= nm2) return -1;
-    const unsigned long long X = (unsigned long long)bp.nr * (unsigned long long)bp.nr * Q;
-    int b = (int)(sqrtf((float)Q) * (float)bp.nr) >> bp.log2nmax;
-    while (b > 0 && (unsigned long long)b * (unsigned long long)b * nm2 > X) --b;
-    while ((unsigned long long)(b + 1) * (unsigned long long)(b + 1) * nm2 <= X) ++b;
-    if (b >= bp.nr) return -1;
+// A(kappa) for a rotated filter (the norm is not separable).
+__device__ __forceinline__ float filter_amplitude(const FilterParams& fp, float x, float y, float z, int ndim) {
+    const float xr = fmaf(fp.cr, x, fp.sr * y);
+    const float yr = fmaf(fp.cr, y, -fp.sr * x);
+    float S = pow_term(fabsf(xr) * fp.inv_a[0], fp.p) + pow_term(fabsf(yr) * fp.inv_a[1], fp.p);
+    if (ndim == 3) S += pow_term(fabsf(z) * fp.inv_a[2], fp.p);
+    return amplitude_from_sum(fp, S);
+}
+
+// Exact angular sector of a folded, nonzero vector (a1 > 0, or a1 = 0 < a0):
+// the largest j with cross(d_j, a) >= 0, d_j the rounded edge directions.
+__device__ __forceinline__ int sector_exact(const long long* ang, int ntheta, long long a0, long long a1) {
+    int lo = 0, hi = ntheta - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ang[mid] * a1 - ang[ntheta + mid] * a0 >= 0)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Bin of a mode (signed indices), -1 when |kappa| >= 1.
+// Radial: Q = |kappa|^2 nmax^2 = 4 sum (n_i nmax / n_i)^2 is an integer below
+// 2^26, and bin b holds b^2 nmax^2 <= nr^2 Q < (b+1)^2 nmax^2, i.e.
+// thr[b] <= Q < thr[b+1] with the integer thresholds thr[b] =
+// ceil(b^2 nmax^2 / nr^2) (thr[nr] = nmax^2); a float square root gives the
+// first guess and integer compares settle it.  Angular (2D): the folded angle
+// from atan2f gives the sector unless it lies within 1e-4 of a sector edge,
+// where the exact 64-bit cross products against the rounded edge directions
+// decide.
+__device__ __forceinline__ int bin_index(const BinParams& bp, const int* thr, const long long* ang, int n0, int n1,
+                                         int n2, int ndim) {
+    const int v0 = n0 << bp.shift[0];
+    const int v1 = n1 << bp.shift[1];
+    const int v2 = ndim == 3 ? (n2 << bp.shift[2]) : 0;
+    const int Q = 4 * (v0 * v0 + v1 * v1 + v2 * v2);
+    if (Q >= thr[bp.nr]) return -1;
+    int b = (int)(sqrtf((float)Q) * __int_as_float((127 - bp.log2nmax) << 23) * (float)bp.nr);
+    b = b < bp.nr - 1 ? b : bp.nr - 1;
+    while (b > 0 && Q < thr[b]) --b;
+    while (Q >= thr[b + 1]) ++b;
     int sector = 0;
     if (bp.ntheta > 1) {
-        long long a0 = v0, a1 = v1;
+        int a0 = v0, a1 = v1;
         if (a1 < 0 || (a1 == 0 && a0 < 0)) {
             a0 = -a0;
             a1 = -a1;
         }
         if (a0 != 0 || a1 != 0) {
-            int lo = 0, hi = bp.ntheta - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (ang[mid] * a1 - ang[bp.ntheta + mid] * a0 >= 0)
-                    lo = mid;
-                else
-                    hi = mid - 1;
+            const float t = atan2f((float)a1, (float)a0) * ((float)bp.ntheta * 0.318309886183790672f);
+            int s = (int)t;
+            const float frac = t - (float)s;
+            if (frac < 1e-4f || frac > 1.0f - 1e-4f || s >= bp.ntheta) {
+                s = sector_exact(ang, bp.ntheta, a0, a1);
             }
-            sector = lo;
+            sector = s;
         }
     }
     return b * bp.ntheta + sector;
+}
+
+// Integer radial thresholds thr[b] = ceil(b^2 nmax^2 / nr^2), b = 0..nr.
+__device__ __forceinline__ void fill_thresholds(const BinParams& bp, int* thr, int t, int T) {
+    const unsigned long long nm2 = 1ull << (2 * bp.log2nmax);
+    const unsigned long long nr2 = (unsigned long long)bp.nr * (unsigned long long)bp.nr;
+    for (int b = t; b <= bp.nr; b += T) {
+        const unsigned long long num = (unsigned long long)b * (unsigned long long)b * nm2;
+        thr[b] = (int)((num + nr2 - 1) / nr2);
+    }
 }
 
 __device__ __forceinline__ void chunk_of(long long ntiles, long long& t0, long long& t1) {
@@ -296,6 +325,16 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
     double* dbin = reinterpret_cast<double*>(sm + (1 << (a.logTB + LOG2L)));  // nb + 1 (last: Parseval)
     long long* ang = reinterpret_cast<long long*>(dbin + nb + 1);              // 2 * ntheta
     float* fbin = reinterpret_cast<float*>(ang + 2 * a.bp.ntheta);             // nb + 1
+    int* thr = reinterpret_cast<int*>(fbin + nb + 1);                          // nr + 1
+    float* tab0 = reinterpret_cast<float*>(thr + a.bp.nr + 1);                 // FILTER: |kappa_0 / a|^p, L
+    if constexpr (MODE == kModeFilter) {
+        if (!a.fp.rotated) {
+            for (int l = c.t; l < (1 << LOG2L); l += c.T) {
+                const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                tab0[l] = l == (1 << (LOG2L - 1)) ? 0.0f : powf(fabsf(x) * a.fp.inv_a[0], a.fp.p);
+            }
+        }
+    }
     if constexpr (kAcc) {
         for (int i = c.t; i <= nb; i += c.T) {
             dbin[i] = 0.0;
@@ -305,6 +344,7 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
             ang[i] = a.bp.ang_c[i];
             ang[a.bp.ntheta + i] = a.bp.ang_s[i];
         }
+        if (nb > 0) fill_thresholds(a.bp, thr, c.t, c.T);
         __syncthreads();
     }
     const long long tpb = a.B >> a.logTB;
@@ -349,45 +389,88 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
                 for_each_element<LOG2L, false, PF::last_radix(), E>(
                     c, [&](int e, int b, int l) { base[(long long)l * a.B + b] = v[e]; });
             } else {
+                // Per-mode power (weight 2 for the k_last > 0 half) goes through
+                // shared memory so that each thread then owns E consecutive n0 of
+                // one column: consecutive modes share a bin, so one atomic per
+                // run of equal bins replaces one per mode.
+                constexpr int L = 1 << LOG2L;
                 float pacc = 0.0f;
-                for_each_element<LOG2L, false, PF::last_radix(), E>(c, [&](int e, int b, int l) {
-                    const int n0 = signed_index(l, LOG2L);
-                    const int col = (int)(c0 + b);
-                    int n1, n2, klast;
+                if constexpr (MODE == kModeFilter) {
+                    // a thread's column is fixed: T is a multiple of TB
+                    const int col = (int)(c0 + (c.t & ((1 << c.logTB) - 1)));
+                    int n1, n2;
                     if (a.ndim == 3) {
                         n1 = signed_index(col >> a.logM, a.log2n[1]);
                         n2 = col & ((1 << a.logM) - 1);
-                        klast = n2;
                     } else {
                         n1 = col;
                         n2 = 0;
-                        klast = n1;
                     }
-                    const float w = klast == 0 ? 1.0f : 2.0f;  // k and -k share a half-spectrum slot
-                    if constexpr (MODE == kModeFilter) {
-                        const bool nyq = (n0 == -(1 << (LOG2L - 1))) ||
-                                         (a.ndim == 3 && n1 == -(1 << (a.log2n[1] - 1)));
+                    const bool nyq_col = a.ndim == 3 && n1 == -(1 << (a.log2n[1] - 1));
+                    const float y = (float)n1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
+                    const float z = a.ndim == 3 ? (float)n2 * __int_as_float((127 + 1 - a.log2n[2]) << 23) : 0.0f;
+                    float s_col = 0.0f;  // separable case: the column's terms of the sum
+                    if (!a.fp.rotated) {
+                        s_col = powf(fabsf(y) * a.fp.inv_a[1], a.fp.p);
+                        if (a.ndim == 3) s_col += powf(fabsf(z) * a.fp.inv_a[2], a.fp.p);
+                    }
+                    for_each_element<LOG2L, false, PF::last_radix(), E>(c, [&](int e, int b, int l) {
+                        const bool nyq = nyq_col || l == (1 << (LOG2L - 1));
                         float h = 0.0f;
                         if (!nyq) {
-                            const float x = (float)n0 * __int_as_float((127 + 1 - LOG2L) << 23);
-                            const float y = (float)n1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
-                            const float z = a.ndim == 3 ? (float)n2 * __int_as_float((127 + 1 - a.log2n[2]) << 23)
-                                                        : 0.0f;
-                            h = filter_amplitude(a.fp, x, y, z, a.ndim);
+                            if (!a.fp.rotated) {
+                                h = amplitude_from_sum(a.fp, tab0[l] + s_col);
+                            } else {
+                                const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                                h = filter_amplitude(a.fp, x, y, z, a.ndim);
+                            }
                         }
                         v[e] = cscale(v[e], h);
-                        const float g2 = w * cabs2(v[e]);
-                        pacc += g2;
-                        if (nb > 0 && g2 != 0.0f) {
-                            const int bin = bin_index(a.bp, ang, n0, n1, n2, a.ndim);
-                            if (bin >= 0) atomicAdd(fbin + bin, g2);
+                    });
+                }
+                if (nb > 0 || MODE == kModeFilter) {
+                    float* ps = reinterpret_cast<float*>(sm);  // [b][L + 1] powers
+                    __syncthreads();                           // the FFT's last exchange is read
+                    for_each_element<LOG2L, false, PF::last_radix(), E>(c, [&](int e, int b, int l) {
+                        const int col = (int)(c0 + b);
+                        const int klast = a.ndim == 3 ? (col & ((1 << a.logM) - 1)) : col;
+                        const float w = klast == 0 ? 1.0f : 2.0f;  // k and -k share a half-spectrum slot
+                        const float pw = (MODE == kModeBins ? w * a.scale : w) * cabs2(v[e]);
+                        pacc += pw;
+                        ps[b * (L + 1) + l] = pw;
+                    });
+                    __syncthreads();
+                    if (nb > 0) {
+                        const int g0 = c.t * E;
+                        const int b = g0 >> LOG2L;
+                        const int l0 = g0 & (L - 1);
+                        const int col = (int)(c0 + b);
+                        int n1, n2;
+                        if (a.ndim == 3) {
+                            n1 = signed_index(col >> a.logM, a.log2n[1]);
+                            n2 = col & ((1 << a.logM) - 1);
+                        } else {
+                            n1 = col;
+                            n2 = 0;
                         }
-                    } else {
-                        const float s2 = w * a.scale * cabs2(v[e]);
-                        const int bin = bin_index(a.bp, ang, n0, n1, n2, a.ndim);
-                        if (bin >= 0) atomicAdd(fbin + bin, s2);
+                        int cur_bin = -1;
+                        float acc = 0.0f;
+                        const int rot = c.t & (E - 1);  // staggered start: spreads the banks
+#pragma unroll 4
+                        for (int i = 0; i < E; ++i) {
+                            const int l = l0 + ((i + rot) & (E - 1));
+                            const float pw = ps[b * (L + 1) + l];
+                            const int bin = bin_index(a.bp, thr, ang, signed_index(l, LOG2L), n1, n2, a.ndim);
+                            if (bin != cur_bin) {
+                                if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
+                                cur_bin = bin;
+                                acc = 0.0f;
+                            }
+                            acc += pw;
+                        }
+                        if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
                     }
-                });
+                }
                 if constexpr (MODE == kModeFilter) {
                     if (c.T >= 32) {  // T is a power of two: whole warps
 #pragma unroll

@@ -241,3 +241,4 @@ def hufield_profile_read(plan: Plan):
     cnt = (C.c_int64 * len(names))()
     _check(_lib.hufield_profile_read(plan.handle, ms, cnt, len(names)), "hufield_profile_read")
     return {nm: (ms[i], cnt[i]) for i, nm in enumerate(names)}
+

@@ -102,7 +102,8 @@ def test_pipeline_bf16_maps_from_fp32(hf):
     a = run_pipeline(hf, plan, gf, shape, 1, 0, levels, 32, 1)
     b = run_pipeline(hf, plan, gf, shape, 1, 0, levels, 32, 1, out_dtype=torch.bfloat16)
     np.testing.assert_array_equal(a["maps"], b["maps"])
-    np.testing.assert_array_equal(a["sums_m"], b["sums_m"])
+    # same maps; the FP64 bin sums differ only by the order of the atomic adds
+    np.testing.assert_allclose(a["sums_m"], b["sums_m"], rtol=1e-6)
     assert 3e-4 < np.linalg.norm(b["f"] - a["f"]) / np.linalg.norm(a["f"]) < 2e-3
 
 
