@@ -65,7 +65,8 @@ enum hufield_status {
     HUFIELD_ERR_UNSUPPORTED_DIMS = 2, /* ndim or n[i] outside the supported set */
     HUFIELD_ERR_WS_TOO_SMALL = 3,     /* ws_bytes below hufield_workspace_bytes() */
     HUFIELD_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed */
-    HUFIELD_ERR_TIMEOUT = 5           /* reserved for bounded device-side waits */
+    HUFIELD_ERR_TIMEOUT = 5,          /* reserved for bounded device-side waits */
+    HUFIELD_ERR_TOO_LARGE = 6         /* lattice larger than a fixed-size static scratch */
 };
 
 enum hufield_dtype { HUFIELD_F32 = 0, HUFIELD_BF16 = 1, HUFIELD_I8 = 2 };
@@ -157,6 +158,29 @@ int hufield_ensemble(hufield_plan *plan, const hufield_filter *filt, uint64_t se
                      int8_t *out_maps, int32_t nr, int32_t ntheta, int32_t accumulate, double *sums_f,
                      int64_t *counts_f, double *sums_m, int64_t *counts_m, void *ws, size_t ws_bytes,
                      void *stream);
+
+/* Allocation-free variant of hufield_spectrum, for callers that must not
+ * allocate device memory: code running where cudaMalloc is forbidden or
+ * unavailable (inside a host-managed memory budget, a plugin that may only
+ * touch buffers handed to it, or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit device synchronisation).  The paper has no
+ * counterpart; this is a deployment convenience.
+ *   - No plan and no workspace: the lattice comes as dims, and the scratch
+ *     (the half spectrum, 4 MiB) and the twiddle table (32 KiB) are file-scope
+ *     static device arrays of the library.  Every GPU that loads the library
+ *     holds them until the process exits.
+ *   - Largest lattice: N = prod n[i] <= 2^20 (e.g. 1024^2, 128^2 x 64);
+ *     larger lattices return HUFIELD_ERR_TOO_LARGE before anything is enqueued.
+ *     Other limits and arguments as hufield_spectrum.
+ *   - The first call on each device does the set-up (looks up the static
+ *     arrays' device addresses, fills the twiddle table and waits for it on
+ *     `stream`); make that first call before any stream capture.
+ *   - Calls never call cudaMalloc, cudaFree or any allocating routine.  Every
+ *     call shares the same scratch, which keeps the previous call's contents
+ *     (each call overwrites all of it before reading it); calls that overlap
+ *     on the GPU race, so serialise them (one stream, or events). */
+int hufield_spectrum_noalloc(const hufield_dims *dims, const void *y, int32_t dtype, int32_t nr, int32_t ntheta,
+                             int32_t accumulate, double *sums, int64_t *counts, void *stream);
 
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,

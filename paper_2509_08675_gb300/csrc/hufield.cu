@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -528,6 +529,7 @@ const char* hufield_status_string(int status) {
         case HUFIELD_ERR_WS_TOO_SMALL: return "workspace too small";
         case HUFIELD_ERR_CUDA: return "CUDA error";
         case HUFIELD_ERR_TIMEOUT: return "device wait timed out";
+        case HUFIELD_ERR_TOO_LARGE: return "lattice larger than the static scratch";
         default: return "unknown status";
     }
 }
@@ -755,3 +757,95 @@ int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, 
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Allocation-free spectrum (hufield_spectrum_noalloc): the scratch and the
+// twiddle table are file-scope device arrays; in host code their names are
+// host-side stand-ins, so their device addresses are looked up once per
+// device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kStaticMaxVoxels = 1ll << 20;  // half spectrum: 2^19 complex64 = 4 MiB
+static __device__ __align__(256) float2 g_static_spec[kStaticMaxVoxels / 2];
+static __device__ __align__(256) float2 g_static_tw[kTwN];
+
+struct StaticScratch {
+    bool ready = false;
+    float2* spec = nullptr;
+    float2* tw = nullptr;
+    int nsm = 0;
+};
+constexpr int kMaxDevices = 64;
+StaticScratch g_static[kMaxDevices];
+std::mutex g_static_mutex;
+
+// Once per device, with that device current: resolve the arrays' device
+// addresses and fill the twiddle table (waited for on `s`).
+int static_setup(int dev, cudaStream_t s, StaticScratch& out) {
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    StaticScratch& st = g_static[dev];
+    if (!st.ready) {
+        void* spec = nullptr;
+        void* tw = nullptr;
+        if (cudaGetSymbolAddress(&spec, g_static_spec) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        if (cudaGetSymbolAddress(&tw, g_static_tw) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        k_twiddles<<<kTwN / 256, 256, 0, s>>>(reinterpret_cast<float2*>(tw));
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        st.spec = reinterpret_cast<float2*>(spec);
+        st.tw = reinterpret_cast<float2*>(tw);
+        st.nsm = nsm;
+        st.ready = true;
+    }
+    out = st;
+    return HUFIELD_OK;
+}
+
+}  // namespace
+
+extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y, int32_t dtype, int32_t nr,
+                                        int32_t ntheta, int32_t accumulate, double* sums, int64_t* counts,
+                                        void* stream) {
+    if (!dims || !y || !sums || !counts || !aligned(y)) return HUFIELD_ERR_INVALID_ARG;
+    if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16 && dtype != HUFIELD_I8) return HUFIELD_ERR_INVALID_ARG;
+    if (accumulate != 0 && accumulate != 1) return HUFIELD_ERR_INVALID_ARG;
+    if (dims->ndim != 2 && dims->ndim != 3) return HUFIELD_ERR_UNSUPPORTED_DIMS;
+    // the plan lives on the host stack: no device allocation
+    hufield_plan p;
+    p.ndim = dims->ndim;
+    long long N = 1;
+    for (int d = 0; d < 3; ++d) {
+        const long long n = d < dims->ndim ? dims->n[d] : 1;
+        if (d < dims->ndim && (!is_pow2(n) || n < 8 || n > 4096)) return HUFIELD_ERR_UNSUPPORTED_DIMS;
+        p.n[d] = n;
+        p.log2n[d] = ilog2(n);
+        N *= n;
+    }
+    if (N > kStaticMaxVoxels) return HUFIELD_ERR_TOO_LARGE;
+    p.N = N;
+    p.half = N / 2;
+    p.logM = p.log2n[p.ndim - 1] - 1;
+    BinParams bp;
+    int rc = make_bins(&p, nr, ntheta, bp);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaGetDevice(&p.device) != cudaSuccess) return HUFIELD_ERR_CUDA;
+    if (p.device < 0 || p.device >= kMaxDevices) return HUFIELD_ERR_CUDA;
+    StaticScratch st;
+    rc = static_setup(p.device, s, st);
+    if (rc) return rc;
+    p.nsm = st.nsm;
+    p.tw = st.tw;
+    if (!accumulate) {
+        HF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * bp.nbins, s));
+        HF_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * bp.nbins, s));
+    }
+    long long* dst[1] = {reinterpret_cast<long long*>(counts)};
+    rc = bin_counts(&p, bp, 1, 1, dst, s);
+    if (rc) return rc;
+    const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
+    rc = forward_rows_and_mid(&p, src, y, 0, 0, st.spec, s);
+    if (rc) return rc;
+    return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, sums, nullptr, s);
+}

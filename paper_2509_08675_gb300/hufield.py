@@ -18,7 +18,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, f"libhufield_{platform.machine()}.so")
 
-OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEOUT = range(6)
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEOUT, ERR_TOO_LARGE = range(7)
 F32, BF16, I8 = 0, 1, 2
 PLAN_PROFILE = 1
 MAX_LEVELS = 8
@@ -90,6 +90,7 @@ def _load():
     lib.hufield_ensemble.argtypes = [vp, fptr, u64, u32, i32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32,
                                      i32, vp, vp, vp, vp, vp, sz, vp]
     lib.hufield_bins_mean.argtypes = [vp, vp, i32, vp, vp]
+    lib.hufield_spectrum_noalloc.argtypes = [C.POINTER(_Dims), vp, i32, i32, i32, i32, vp, vp, vp]
     lib.hufield_status_string.argtypes = [C.c_int]
     lib.hufield_status_string.restype = C.c_char_p
     lib.hufield_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
@@ -242,3 +243,14 @@ def hufield_profile_read(plan: Plan):
     _check(_lib.hufield_profile_read(plan.handle, ms, cnt, len(names)), "hufield_profile_read")
     return {nm: (ms[i], cnt[i]) for i, nm in enumerate(names)}
 
+
+def hufield_spectrum_noalloc(shape, y: torch.Tensor, nr: int, ntheta: int, accumulate: bool, sums: torch.Tensor,
+                             counts: torch.Tensor, stream=None):
+    """hufield_spectrum without a plan or workspace: the library's static device
+    scratch holds the spectrum (lattices up to 2^20 voxels; see include/hufield.h)."""
+    shape = tuple(int(v) for v in shape)
+    if len(shape) not in (2, 3):
+        raise HufieldError(ERR_UNSUPPORTED_DIMS, "hufield_spectrum_noalloc")
+    dims = _Dims(len(shape), 0, (C.c_int64 * 3)(*(shape + (1,) * (3 - len(shape)))))
+    _check(_lib.hufield_spectrum_noalloc(C.byref(dims), _ptr(y), _DTYPES[y.dtype], nr, ntheta, int(accumulate),
+                                         _ptr(sums), _ptr(counts), _stream(stream)), "hufield_spectrum_noalloc")
