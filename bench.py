@@ -41,6 +41,10 @@ WORKLOADS = {
                    levels=(0.0,), nr=128, ntheta=1),
 }
 METRIC = "voxels/s for gen+threshold+S(k)"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant pass from an ncu capture of the current kernels, keyed by
+# (workload, pass); None until captured.
+TRAFFIC = {}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -174,6 +178,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
+    ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.fields > 0:
@@ -201,6 +206,44 @@ def main():
         dist.barrier()
     from paper_2509_08675_gb300 import hufield as hf
 
+    res = measure(hf, torch, wl, args.workload, args, rank, world, dist)
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(hf, torch, res["plan"], res["filt"], wl, args, *res["bufs"], res["field0"], dist, world)
+    also = {}
+    if args.also and args.also != args.workload and world == 1:
+        wl2 = dict(WORKLOADS[args.also])
+        r2 = measure(hf, torch, wl2, args.also, args, rank, world, dist)
+        also[args.also] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "pipeline", "passes", "clocks")}
+        del r2
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl, wl["nfields"])
+    if rank == 0:
+        shape, nlev = wl["shape"], len(wl["levels"])
+        line = {"metric": METRIC, "value": res["value"], "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": args.workload, "shape": list(shape), "fields_per_step": wl["nfields"],
+                           "levels": list(wl["levels"]), "bins": [wl["nr"], wl["ntheta"]],
+                           "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
+                "roofline": res["roofline"],
+                "pipeline": res["pipeline"],
+                "passes": res["passes"],
+                "gpu_launches": res["gpu_launches"],
+                "clocks": res["clocks"],
+                "e2e": e2e,
+                "cpu_baseline": cpu}
+        if also:
+            line["also"] = also
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure(hf, torch, wl, name, args, rank, world, dist):
+    """Device-timed steps of one workload: per-step CUDA events on the launching
+    stream, L2 flushed between steps, live per-pass event times of the plan."""
     shape, nf, levels = wl["shape"], wl["nfields"], wl["levels"]
     nlev, nr, nt = len(levels), wl["nr"], wl["ntheta"]
     nb = nr * nt
@@ -226,6 +269,8 @@ def main():
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
+    if hf.hufield_workspace_status(ws) != hf.OK:
+        raise RuntimeError("device-side timeout during warm-up")
     hf.hufield_profile_read(plan)  # drop warm-up records
 
     clocks = ClockSampler()
@@ -245,14 +290,15 @@ def main():
     torch.cuda.synchronize()
     bus = None
     try:
-        pr = torch.cuda.get_device_properties(local)
+        pr = torch.cuda.get_device_properties(torch.cuda.current_device())
         bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
     except Exception:
         bus = None
     clk = clocks.stop(bus)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
+    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
     prof = hf.hufield_profile_read(plan)
+    if hf.hufield_workspace_status(ws) != hf.OK:
+        raise RuntimeError("device-side timeout during the timed steps")
     if dist is not None:
         t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -271,39 +317,16 @@ def main():
         passes[k] = {"launches": cnt, "ms_total": round(ms, 4), "ms_per_launch": round(per, 5),
                      "GBps": round(gbs, 1) if gbs else None, "frac": round(gbs / peak, 4) if gbs else None}
     dom = max((k for k in passes if algo.get(k, 0)), key=lambda k: passes[k]["ms_total"])
-    per_step_bytes = nf * sum(algo[k] * passes[k]["launches"] / (args.steps * nf) for k in passes if algo.get(k))
+    per_step_bytes = sum(algo[k] * passes[k]["launches"] / args.steps for k in passes if algo.get(k))
     pipe_gbs = per_step_bytes / (tot_ms / args.steps / 1e3) / 1e9
-    traffic = None
     roof = {"bound": "hbm", "achieved": passes[dom]["GBps"], "peak": peak, "unit": "GB/s",
-            "frac": passes[dom]["frac"], "traffic": traffic, "kernel": dom, "peak_source": peak_kind}
-
-    e2e = None
-    if not args.no_e2e:
-        e2e = measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws, field0, dist, world)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(wl, nf)
-
-    launches = sum(p["launches"] for p in passes.values()) // args.steps
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-                "config": {"workload": args.workload, "shape": list(shape), "fields_per_step": nf,
-                           "levels": list(levels), "bins": [nr, nt], "l2": "flushed between timed steps",
-                           "parallelism": f"replicas x{world}"},
-                "roofline": roof,
-                "pipeline": {"bytes_per_voxel": round(per_step_bytes / (nf * N), 2), "GBps": round(pipe_gbs, 1),
-                             "frac": round(pipe_gbs / peak, 4)},
-                "passes": passes,
-                "gpu_launches": launches * args.steps,
-                "clocks": clk,
-                "e2e": e2e,
-                "cpu_baseline": cpu}
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+            "frac": passes[dom]["frac"], "traffic": TRAFFIC.get((name, dom)),
+            "kernel": dom, "peak_source": peak_kind}
+    return {"value": value, "ms_per_step": tot_ms / args.steps, "roofline": roof,
+            "pipeline": {"bytes_per_voxel": round(per_step_bytes / (nf * N), 2), "GBps": round(pipe_gbs, 1),
+                         "frac": round(pipe_gbs / peak, 4)},
+            "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()), "clocks": clk,
+            "plan": plan, "filt": filt, "bufs": (out_f, maps, sf, cf, sm, cm, ws), "field0": field0}
 
 
 def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws, field0, dist, world):

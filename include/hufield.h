@@ -76,6 +76,12 @@ typedef struct hufield_plan hufield_plan;
 /* Plan flag: record CUDA events around every kernel launch of the plan's
  * calls (per-pass device times for profiling; see hufield_profile_read). */
 #define HUFIELD_PLAN_PROFILE 1u
+/* Plan flag, test hook for failure detection: the plan's strided passes never
+ * issue the load of their first tile and bound each wait to ~2 ms, so every
+ * such pass gives up, drains its own copies, and records a timeout in the
+ * workspace status word (see hufield_workspace_status).  Outputs are then
+ * undefined.  Not for production use. */
+#define HUFIELD_PLAN_INJECT_TIMEOUT 2u
 
 typedef struct {
     int32_t ndim;   /* 2 or 3 */
@@ -97,7 +103,8 @@ typedef struct {
 
 /* Plan for one lattice.  Allocates the twiddle table on the current CUDA
  * device and chooses launch shapes; the plan must be used on that device.
- * flags is 0 or HUFIELD_PLAN_PROFILE.  Returns HUFIELD_ERR_UNSUPPORTED_DIMS
+ * flags is 0 or a combination of HUFIELD_PLAN_PROFILE and
+ * HUFIELD_PLAN_INJECT_TIMEOUT.  Returns HUFIELD_ERR_UNSUPPORTED_DIMS
  * for a lattice outside the set above. */
 int hufield_plan_create(hufield_plan **plan, const hufield_dims *dims, uint32_t flags);
 int hufield_plan_destroy(hufield_plan *plan);
@@ -114,7 +121,8 @@ int hufield_noise(hufield_plan *plan, uint64_t seed, uint32_t field_idx, uint32_
                   void *stream);
 
 /* Forward r2c DFT of the noise (diagnostic): X(n) = sum_x z(x) e^{-2 pi i n.x/N}
- * into ws as complex64 [n0][n1]...[n_last/2], i.e. the half spectrum without
+ * into ws at byte offset 256 (every workspace begins with a 256-byte status
+ * header) as complex64 [n0][n1]...[n_last/2], i.e. the half spectrum without
  * its Nyquist plane along the last axis (k_last = 0 .. n_last/2 - 1). */
 int hufield_forward(hufield_plan *plan, uint64_t seed, uint32_t field_idx, void *ws, size_t ws_bytes,
                     void *stream);
@@ -185,6 +193,14 @@ int hufield_spectrum_noalloc(const hufield_dims *dims, const void *y, int32_t dt
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,
                       void *stream);
+
+/* Device-side status of the most recent call that used workspace `ws`: the
+ * strided passes bound every wait on their bulk copies (~1 s); one that runs
+ * out leaves the call's outputs undefined, returns early and sets a bit in
+ * the first word of the workspace (every call clears that word when it
+ * starts, in stream order).  This function waits for `stream`, reads the word
+ * and returns HUFIELD_ERR_TIMEOUT if the bit is set, HUFIELD_OK otherwise. */
+int hufield_workspace_status(const void *ws, void *stream);
 
 /* Profiling (plans created with HUFIELD_PLAN_PROFILE): waits for the events
  * recorded since the previous read and adds, per pass kind, the device time

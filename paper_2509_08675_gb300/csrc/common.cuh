@@ -63,33 +63,67 @@ __device__ __forceinline__ uint4 noise_block(uint64_t seed, uint32_t field_idx, 
                          (uint32_t)(seed >> 32));
 }
 
-// ln u for u = (x + 1/2) 2^-32.  Below 1/2 the FP32 value of u carries the
-// full relative precision; above it the complement 1 - u = (~x + 1/2) 2^-32
-// is exact in integers and log1pf keeps the small logarithm accurate.
+// ln u for u = (x + 1/2) 2^-32, without the library logarithm.  The argument
+// is reduced exactly to u = 2^e m with m in [sqrt(1/2), sqrt(2)) and f = m - 1
+// (exact), then ln u = e ln2 + 2 atanh(f / (2 + f)) by the series
+// 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9), |s| <= 0.1716 (Abramowitz & Stegun
+// 4.1.27; the next term is below 2.5e-9 of the sum).  For u >= 1/2 the
+// complement d = 1 - u = (~x + 1/2) 2^-32 is exact in integers, so f = -d or
+// f = 1 - 2d stays exact and ln u keeps full relative precision near u = 1.
 __device__ __forceinline__ float log_uniform(uint32_t x) {
-    if (x < 0x80000000u) {
-        return logf(fmaf(__uint2float_rn(x), 0x1p-32f, 0x1p-33f));
+    float f;
+    int e;
+    if (x >= 0x80000000u) {
+        const float d = fmaf(__uint2float_rn(~x), 0x1p-32f, 0x1p-33f);  // (0, 1/2]
+        const bool low = d > 0.29289321881345248f;                       // u < sqrt(1/2)
+        f = low ? fmaf(-2.0f, d, 1.0f) : -d;
+        e = low ? -1 : 0;
+    } else {
+        const float u = fmaf(__uint2float_rn(x), 0x1p-32f, 0x1p-33f);  // (0, 1/2)
+        const int bits = __float_as_int(u);
+        e = ((bits >> 23) & 0xff) - 127;
+        float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);  // [1, 2)
+        if (m > 1.41421356237309505f) {
+            m *= 0.5f;
+            e += 1;
+        }
+        f = m - 1.0f;
     }
-    const float d = fmaf(__uint2float_rn(~x), 0x1p-32f, 0x1p-33f);
-    return log1pf(-d);
+    const float s = __fdividef(f, 2.0f + f);
+    const float s2 = s * s;
+    const float p = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+    // e ln2 with ln2 split into a head exact in FP32 and a tail
+    const float fe = (float)e;
+    return fmaf(fe, 0.693145751953125f, fmaf(fe, 1.42860682030941723e-6f, 2.0f * s * p));
 }
 
 // (cos, sin)(2 pi u) for u = (x + 1/2) 2^-32: the quadrant comes from the top
-// two bits (after centring), the remainder |y| <= 1/4 (units of pi) is
-// formed exactly in integers before one rounding to FP32.
+// two bits (after centring) and the remainder y = (2 rem + 1) 2^-32, |y| <= 1/4
+// (angle pi y), is formed exactly in integers before one rounding to FP32.
+// sin(pi y) and cos(pi y) are their Taylor series in pi y up to the y^9 and
+// y^10 terms (truncation below 2e-9 on |y| <= 1/4), evaluated by Horner.
 __device__ __forceinline__ float2 cis_uniform(uint32_t x) {
     const uint32_t xs = x + 0x20000000u;  // centre the quadrants
     const uint32_t q = xs >> 30;
     const int32_t rem = (int32_t)(xs & 0x3FFFFFFFu) - 0x20000000;  // [-2^29, 2^29)
-    // angle = q pi/2 + 2 pi (rem + 1/2) / 2^32  ->  sincospi argument (2 rem + 1) 2^-32
     const float y = __int2float_rn(2 * rem + 1) * 0x1p-32f;
-    float s, c;
-    sincospif(y, &s, &c);
+    const float y2 = y * y;
+    // pi, -pi^3/3!, pi^5/5!, -pi^7/7!, pi^9/9!
+    const float sp = y * fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, 0.0821458866111282287f, -0.599264529320792077f),
+                                                 2.55016403987734544f),
+                                      -5.16771278004997003f),
+                              3.14159265358979324f);
+    // 1, -pi^2/2!, pi^4/4!, -pi^6/6!, pi^8/8!, -pi^10/10!
+    const float cp = fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, -0.0258068913900140600f, 0.235330630358893204f),
+                                                     -1.33526276885458949f),
+                                          4.05871212641676822f),
+                               -4.93480220054467931f),
+                          1.0f);
     switch (q) {
-        case 0: return make_float2(c, s);
-        case 1: return make_float2(-s, c);
-        case 2: return make_float2(-c, -s);
-        default: return make_float2(s, -c);
+        case 0: return make_float2(cp, sp);
+        case 1: return make_float2(-sp, cp);
+        case 2: return make_float2(-cp, -sp);
+        default: return make_float2(sp, -cp);
     }
 }
 

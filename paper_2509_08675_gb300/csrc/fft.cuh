@@ -9,9 +9,11 @@
 // input r by W_{Ns R}^{(j mod Ns) r}, and writes output r at
 // (j / Ns) Ns R + (j mod Ns) + r Ns.
 //
-// Two thread layouts:
+// The geometry (line length, lines per CTA, threads) is a compile-time
+// context, so every shared-memory address reduces to a per-thread base plus
+// an immediate offset.  Two thread layouts:
 //   COL  line b = g mod TB, butterfly j = g / TB  (lines are adjacent columns
-//        of a strided axis; lanes run over b so global loads are coalesced)
+//        of a strided axis; lanes run over b)
 //   ROW  butterfly j = g mod (L/R), line b = g / (L/R) (lines are contiguous
 //        rows; lanes run over j)
 // with g = t + T i for the thread's i-th butterfly.
@@ -106,92 +108,97 @@ template <int LOG2L, bool REV>
 struct Plan {
     static constexpr int L = 1 << LOG2L;
     static constexpr int NS = (LOG2L + 3) / 4;
-    static constexpr int bits_fwd(int s) {
-        return LOG2L / NS + (s >= NS - LOG2L % NS ? 1 : 0);
-    }
+    static constexpr int bits_fwd(int s) { return LOG2L / NS + (s >= NS - LOG2L % NS ? 1 : 0); }
     static constexpr int bits(int s) { return REV ? bits_fwd(NS - 1 - s) : bits_fwd(s); }
     static constexpr int radix(int s) { return 1 << bits(s); }
     static constexpr int log2_before(int s) { return s == 0 ? 0 : log2_before(s - 1) + bits(s - 1); }
-    static constexpr int max_radix() {
-        int m = 1;
-        for (int s = 0; s < NS; ++s) m = radix(s) > m ? radix(s) : m;
-        return m;
-    }
     static constexpr int first_radix() { return radix(0); }
     static constexpr int last_radix() { return radix(NS - 1); }
 };
 
-// Thread context for the butterfly mapping.
-struct Ctx {
-    int t;      // thread index
-    int T;      // threads in the CTA
-    int logTB;  // log2 of lines per CTA (TB)
+// Elements per thread for a line length: 16, never more than the line itself.
+constexpr int elems_for(int log2l) { return log2l >= 4 ? 16 : (1 << log2l); }
+
+// Compile-time geometry of a CTA: TB = 2^LOGTB lines of L = 2^LOG2L, E
+// elements per thread, T threads.  TWLOG: log2 of the length of the CTA's
+// twiddle table W_{2^TWLOG}^q in shared memory (>= LOG2L).
+template <int LOG2L_, int LOGTB_, bool ROW_, int TWLOG_>
+struct Geo {
+    static constexpr int LOG2L = LOG2L_;
+    static constexpr int L = 1 << LOG2L_;
+    static constexpr int LOGTB = LOGTB_;
+    static constexpr int TB = 1 << LOGTB_;
+    static constexpr bool ROW = ROW_;
+    static constexpr int E = elems_for(LOG2L_);
+    static constexpr int T = (TB * L) / E;
+    static constexpr int TWLOG = TWLOG_;
+    static_assert(T >= 1 && T <= 512, "threads per CTA");
+    static_assert(TWLOG_ >= LOG2L_, "twiddle table too short");
 };
 
 // Butterfly (line b, index j) of a thread's i-th radix-2^LR butterfly.
-template <int LOG2L, bool ROW, int LR>
-__device__ __forceinline__ void butterfly_of(const Ctx& c, int i, int& b, int& j) {
-    const int g = c.t + c.T * i;
-    if constexpr (ROW) {
-        j = g & ((1 << (LOG2L - LR)) - 1);
-        b = g >> (LOG2L - LR);
+template <class G, int LR>
+__device__ __forceinline__ void butterfly_of(int t, int i, int& b, int& j) {
+    const int g = t + G::T * i;
+    if constexpr (G::ROW) {
+        j = g & ((1 << (G::LOG2L - LR)) - 1);
+        b = g >> (G::LOG2L - LR);
     } else {
-        b = g & ((1 << c.logTB) - 1);
-        j = g >> c.logTB;
+        b = g & (G::TB - 1);
+        j = g >> G::LOGTB;
     }
 }
 
 // Shared-memory slot of element l of line b.  ROW lines are contiguous
 // with the low four bits of l XOR-ed by the next four (bank spread for the
 // stride patterns of the exchanges); COL tiles are [l][b].
-template <int LOG2L, bool ROW>
-__device__ __forceinline__ int smem_slot(const Ctx& c, int l, int b) {
-    if constexpr (ROW) {
-        return (b << LOG2L) + (l ^ ((l >> 4) & 15));
+template <class G>
+__device__ __forceinline__ int smem_slot(int l, int b) {
+    if constexpr (G::ROW) {
+        return (b << G::LOG2L) + (l ^ ((l >> 4) & 15));
     } else {
-        return (l << c.logTB) + b;
+        return (l << G::LOGTB) + b;
     }
 }
 
 // Element positions of the data a thread holds before stage 0 (IN) or after
 // the last stage (OUT) of a plan: the i-th butterfly of radix R holds
 // elements j + r L/R, r = 0..R-1, in v[i R + r].
-template <int LOG2L, bool ROW, int R, int E, class F>
-__device__ __forceinline__ void for_each_element(const Ctx& c, F&& f) {
+template <class G, int R, class F>
+__device__ __forceinline__ void for_each_element(int t, F&& f) {
     constexpr int LR = (R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 0);
     static_assert((1 << LR) == R, "radix");
 #pragma unroll
-    for (int i = 0; i < E / R; ++i) {
+    for (int i = 0; i < G::E / R; ++i) {
         int b, j;
-        butterfly_of<LOG2L, ROW, LR>(c, i, b, j);
+        butterfly_of<G, LR>(t, i, b, j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) f(i * R + r, b, j + r * ((1 << LOG2L) / R));
+        for (int r = 0; r < R; ++r) f(i * R + r, b, j + r * (G::L / R));
     }
 }
 
-template <int LOG2L, int E, int DIR, bool REV, bool ROW, int S>
+template <class G, int DIR, bool REV, int S>
 struct Stages {
-    using P = Plan<LOG2L, REV>;
+    using P = Plan<G::LOG2L, REV>;
     static constexpr int R = P::radix(S);
     static constexpr int LR = P::bits(S);
     static constexpr int LNS = P::log2_before(S);  // log2 Ns
+    static constexpr int E = G::E;
     static_assert(E % R == 0, "E must be a multiple of every radix");
 
-    __device__ __forceinline__ static void run(float2 (&v)[E], float2* sm, const float2* __restrict__ tw,
-                                               const Ctx& c) {
-        constexpr int L = 1 << LOG2L;
+    __device__ __forceinline__ static void run(float2 (&v)[E], float2* sm, const float2* tw, int t) {
         constexpr int NB = E / R;
         if constexpr (LNS > 0) {
-            // twiddles W_{Ns R}^{k r}, k = j mod Ns
-            constexpr int shift = kTwLog2 - (LNS + LR);
+            // twiddles W_{Ns R}^{k r} = tw[k r 2^TWLOG / (Ns R)], k = j mod Ns
+            constexpr int shift = G::TWLOG - (LNS + LR);
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
                 int b, j;
-                butterfly_of<LOG2L, ROW, LR>(c, i, b, j);
+                butterfly_of<G, LR>(t, i, b, j);
                 const int k = j & ((1 << LNS) - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = __ldg(tw + ((k * r) << shift));
+                    const float2 w = tw[(k * r) << shift];
                     v[i * R + r] = DIR < 0 ? cmul(v[i * R + r], w) : cmulc(v[i * R + r], w);
                 }
             }
@@ -203,40 +210,34 @@ struct Stages {
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
                 int b, j;
-                butterfly_of<LOG2L, ROW, LR>(c, i, b, j);
+                butterfly_of<G, LR>(t, i, b, j);
                 const int k = j & ((1 << LNS) - 1);
                 const int base = ((j >> LNS) << (LNS + LR)) + k;
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[smem_slot<LOG2L, ROW>(c, base + (r << LNS), b)] = v[i * R + r];
+                for (int r = 0; r < R; ++r) sm[smem_slot<G>(base + (r << LNS), b)] = v[i * R + r];
             }
             __syncthreads();
             constexpr int R2 = P::radix(S + 1);
-            for_each_element<LOG2L, ROW, R2, E>(c, [&](int e, int b, int l) {
-                v[e] = sm[smem_slot<LOG2L, ROW>(c, l, b)];
-            });
-            (void)L;
-            Stages<LOG2L, E, DIR, REV, ROW, S + 1>::run(v, sm, tw, c);
+            for_each_element<G, R2>(t, [&](int e, int b, int l) { v[e] = sm[smem_slot<G>(l, b)]; });
+            Stages<G, DIR, REV, S + 1>::run(v, sm, tw, t);
         }
     }
 };
 
 // Full transform.  On entry v holds the plan's IN positions, on exit its OUT
-// positions.  Uses sm (TB * L slots) for the exchanges; contains
-// __syncthreads(), so every thread of the CTA must call it.
-template <int LOG2L, int E, int DIR, bool REV, bool ROW>
-__device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const float2* __restrict__ tw, const Ctx& c) {
-    Stages<LOG2L, E, DIR, REV, ROW, 0>::run(v, sm, tw, c);
+// positions.  sm (TB * L slots) holds the exchanges and tw the CTA's twiddle
+// table (shared memory); contains __syncthreads(), so every thread of the CTA
+// must call it.
+template <class G, int DIR, bool REV>
+__device__ __forceinline__ void fft(float2 (&v)[G::E], float2* sm, const float2* tw, int t) {
+    Stages<G, DIR, REV, 0>::run(v, sm, tw, t);
 }
 
-// Elements per thread for a line length: 16 (32 for the long strided lines),
-// never more than the line itself.
-template <int LOG2L>
-struct ColShape {
-    static constexpr int E = LOG2L >= 11 ? 32 : (LOG2L >= 4 ? 16 : (1 << LOG2L));
-};
-template <int LOG2L>
-struct RowShape {
-    static constexpr int E = LOG2L >= 4 ? 16 : (1 << LOG2L);
-};
+// The CTA's twiddle table: tw_s[q] = W_{2^TWLOG}^q from the plan's 4096-entry
+// table, q < 2^TWLOG.
+template <class G>
+__device__ __forceinline__ void load_twiddles(float2* tw_s, const float2* __restrict__ tw, int t) {
+    for (int q = t; q < (1 << G::TWLOG); q += G::T) tw_s[q] = __ldg(tw + (q << (kTwLog2 - G::TWLOG)));
+}
 
 }  // namespace hf

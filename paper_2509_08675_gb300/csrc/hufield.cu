@@ -9,18 +9,30 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/hufield.h"
 #include "kernels.cuh"
 #include "launch.h"
 
 namespace hf {
-const void* cols_plain_kernel(int log2l, int mode, int dir);
-const void* cols_acc_kernel(int log2l, int mode, int dir);
+KernelInfo r2c_kernel_noise(int log2m, bool big, int src);
+KernelInfo r2c_kernel_src(int log2m, bool big, int src);
+KernelInfo cols_kernel_plain(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_filter(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_bins(int log2l, bool big, int mode, int dir);
 
-const void* cols_kernel(int log2l, int mode, int dir) {
-    return mode == kModePlain ? cols_plain_kernel(log2l, mode, dir) : cols_acc_kernel(log2l, mode, dir);
+KernelInfo r2c_kernel(int log2m, bool big, int src) {
+    return src == kSrcNoise ? r2c_kernel_noise(log2m, big, src) : r2c_kernel_src(log2m, big, src);
 }
-int col_elems(int log2l) { return log2l >= 11 ? 32 : (log2l >= 4 ? 16 : (1 << log2l)); }
+KernelInfo cols_kernel(int log2l, bool big, int mode, int dir) {
+    switch (mode) {
+        case kModePlain: return cols_kernel_plain(log2l, big, mode, dir);
+        case kModeFilter: return cols_kernel_filter(log2l, big, mode, dir);
+        default: return cols_kernel_bins(log2l, big, mode, dir);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Small kernels.
@@ -89,12 +101,9 @@ __global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ Coun
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem_raw);
     long long* ang = reinterpret_cast<long long*>(cnt + a.bp.nbins);
-    int* thr = reinterpret_cast<int*>(ang + 2 * a.bp.ntheta);
+    int* thr = reinterpret_cast<int*>(ang + 2 * (a.bp.ntheta + 1));
     for (int i = threadIdx.x; i < a.bp.nbins; i += blockDim.x) cnt[i] = 0;
-    for (int i = threadIdx.x; i < a.bp.ntheta; i += blockDim.x) {
-        ang[i] = a.bp.ang_c[i];
-        ang[a.bp.ntheta + i] = a.bp.ang_s[i];
-    }
+    fill_angles(a.bp, ang, threadIdx.x, blockDim.x);
     fill_thresholds(a.bp, thr, threadIdx.x, blockDim.x);
     __syncthreads();
     const int logM = a.log2n[a.ndim - 1] - 1;
@@ -118,12 +127,13 @@ __global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ Coun
         }
         int run_bin = -1;
         unsigned long long run = 0;
+        BinRun cache;
         for (int k = k0; k < k0 + RL; ++k) {
             int bin;
             if (a.ndim == 3) {
-                bin = bin_index(a.bp, thr, ang, n0, n1, k, 3);
+                bin = bin_index_run(a.bp, thr, ang, n0, n1, k, 3, cache);
             } else {
-                bin = bin_index(a.bp, thr, ang, n0, k, 0, 2);
+                bin = bin_index_run(a.bp, thr, ang, n0, k, 0, 2, cache);
             }
             const unsigned long long w = k == 0 ? 1 : 2;
             if (bin != run_bin) {
@@ -183,6 +193,9 @@ struct hufield_plan {
     int device;
     int nsm;
     float2* tw;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;  // driver entry point (no libcuda link)
+    long long wait_budget = 0;                            // SM cycles per bounded mbarrier wait
+    bool inject_timeout = false;                          // test hook (HUFIELD_PLAN_INJECT_TIMEOUT)
 };
 
 namespace {
@@ -191,6 +204,21 @@ struct Launch {
     int grid = 0, block = 0;
     size_t smem = 0;
 };
+
+// Bound of one mbarrier wait: ~1 s at the GB300's 2.07 GHz SM clock.
+constexpr long long kWaitBudget = 2000000000ll;
+// Bound used by the timeout test hook (~2 ms).
+constexpr long long kInjectWaitBudget = 4000000ll;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_entry() {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
 
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(long long v) {
@@ -214,33 +242,43 @@ int occupancy_grid(const void* fn, int block, size_t smem, long long work, int n
     return (int)(g < 1 ? 1 : g);
 }
 
-// Rows of length M = 2^log2m: TR rows per CTA with 256 threads at most.
-bool row_launch(const hufield_plan* p, const void* fn, long long nrows, int& logTR, Launch& L) {
-    const int log2m = p->logM;
-    const int E = row_elems(log2m);
-    long long TR = (256ll * E) >> log2m;
-    if (TR < 1) TR = 1;
-    if (TR > nrows) TR = nrows;
-    logTR = ilog2(TR);
-    L.block = (int)((TR << log2m) / E);
-    L.smem = (size_t)(TR << log2m) * sizeof(float2);
-    L.grid = occupancy_grid(fn, L.block, L.smem, nrows >> logTR, p->nsm);
-    return fn != nullptr && L.grid > 0;
+// Row kernels: the big tile when there are enough rows, else the small one.
+bool row_launch(const hufield_plan* p, const KernelInfo& k, long long nrows, Launch& L) {
+    if (!k.fn) return false;
+    L.block = k.threads;
+    L.smem = k.fixed_smem;
+    L.grid = occupancy_grid(k.fn, L.block, L.smem, nrows >> k.log2_lines, p->nsm);
+    return L.grid > 0;
+}
+KernelInfo pick_row(int log2m, long long nrows, KernelInfo (*table)(int, bool, int), int variant) {
+    const bool big = nrows >= (1ll << row_logtr(log2m, true));
+    return table(log2m, big, variant);
 }
 
-// Columns of a strided axis of length 2^log2l: TB columns per CTA.
-bool col_launch(const hufield_plan* p, const void* fn, int log2l, long long B, long long A, size_t extra_smem,
-                int& logTB, Launch& L) {
-    const int E = col_elems(log2l);
-    const long long tmax = log2l >= 11 ? 512 : 256;
-    long long TB = (tmax * E) >> log2l;
-    if (TB < 1) TB = 1;
-    if (TB > B) TB = B;
-    logTB = ilog2(TB);
-    L.block = (int)((TB << log2l) / E);
-    L.smem = (size_t)(TB << log2l) * sizeof(float2) + extra_smem;
-    L.grid = occupancy_grid(fn, L.block, L.smem, A * (B >> logTB), p->nsm);
-    return fn != nullptr && L.grid > 0;
+// Column kernels: tiles of TB columns x L rows, double-buffered in shared
+// memory; TB >= 2 keeps a TMA box row at 16 bytes or more.
+bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, size_t extra_smem,
+                KernelInfo& k, Launch& L) {
+    const bool big = B >= (1ll << col_logtb(log2l, true));
+    k = cols_kernel(log2l, big, mode, dir);
+    if (!k.fn || B < (1ll << k.log2_lines)) return false;
+    L.block = k.threads;
+    L.smem = k.fixed_smem + extra_smem;
+    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm);
+    return L.grid > 0;
+}
+
+// Tensor map over data viewed as (B, L, A) 8-byte elements with row stride B
+// and batch stride bstride elements; box (TB, min(L, 256), 1).
+bool col_map(const hufield_plan* p, CUtensorMap* map, void* data, long long B, int log2l, long long A,
+             long long bstride, int logTB) {
+    const cuuint64_t dims[3] = {(cuuint64_t)B, (cuuint64_t)1 << log2l, (cuuint64_t)A};
+    const cuuint64_t strides[2] = {(cuuint64_t)B * sizeof(float2), (cuuint64_t)bstride * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)1 << logTB, (cuuint32_t)(log2l < 8 ? 1 << log2l : 256), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return p->encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, data, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaEvent_t pool_event(hufield_plan* p) {
@@ -330,8 +368,12 @@ int make_bins(const hufield_plan* p, int nr, int ntheta, BinParams& bp) {
     return HUFIELD_OK;
 }
 
-// Workspace: [spectrum: max(nlev,1) * N/2 complex64][P: double][raw field bins: nbins doubles]
+// Workspace: [header 256 B: status word][spectrum: max(nlev,1) * N/2 complex64]
+//            [P: double][raw field bins: nbins doubles]
+constexpr size_t kWsHeader = 256;
+
 struct Workspace {
+    unsigned* status;
     float2* spec;
     double* P;
     double* raw;
@@ -339,7 +381,7 @@ struct Workspace {
 
 size_t ws_bytes(const hufield_plan* p, int nlev, int nbins) {
     const size_t spec = align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
-    return spec + align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0)));
+    return kWsHeader + spec + align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0)));
 }
 
 int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Workspace& w) {
@@ -347,8 +389,10 @@ int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Wo
     if (((uintptr_t)ws & 255) != 0) return HUFIELD_ERR_INVALID_ARG;
     if (bytes < ws_bytes(p, nlev, nbins)) return HUFIELD_ERR_WS_TOO_SMALL;
     const size_t spec = align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
-    w.spec = reinterpret_cast<float2*>(ws);
-    w.P = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + spec);
+    char* base = reinterpret_cast<char*>(ws);
+    w.status = reinterpret_cast<unsigned*>(base);
+    w.spec = reinterpret_cast<float2*>(base + kWsHeader);
+    w.P = reinterpret_cast<double*>(base + kWsHeader + spec);
     w.raw = w.P + 1;
     return HUFIELD_OK;
 }
@@ -360,10 +404,30 @@ bool aligned(const void* ptr) { return ((uintptr_t)ptr & 255) == 0; }
         if ((expr) != cudaSuccess) return HUFIELD_ERR_CUDA; \
     } while (0)
 
+// Strided pass along axis 1 (3D) over `nbatch` spectra of N/2 modes each.
+int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind, unsigned* status, cudaStream_t s) {
+    ColArgs ca{};
+    ca.data = data;
+    ca.B = 1ll << p->logM;
+    ca.A = nbatch * p->n[0];
+    ca.bstride = p->n[1] << p->logM;
+    ca.tw = p->tw;
+    ca.status = status;
+    ca.wait_budget = p->wait_budget;
+    ca.inject_skip = p->inject_timeout ? 1 : 0;
+    Launch L;
+    KernelInfo k;
+    if (!col_launch(p, p->log2n[1], kModePlain, dir, ca.B, ca.A, 0, k, L)) return HUFIELD_ERR_CUDA;
+    ca.ntiles = ca.A * (ca.B >> k.log2_lines);
+    if (!col_map(p, &ca.map, data, ca.B, p->log2n[1], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kind, k.fn, L, &ca, s));
+    return HUFIELD_OK;
+}
+
 // r2c rows of the noise (src == kSrcNoise) or of a stored field into w.spec,
 // then the forward FFT along axis 1 for 3D.
 int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed, uint32_t field_idx,
-                         float2* spec, cudaStream_t s) {
+                         float2* spec, unsigned* status, cudaStream_t s) {
     const long long nrows = p->N >> (p->logM + 1);
     RowArgs ra{};
     ra.src = y;
@@ -373,28 +437,20 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
     ra.field_idx = field_idx;
     ra.tw = p->tw;
     Launch L;
-    const void* fn = r2c_kernel(p->logM, src);
-    if (!row_launch(p, fn, nrows, ra.logTR, L)) return HUFIELD_ERR_CUDA;
-    HF_CUDA(launch(p, kPassR2C, fn, L, &ra, s));
-    if (p->ndim == 3) {
-        ColArgs ca{};
-        ca.data = spec;
-        ca.B = 1ll << p->logM;
-        ca.A = p->n[0];
-        ca.bstride = p->n[1] << p->logM;
-        ca.tw = p->tw;
-        const void* cf = cols_kernel(p->log2n[1], kModePlain, -1);
-        if (!col_launch(p, cf, p->log2n[1], ca.B, ca.A, 0, ca.logTB, L)) return HUFIELD_ERR_CUDA;
-        ca.ntiles = ca.A * (ca.B >> ca.logTB);
-        HF_CUDA(launch(p, kPassMidFwd, cf, L, &ca, s));
-    }
+    const KernelInfo k = pick_row(p->logM, nrows, r2c_kernel, src);
+    if (!row_launch(p, k, nrows, L)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassR2C, k.fn, L, &ra, s));
+    if (p->ndim == 3) return mid_pass(p, -1, spec, 1, kPassMidFwd, status, s);
     return HUFIELD_OK;
 }
 
 // Strided pass along axis 0 over `nbatch` spectra of N/2 modes each.
 int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const FilterParams* fp,
-               const BinParams& bp, double* gbins, double* gP, cudaStream_t s) {
+               const BinParams& bp, double* gbins, double* gP, unsigned* status, cudaStream_t s) {
     ColArgs ca{};
+    ca.status = status;
+    ca.wait_budget = p->wait_budget;
+    ca.inject_skip = p->inject_timeout ? 1 : 0;
     ca.data = data;
     ca.B = p->half >> p->log2n[0];
     ca.A = nbatch;
@@ -410,32 +466,19 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     ca.scale = (float)(1.0 / (double)p->N);
     const size_t extra = mode == kModePlain ? 0
                                             : (size_t)(bp.nbins + 1) * (sizeof(double) + sizeof(float)) +
-                                                  (size_t)2 * bp.ntheta * sizeof(long long) +
+                                                  (size_t)2 * (bp.ntheta + 1) * sizeof(long long) +
                                                   (size_t)(bp.nr + 1) * sizeof(int) +
                                                   (mode == kModeFilter ? sizeof(float) << p->log2n[0] : 0);
     Launch L;
-    const void* fn = cols_kernel(p->log2n[0], mode, -1);
-    if (!col_launch(p, fn, p->log2n[0], ca.B, ca.A, extra, ca.logTB, L)) return HUFIELD_ERR_CUDA;
-    ca.ntiles = ca.A * (ca.B >> ca.logTB);
+    KernelInfo k;
+    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, extra, k, L)) return HUFIELD_ERR_CUDA;
+    ca.ntiles = ca.A * (ca.B >> k.log2_lines);
+    if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     const int kind = mode == kModeFilter ? kPassFilter : mode == kModeBins ? kPassBins : kPassMidFwd;
-    HF_CUDA(launch(p, kind, fn, L, &ca, s));
+    HF_CUDA(launch(p, kind, k.fn, L, &ca, s));
     return HUFIELD_OK;
 }
 
-int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind, cudaStream_t s) {
-    ColArgs ca{};
-    ca.data = data;
-    ca.B = 1ll << p->logM;
-    ca.A = nbatch * p->n[0];
-    ca.bstride = p->n[1] << p->logM;
-    ca.tw = p->tw;
-    Launch L;
-    const void* fn = cols_kernel(p->log2n[1], kModePlain, dir);
-    if (!col_launch(p, fn, p->log2n[1], ca.B, ca.A, 0, ca.logTB, L)) return HUFIELD_ERR_CUDA;
-    ca.ntiles = ca.A * (ca.B >> ca.logTB);
-    HF_CUDA(launch(p, kind, fn, L, &ca, s));
-    return HUFIELD_OK;
-}
 
 int bin_counts(hufield_plan* p, const BinParams& bp, long long mult, int ndst, long long** dst,
                cudaStream_t s) {
@@ -449,7 +492,7 @@ int bin_counts(hufield_plan* p, const BinParams& bp, long long mult, int ndst, l
     ca.bp = bp;
     Launch L;
     L.block = 256;
-    L.smem = (size_t)bp.nbins * sizeof(unsigned long long) + (size_t)2 * bp.ntheta * sizeof(long long) +
+    L.smem = (size_t)bp.nbins * sizeof(unsigned long long) + (size_t)2 * (bp.ntheta + 1) * sizeof(long long) +
              (size_t)(bp.nr + 1) * sizeof(int);
     L.grid = occupancy_grid(reinterpret_cast<const void*>(&k_bin_counts), L.block, L.smem,
                             ((p->half >> 3) + L.block - 1) / L.block, p->nsm);
@@ -468,12 +511,12 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     none.ntheta = 1;
     const BinParams& b = bp ? *bp : none;
     HF_CUDA(cudaMemsetAsync(w.P, 0, sizeof(double) * (size_t)(1 + b.nbins), s));
-    int rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, s);
+    int rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
     if (rc) return rc;
-    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, w.raw, w.P, s);
+    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, w.raw, w.P, w.status, s);
     if (rc) return rc;
     if (p->ndim == 3) {
-        rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, s);
+        rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s);
         if (rc) return rc;
     }
     if (bp && sums_f) {
@@ -494,16 +537,19 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     ca.P = w.P;
     ca.sigma_f = f->sigma_f;
     ca.tw = p->tw;
+    ca.status = w.status;
+    ca.wait_budget = p->wait_budget;
+    ca.inject_skip = p->inject_timeout ? 1 : 0;
     Launch L;
-    const void* fn = c2r_kernel(p->logM, out_dtype == HUFIELD_BF16 ? 1 : 0);
-    if (!row_launch(p, fn, ca.nrows, ca.logTR, L)) return HUFIELD_ERR_CUDA;
-    HF_CUDA(launch(p, kPassC2R, fn, L, &ca, s));
+    const KernelInfo k = pick_row(p->logM, ca.nrows, c2r_kernel, out_dtype == HUFIELD_BF16 ? 1 : 0);
+    if (!row_launch(p, k, ca.nrows, L)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassC2R, k.fn, L, &ca, s));
     if (bp && nlev > 0 && sums_m) {
         if (p->ndim == 3) {
-            rc = mid_pass(p, -1, w.spec, nlev, kPassMidMaps, s);
+            rc = mid_pass(p, -1, w.spec, nlev, kPassMidMaps, w.status, s);
             if (rc) return rc;
         }
-        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, sums_m, nullptr, s);
+        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, sums_m, nullptr, w.status, s);
         if (rc) return rc;
     }
     return HUFIELD_OK;
@@ -535,7 +581,8 @@ const char* hufield_status_string(int status) {
 }
 
 int hufield_plan_create(hufield_plan** out, const hufield_dims* dims, uint32_t flags) {
-    if (!out || !dims || (flags & ~HUFIELD_PLAN_PROFILE) != 0) return HUFIELD_ERR_INVALID_ARG;
+    if (!out || !dims || (flags & ~(HUFIELD_PLAN_PROFILE | HUFIELD_PLAN_INJECT_TIMEOUT)) != 0)
+        return HUFIELD_ERR_INVALID_ARG;
     *out = nullptr;
     if (dims->ndim != 2 && dims->ndim != 3) return HUFIELD_ERR_UNSUPPORTED_DIMS;
     long long N = 1;
@@ -548,6 +595,13 @@ int hufield_plan_create(hufield_plan** out, const hufield_dims* dims, uint32_t f
     hufield_plan* p = new (std::nothrow) hufield_plan();
     if (!p) return HUFIELD_ERR_CUDA;
     p->profile = (flags & HUFIELD_PLAN_PROFILE) != 0;
+    p->inject_timeout = (flags & HUFIELD_PLAN_INJECT_TIMEOUT) != 0;
+    p->wait_budget = p->inject_timeout ? kInjectWaitBudget : kWaitBudget;
+    p->encode = encode_entry();
+    if (!p->encode) {
+        delete p;
+        return HUFIELD_ERR_CUDA;
+    }
     p->ndim = dims->ndim;
     for (int d = 0; d < 3; ++d) {
         p->n[d] = d < dims->ndim ? dims->n[d] : 1;
@@ -610,11 +664,12 @@ int hufield_forward(hufield_plan* p, uint64_t seed, uint32_t field_idx, void* ws
     int rc = carve(p, ws, bytes, 0, 0, w);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, s);
+    HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), s));
+    rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
     if (rc) return rc;
     BinParams none{};
     none.ntheta = 1;
-    return axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, s);
+    return axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, w.status, s);
 }
 
 int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx,
@@ -627,6 +682,7 @@ int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     Workspace w;
     rc = carve(p, ws, bytes, 0, 0, w);
     if (rc) return rc;
+    HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), (cudaStream_t)stream));
     return run_field(p, f, seed, field_idx, out_dtype, out_f, nullptr, 0, nullptr, nullptr, nullptr, nullptr, w,
                      (cudaStream_t)stream);
 }
@@ -662,6 +718,7 @@ int hufield_spectrum(hufield_plan* p, const void* y, int32_t dtype, int32_t nr, 
     Workspace w;
     rc = carve(p, ws, bytes, 1, bp.nbins, w);
     if (rc) return rc;
+    HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), (cudaStream_t)stream));
     cudaStream_t s = (cudaStream_t)stream;
     if (!accumulate) {
         HF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * bp.nbins, s));
@@ -671,9 +728,9 @@ int hufield_spectrum(hufield_plan* p, const void* y, int32_t dtype, int32_t nr, 
     rc = bin_counts(p, bp, 1, 1, dst, s);
     if (rc) return rc;
     const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
-    rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, s);
+    rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, w.status, s);
     if (rc) return rc;
-    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, sums, nullptr, s);
+    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, sums, nullptr, w.status, s);
 }
 
 int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field0, int32_t nfields,
@@ -695,6 +752,7 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     Workspace w;
     rc = carve(p, ws, bytes, nlev, bp.nbins, w);
     if (rc) return rc;
+    HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), (cudaStream_t)stream));
     cudaStream_t s = (cudaStream_t)stream;
     if (!accumulate) {
         HF_CUDA(cudaMemsetAsync(sums_f, 0, sizeof(double) * bp.nbins, s));
@@ -747,6 +805,15 @@ int hufield_profile_read(hufield_plan* p, double* ms, int64_t* launches, int32_t
 
 const char* hufield_profile_names(void) { return kPassNames; }
 
+int hufield_workspace_status(const void* ws, void* stream) {
+    if (!ws || ((uintptr_t)ws & 255) != 0) return HUFIELD_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned word = 0;
+    HF_CUDA(cudaMemcpyAsync(&word, ws, sizeof(word), cudaMemcpyDeviceToHost, s));
+    HF_CUDA(cudaStreamSynchronize(s));
+    return (word & kStatusTimeout) ? HUFIELD_ERR_TIMEOUT : HUFIELD_OK;
+}
+
 int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, double* out, void* stream) {
     if (!sums || !counts || !out || nbins < 1) return HUFIELD_ERR_INVALID_ARG;
     k_bins_mean<<<(nbins + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
@@ -768,12 +835,15 @@ namespace {
 constexpr long long kStaticMaxVoxels = 1ll << 20;  // half spectrum: 2^19 complex64 = 4 MiB
 static __device__ __align__(256) float2 g_static_spec[kStaticMaxVoxels / 2];
 static __device__ __align__(256) float2 g_static_tw[kTwN];
+static __device__ __align__(256) unsigned g_static_status[64];
 
 struct StaticScratch {
     bool ready = false;
     float2* spec = nullptr;
     float2* tw = nullptr;
+    unsigned* status = nullptr;
     int nsm = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
 };
 constexpr int kMaxDevices = 64;
 StaticScratch g_static[kMaxDevices];
@@ -787,15 +857,21 @@ int static_setup(int dev, cudaStream_t s, StaticScratch& out) {
     if (!st.ready) {
         void* spec = nullptr;
         void* tw = nullptr;
+        void* status = nullptr;
         if (cudaGetSymbolAddress(&spec, g_static_spec) != cudaSuccess) return HUFIELD_ERR_CUDA;
         if (cudaGetSymbolAddress(&tw, g_static_tw) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        if (cudaGetSymbolAddress(&status, g_static_status) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        PFN_cuTensorMapEncodeTiled_v12000 enc = encode_entry();
+        if (!enc) return HUFIELD_ERR_CUDA;
         int nsm = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HUFIELD_ERR_CUDA;
         k_twiddles<<<kTwN / 256, 256, 0, s>>>(reinterpret_cast<float2*>(tw));
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return HUFIELD_ERR_CUDA;
         st.spec = reinterpret_cast<float2*>(spec);
         st.tw = reinterpret_cast<float2*>(tw);
+        st.status = reinterpret_cast<unsigned*>(status);
         st.nsm = nsm;
+        st.encode = enc;
         st.ready = true;
     }
     out = st;
@@ -837,6 +913,9 @@ extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y,
     if (rc) return rc;
     p.nsm = st.nsm;
     p.tw = st.tw;
+    p.encode = st.encode;
+    p.wait_budget = kWaitBudget;
+    HF_CUDA(cudaMemsetAsync(st.status, 0, sizeof(unsigned), s));
     if (!accumulate) {
         HF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * bp.nbins, s));
         HF_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * bp.nbins, s));
@@ -845,7 +924,7 @@ extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y,
     rc = bin_counts(&p, bp, 1, 1, dst, s);
     if (rc) return rc;
     const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
-    rc = forward_rows_and_mid(&p, src, y, 0, 0, st.spec, s);
+    rc = forward_rows_and_mid(&p, src, y, 0, 0, st.spec, st.status, s);
     if (rc) return rc;
-    return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, sums, nullptr, s);
+    return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, sums, nullptr, st.status, s);
 }

@@ -1,29 +1,51 @@
-// Instantiations of the row c2r (normalise, threshold, map r2c) kernel.
-#include "kernels.cuh"
-#include "launch.h"
+// Row c2r kernels (normalise, sign maps, map r2c).
+#include "instantiate.cuh"
 
 namespace hf {
 
-template <int LOG2M>
-static const void* c2r_for(int out_dtype) {
-    return out_dtype == 0 ? reinterpret_cast<const void*>(&k_c2r<LOG2M, 0>)
-                          : reinterpret_cast<const void*>(&k_c2r<LOG2M, 1>);
-}
-
-const void* c2r_kernel(int log2m, int out_dtype) {
-    if (out_dtype != 0 && out_dtype != 1) return nullptr;
+KernelInfo c2r_kernel(int log2m, bool big, int out_dtype) {
     switch (log2m) {
-        case 2: return c2r_for<2>(out_dtype);
-        case 3: return c2r_for<3>(out_dtype);
-        case 4: return c2r_for<4>(out_dtype);
-        case 5: return c2r_for<5>(out_dtype);
-        case 6: return c2r_for<6>(out_dtype);
-        case 7: return c2r_for<7>(out_dtype);
-        case 8: return c2r_for<8>(out_dtype);
-        case 9: return c2r_for<9>(out_dtype);
-        case 10: return c2r_for<10>(out_dtype);
-        case 11: return c2r_for<11>(out_dtype);
-        default: return nullptr;
+        case 2:
+            if (out_dtype == 0) return big ? c2r_info<2, 8, 0>() : c2r_info<2, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<2, 8, 1>() : c2r_info<2, 0, 1>();
+            return {};
+        case 3:
+            if (out_dtype == 0) return big ? c2r_info<3, 8, 0>() : c2r_info<3, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<3, 8, 1>() : c2r_info<3, 0, 1>();
+            return {};
+        case 4:
+            if (out_dtype == 0) return big ? c2r_info<4, 8, 0>() : c2r_info<4, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<4, 8, 1>() : c2r_info<4, 0, 1>();
+            return {};
+        case 5:
+            if (out_dtype == 0) return big ? c2r_info<5, 7, 0>() : c2r_info<5, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<5, 7, 1>() : c2r_info<5, 0, 1>();
+            return {};
+        case 6:
+            if (out_dtype == 0) return big ? c2r_info<6, 6, 0>() : c2r_info<6, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<6, 6, 1>() : c2r_info<6, 0, 1>();
+            return {};
+        case 7:
+            if (out_dtype == 0) return big ? c2r_info<7, 5, 0>() : c2r_info<7, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<7, 5, 1>() : c2r_info<7, 0, 1>();
+            return {};
+        case 8:
+            if (out_dtype == 0) return big ? c2r_info<8, 4, 0>() : c2r_info<8, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<8, 4, 1>() : c2r_info<8, 0, 1>();
+            return {};
+        case 9:
+            if (out_dtype == 0) return big ? c2r_info<9, 3, 0>() : c2r_info<9, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<9, 3, 1>() : c2r_info<9, 0, 1>();
+            return {};
+        case 10:
+            if (out_dtype == 0) return big ? c2r_info<10, 2, 0>() : c2r_info<10, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<10, 2, 1>() : c2r_info<10, 0, 1>();
+            return {};
+        case 11:
+            if (out_dtype == 0) return big ? c2r_info<11, 1, 0>() : c2r_info<11, 0, 0>();
+            if (out_dtype == 1) return big ? c2r_info<11, 1, 1>() : c2r_info<11, 0, 1>();
+            return {};
+        default: return {};
     }
 }
 

@@ -1,30 +1,51 @@
-// Instantiations of the strided-axis kernel (plain modes).
-#include "kernels.cuh"
-#include "launch.h"
+// Strided-axis FFT kernels (forward and inverse).
+#include "instantiate.cuh"
 
 namespace hf {
 
-template <int LOG2L>
-static const void* pick(int mode, int dir) {
-    (void)dir;
-    if (mode == kModePlain) return dir < 0 ? reinterpret_cast<const void*>(&k_cols<LOG2L, kModePlain, -1>)
-                                           : reinterpret_cast<const void*>(&k_cols<LOG2L, kModePlain, +1>);
-    return nullptr;
-}
-
-const void* cols_plain_kernel(int log2l, int mode, int dir) {
+KernelInfo cols_kernel_plain(int log2l, bool big, int mode, int dir) {
     switch (log2l) {
-        case 3: return pick<3>(mode, dir);
-        case 4: return pick<4>(mode, dir);
-        case 5: return pick<5>(mode, dir);
-        case 6: return pick<6>(mode, dir);
-        case 7: return pick<7>(mode, dir);
-        case 8: return pick<8>(mode, dir);
-        case 9: return pick<9>(mode, dir);
-        case 10: return pick<10>(mode, dir);
-        case 11: return pick<11>(mode, dir);
-        case 12: return pick<12>(mode, dir);
-        default: return nullptr;
+        case 3:
+            if (mode == 0 && dir == -1) return big ? cols_info<3, 8, 0, -1>() : cols_info<3, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<3, 8, 0, 1>() : cols_info<3, 1, 0, 1>();
+            return {};
+        case 4:
+            if (mode == 0 && dir == -1) return big ? cols_info<4, 8, 0, -1>() : cols_info<4, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<4, 8, 0, 1>() : cols_info<4, 1, 0, 1>();
+            return {};
+        case 5:
+            if (mode == 0 && dir == -1) return big ? cols_info<5, 7, 0, -1>() : cols_info<5, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<5, 7, 0, 1>() : cols_info<5, 1, 0, 1>();
+            return {};
+        case 6:
+            if (mode == 0 && dir == -1) return big ? cols_info<6, 6, 0, -1>() : cols_info<6, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<6, 6, 0, 1>() : cols_info<6, 1, 0, 1>();
+            return {};
+        case 7:
+            if (mode == 0 && dir == -1) return big ? cols_info<7, 5, 0, -1>() : cols_info<7, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<7, 5, 0, 1>() : cols_info<7, 1, 0, 1>();
+            return {};
+        case 8:
+            if (mode == 0 && dir == -1) return big ? cols_info<8, 4, 0, -1>() : cols_info<8, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<8, 4, 0, 1>() : cols_info<8, 1, 0, 1>();
+            return {};
+        case 9:
+            if (mode == 0 && dir == -1) return big ? cols_info<9, 3, 0, -1>() : cols_info<9, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<9, 3, 0, 1>() : cols_info<9, 1, 0, 1>();
+            return {};
+        case 10:
+            if (mode == 0 && dir == -1) return big ? cols_info<10, 2, 0, -1>() : cols_info<10, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<10, 2, 0, 1>() : cols_info<10, 1, 0, 1>();
+            return {};
+        case 11:
+            if (mode == 0 && dir == -1) return big ? cols_info<11, 2, 0, -1>() : cols_info<11, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<11, 2, 0, 1>() : cols_info<11, 1, 0, 1>();
+            return {};
+        case 12:
+            if (mode == 0 && dir == -1) return big ? cols_info<12, 1, 0, -1>() : cols_info<12, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<12, 1, 0, 1>() : cols_info<12, 1, 0, 1>();
+            return {};
+        default: return {};
     }
 }
 

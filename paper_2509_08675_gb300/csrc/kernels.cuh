@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace hf {
 
@@ -30,16 +31,14 @@ struct RowArgs {
     const void* src;        // real input rows (kSrcF32/BF16/I8)
     float2* out;            // [nrows][M] half spectrum
     long long nrows;
-    int logTR;              // rows per CTA
     unsigned long long seed;
     unsigned int field_idx;
-    const float2* tw;
+    const float2* tw;       // plan twiddles (4096)
 };
 
 struct C2RArgs {
     float2* spec;           // [nrows][M] filtered spectrum in; map spectra out (level t at spec + t * half)
     long long nrows;
-    int logTR;
     long long half;         // N / 2
     long long N;
     void* out_f;            // field (F32 or BF16), may be null
@@ -49,14 +48,17 @@ struct C2RArgs {
     const double* P;        // sum over the full lattice of |G|^2
     float sigma_f;
     const float2* tw;
+    unsigned* status;       // workspace status word (kStatusTimeout)
+    long long wait_budget;  // clock cycles allowed per mbarrier wait
+    int inject_skip;        // test hook: 1 = the first tile's load is never issued
 };
 
 struct ColArgs {
+    CUtensorMap map;        // (B, L, A) of 8-byte elements, box (TB, min(L, 256), 1); loads and stores
     float2* data;           // element (a, l, c) at data[a * bstride + l * B + c]
     long long B;            // contiguous columns
     long long A;            // batches
     long long bstride;
-    int logTB;              // columns per CTA
     long long ntiles;       // A * B / TB
     const float2* tw;
     // mode decoding for the pass along axis 0 (FILTER, BINS)
@@ -68,7 +70,15 @@ struct ColArgs {
     double* gbins;          // FILTER: raw field bins [nbins]; BINS: [A][nbins]
     double* gP;             // FILTER: Parseval sum
     float scale;            // BINS: 1 / N
+    unsigned* status;       // workspace status word (kStatusTimeout)
+    long long wait_budget;  // clock cycles allowed per mbarrier wait
+    int inject_skip;        // test hook: 1 = the first tile's load is never issued (its wait must time out)
 };
+
+// Minimum resident CTAs per SM asked of the compiler: keeps the kernels of
+// 128 threads or more at 128 registers per thread or fewer (65536 / (128 T)
+// CTAs of T threads); the small tiles of tiny lattices are left unbounded.
+constexpr int min_blocks(int T) { return T >= 512 ? 1 : (T >= 128 ? 512 / T : 1); }
 
 __device__ __forceinline__ int signed_index(int i, int log2n) {
     return i < (1 << (log2n - 1)) ? i : i - (1 << log2n);
@@ -97,13 +107,29 @@ __device__ __forceinline__ float filter_amplitude(const FilterParams& fp, float 
     return amplitude_from_sum(fp, S);
 }
 
-// Exact angular sector of a folded, nonzero vector (a1 > 0, or a1 = 0 < a0):
-// the largest j with cross(d_j, a) >= 0, d_j the rounded edge directions.
-__device__ __forceinline__ int sector_exact(const long long* ang, int ntheta, long long a0, long long a1) {
+// ---------------------------------------------------------------------------
+// Binning.  Radial: Q = |kappa|^2 nmax^2 = 4 sum (n_i nmax / n_i)^2 is an
+// integer below 2^26 and bin b holds b^2 nmax^2 <= nr^2 Q < (b+1)^2 nmax^2,
+// i.e. thr[b] <= Q < thr[b+1] with the integer thresholds thr[b] =
+// ceil(b^2 nmax^2 / nr^2) (thr[nr] = nmax^2: beyond it |kappa| >= 1, dropped).
+// Angular (2D): the folded vector's sector is the largest j with
+// cross(d_j, a) >= 0 for the edge directions d_j = round(2^30 (cos, sin)
+// (j pi / ntheta)), j = 0..ntheta, d_ntheta = (-2^30, 0).
+// ---------------------------------------------------------------------------
+// Angle table in shared memory: C_j at ang[j], S_j at ang[ntheta + 1 + j].
+__device__ __forceinline__ long long ang_c(const long long* ang, int j) { return ang[j]; }
+__device__ __forceinline__ long long ang_s(const long long* ang, int nt, int j) { return ang[nt + 1 + j]; }
+
+__device__ __forceinline__ long long cross_edge(const long long* ang, int nt, int j, int a0, int a1) {
+    return ang_c(ang, j) * (long long)a1 - ang_s(ang, nt, j) * (long long)a0;
+}
+
+// Exact sector of a folded, nonzero vector by bisection.
+__device__ __forceinline__ int sector_exact(const long long* ang, int ntheta, int a0, int a1) {
     int lo = 0, hi = ntheta - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (ang[mid] * a1 - ang[ntheta + mid] * a0 >= 0)
+        if (cross_edge(ang, ntheta, mid, a0, a1) >= 0)
             lo = mid;
         else
             hi = mid - 1;
@@ -111,44 +137,94 @@ __device__ __forceinline__ int sector_exact(const long long* ang, int ntheta, lo
     return lo;
 }
 
-// Bin of a mode (signed indices), -1 when |kappa| >= 1.
-// Radial: Q = |kappa|^2 nmax^2 = 4 sum (n_i nmax / n_i)^2 is an integer below
-// 2^26, and bin b holds b^2 nmax^2 <= nr^2 Q < (b+1)^2 nmax^2, i.e.
-// thr[b] <= Q < thr[b+1] with the integer thresholds thr[b] =
-// ceil(b^2 nmax^2 / nr^2) (thr[nr] = nmax^2); a float square root gives the
-// first guess and integer compares settle it.  Angular (2D): the folded angle
-// from atan2f gives the sector unless it lies within 1e-4 of a sector edge,
-// where the exact 64-bit cross products against the rounded edge directions
-// decide.
+__device__ __forceinline__ void fold_vector(int& a0, int& a1) {
+    if (a1 < 0 || (a1 == 0 && a0 < 0)) {
+        a0 = -a0;
+        a1 = -a1;
+    }
+}
+
+// Radial bin (or nr when outside) from scratch: a float square root gives the
+// first guess and integer compares settle it.
+__device__ __forceinline__ int radial_from_scratch(const BinParams& bp, const int* thr, int Q) {
+    if (Q >= thr[bp.nr]) return bp.nr;
+    int b = (int)(sqrtf((float)Q) * __int_as_float((127 - bp.log2nmax) << 23) * (float)bp.nr);
+    b = b < bp.nr - 1 ? b : bp.nr - 1;
+    while (b > 0 && Q < thr[b]) --b;
+    while (Q >= thr[b + 1]) ++b;
+    return b;
+}
+
+// Sector from scratch: the folded angle from atan2f gives it unless it lies
+// within 1e-4 of an edge, where the exact bisection decides.
+__device__ __forceinline__ int sector_from_scratch(const BinParams& bp, const long long* ang, int a0, int a1) {
+    if (a0 == 0 && a1 == 0) return 0;
+    const float t = atan2f((float)a1, (float)a0) * ((float)bp.ntheta * 0.318309886183790672f);
+    int s = (int)t;
+    const float frac = t - (float)s;
+    if (frac < 1e-4f || frac > 1.0f - 1e-4f || s >= bp.ntheta) s = sector_exact(ang, bp.ntheta, a0, a1);
+    return s;
+}
+
+// Bin of one mode (signed indices), -1 when |kappa| >= 1.
 __device__ __forceinline__ int bin_index(const BinParams& bp, const int* thr, const long long* ang, int n0, int n1,
                                          int n2, int ndim) {
     const int v0 = n0 << bp.shift[0];
     const int v1 = n1 << bp.shift[1];
     const int v2 = ndim == 3 ? (n2 << bp.shift[2]) : 0;
     const int Q = 4 * (v0 * v0 + v1 * v1 + v2 * v2);
-    if (Q >= thr[bp.nr]) return -1;
-    int b = (int)(sqrtf((float)Q) * __int_as_float((127 - bp.log2nmax) << 23) * (float)bp.nr);
-    b = b < bp.nr - 1 ? b : bp.nr - 1;
-    while (b > 0 && Q < thr[b]) --b;
-    while (Q >= thr[b + 1]) ++b;
-    int sector = 0;
-    if (bp.ntheta > 1) {
-        int a0 = v0, a1 = v1;
-        if (a1 < 0 || (a1 == 0 && a0 < 0)) {
-            a0 = -a0;
-            a1 = -a1;
-        }
-        if (a0 != 0 || a1 != 0) {
-            const float t = atan2f((float)a1, (float)a0) * ((float)bp.ntheta * 0.318309886183790672f);
-            int s = (int)t;
-            const float frac = t - (float)s;
-            if (frac < 1e-4f || frac > 1.0f - 1e-4f || s >= bp.ntheta) {
-                s = sector_exact(ang, bp.ntheta, a0, a1);
-            }
-            sector = s;
-        }
+    const int rb = radial_from_scratch(bp, thr, Q);
+    if (rb >= bp.nr) return -1;
+    if (bp.ntheta == 1) return rb;
+    int a0 = v0, a1 = v1;
+    fold_vector(a0, a1);
+    return rb * bp.ntheta + sector_from_scratch(bp, ang, a0, a1);
+}
+
+// Bins of a run of modes: the radial bin and the sector of the previous
+// mode are stepped to the current one with exact integer compares (the
+// thresholds and the edge cross products), which is cheap because
+// neighbouring modes lie in the same or a neighbouring bin.
+struct BinRun {
+    int rb = -1;  // radial bin (nr = outside); -1: none yet
+    int sec = 0;
+};
+
+__device__ __forceinline__ int bin_index_run(const BinParams& bp, const int* thr, const long long* ang, int n0, int n1,
+                                             int n2, int ndim, BinRun& st) {
+    const int v0 = n0 << bp.shift[0];
+    const int v1 = n1 << bp.shift[1];
+    const int v2 = ndim == 3 ? (n2 << bp.shift[2]) : 0;
+    const int Q = 4 * (v0 * v0 + v1 * v1 + v2 * v2);
+    int b = st.rb;
+    if (b < 0) {
+        b = radial_from_scratch(bp, thr, Q);
+    } else {
+        while (b < bp.nr && Q >= thr[b + 1]) ++b;
+        while (b > 0 && Q < thr[b]) --b;
     }
-    return b * bp.ntheta + sector;
+    st.rb = b;
+    if (b >= bp.nr) return -1;
+    if (bp.ntheta == 1) return b;
+    int a0 = v0, a1 = v1;
+    fold_vector(a0, a1);
+    int s = st.sec;
+    if (a0 == 0 && a1 == 0) {
+        s = 0;
+    } else {
+        while (s + 1 < bp.ntheta && cross_edge(ang, bp.ntheta, s + 1, a0, a1) >= 0) ++s;
+        while (s > 0 && cross_edge(ang, bp.ntheta, s, a0, a1) < 0) --s;
+    }
+    st.sec = s;
+    return b * bp.ntheta + s;
+}
+
+// Angle table (ntheta + 1 edges) from the parameter block into shared memory.
+__device__ __forceinline__ void fill_angles(const BinParams& bp, long long* ang, int t, int T) {
+    for (int i = t; i <= bp.ntheta; i += T) {
+        ang[i] = i < bp.ntheta ? bp.ang_c[i] : -(1ll << 30);
+        ang[bp.ntheta + 1 + i] = i < bp.ntheta ? bp.ang_s[i] : 0ll;
+    }
 }
 
 // Integer radial thresholds thr[b] = ceil(b^2 nmax^2 / nr^2), b = 0..nr.
@@ -167,34 +243,46 @@ __device__ __forceinline__ void chunk_of(long long ntiles, long long& t0, long l
     t1 = ntiles * ((long long)blockIdx.x + 1) / G;
 }
 
-// r2c post-processing of one row held in shared memory: from Z = DFT_M of
-// z[j] = x[2j] + i x[2j+1], X[k] = (Z[k] + Z*[M-k])/2 - i W_N^k (Z[k] - Z*[M-k])/2.
-template <int LOG2M>
-__device__ __forceinline__ float2 r2c_post(float2 Z, float2 Zm_conj, const float2* __restrict__ tw, int k) {
+// One elected thread polls the mbarrier (bounded); the CTA then agrees.
+// Returns false (for every thread) when the wait ran out.
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, long long budget) {
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait_bounded(bar, parity, budget);
+    return !__syncthreads_or(!ok);
+}
+
+// r2c post-processing: from Z = DFT_M of z[j] = x[2j] + i x[2j+1],
+// X[k] = (Z[k] + Z*[M-k])/2 - i W_N^k (Z[k] - Z*[M-k])/2, with W_N^k = tw[k]
+// in the CTA's table of length N = 2M.
+__device__ __forceinline__ float2 r2c_post(float2 Z, float2 Zm_conj, float2 w) {
     const float2 ev = cscale(cadd(Z, Zm_conj), 0.5f);
     const float2 od = cscale(cmul_i<-1>(csub(Z, Zm_conj)), 0.5f);
-    const float2 w = __ldg(tw + (k << (kTwLog2 - LOG2M - 1)));
     return cadd(ev, cmul(od, w));
 }
 
 // ---------------------------------------------------------------------------
 // Rows: real input -> half spectrum.
 // ---------------------------------------------------------------------------
-template <int LOG2M, int SRC>
-__global__ void __launch_bounds__(256) k_r2c(const __grid_constant__ RowArgs a) {
-    constexpr int M = 1 << LOG2M;
-    constexpr int E = RowShape<LOG2M>::E;
+template <int LOG2M, int LOGTR, int SRC>
+__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blocks(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T))
+    k_r2c(const __grid_constant__ RowArgs a) {
+    using G = Geo<LOG2M, LOGTR, true, LOG2M + 1>;
+    constexpr int M = G::L;
+    constexpr int E = G::E;
     using PF = Plan<LOG2M, false>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sm = reinterpret_cast<float2*>(smem_raw);
-    const Ctx c{(int)threadIdx.x, (int)blockDim.x, a.logTR};
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);  // TR * M exchange
+    float2* tw = sm + G::TB * M;                        // 2M twiddles
+    const int t = threadIdx.x;
+    load_twiddles<G>(tw, a.tw, t);
     long long t0, t1;
-    chunk_of(a.nrows >> a.logTR, t0, t1);
-    const int nq = (1 << (a.logTR + LOG2M)) >> 1;  // blocks of four reals per tile
+    chunk_of(a.nrows >> LOGTR, t0, t1);
+    constexpr int nq = (G::TB * M) / 2;  // blocks of four reals per tile
     for (long long tile = t0; tile < t1; ++tile) {
-        const long long row0 = tile << a.logTR;
-        __syncthreads();  // previous tile is done with shared memory
-        for (int q = c.t; q < nq; q += c.T) {
+        const long long row0 = tile << LOGTR;
+        __syncthreads();  // previous tile is done with shared memory (and the twiddles are loaded)
+#pragma unroll
+        for (int q = t; q < nq; q += G::T) {
             const long long gq = row0 * (M / 2) + q;  // global block index
             float4 x;
             if constexpr (SRC == kSrcNoise) {
@@ -212,48 +300,79 @@ __global__ void __launch_bounds__(256) k_r2c(const __grid_constant__ RowArgs a) 
             }
             const int e2 = 2 * q;
             const int b = e2 >> LOG2M, j = e2 & (M - 1);
-            sm[smem_slot<LOG2M, true>(c, j, b)] = make_float2(x.x, x.y);
-            sm[smem_slot<LOG2M, true>(c, j + 1, b)] = make_float2(x.z, x.w);
+            sm[smem_slot<G>(j, b)] = make_float2(x.x, x.y);
+            sm[smem_slot<G>(j + 1, b)] = make_float2(x.z, x.w);
         }
         __syncthreads();
         float2 v[E];
-        for_each_element<LOG2M, true, PF::first_radix(), E>(
-            c, [&](int e, int b, int l) { v[e] = sm[smem_slot<LOG2M, true>(c, l, b)]; });
-        fft<LOG2M, E, -1, false, true>(v, sm, a.tw, c);
+        for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int l) { v[e] = sm[smem_slot<G>(l, b)]; });
+        fft<G, -1, false>(v, sm, tw, t);
         __syncthreads();
-        for_each_element<LOG2M, true, PF::last_radix(), E>(
-            c, [&](int e, int b, int l) { sm[smem_slot<LOG2M, true>(c, l, b)] = v[e]; });
+        for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { sm[smem_slot<G>(l, b)] = v[e]; });
         __syncthreads();
-        for_each_element<LOG2M, true, PF::last_radix(), E>(c, [&](int e, int b, int k) {
-            const float2 zc = cconj(sm[smem_slot<LOG2M, true>(c, (M - k) & (M - 1), b)]);
-            a.out[(row0 + b) * M + k] = r2c_post<LOG2M>(v[e], zc, a.tw, k);
+        for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int k) {
+            const float2 zc = cconj(sm[smem_slot<G>((M - k) & (M - 1), b)]);
+            a.out[(row0 + b) * M + k] = r2c_post(v[e], zc, tw[k]);
         });
     }
 }
 
 // ---------------------------------------------------------------------------
 // Rows: filtered half spectrum -> field (Eq. 15) -> sign maps -> map spectra.
+// Row tiles (TR contiguous rows) arrive by 1D bulk copies into two
+// shared-memory buffers, the next tile in flight while the current one is
+// transformed; the current buffer then serves as the FFT exchange area.
 // ---------------------------------------------------------------------------
-template <int LOG2M, int OUTDT>
-__global__ void __launch_bounds__(256) k_c2r(const __grid_constant__ C2RArgs a) {
-    constexpr int M = 1 << LOG2M;
-    constexpr int E = RowShape<LOG2M>::E;
+template <int LOG2M, int LOGTR, int OUTDT>
+__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blocks(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T))
+    k_c2r(const __grid_constant__ C2RArgs a) {
+    using G = Geo<LOG2M, LOGTR, true, LOG2M + 1>;
+    constexpr int M = G::L;
+    constexpr int E = G::E;
     using PF = Plan<LOG2M, false>;
     using PI = Plan<LOG2M, true>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sm = reinterpret_cast<float2*>(smem_raw);
-    const Ctx c{(int)threadIdx.x, (int)blockDim.x, a.logTR};
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int tile_elems = G::TB * M;
+    float2* bufs[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw) + tile_elems};
+    float2* tw = bufs[1] + tile_elems;  // 2M twiddles
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + 2 * M);
+    constexpr uint32_t tile_bytes = (uint32_t)tile_elems * (uint32_t)sizeof(float2);
+    const int t = threadIdx.x;
     // f = sigma_f * u / sqrt(sum |G|^2), u the unnormalised inverse (the mean
     // is zero because A(0) = 0): Var = sum|G|^2 / N^2 by Parseval.
     const float scale = (float)((double)a.sigma_f / sqrt(*a.P));
     long long t0, t1;
-    chunk_of(a.nrows >> a.logTR, t0, t1);
+    chunk_of(a.nrows >> LOGTR, t0, t1);
+    auto issue = [&](long long tile, float2* dst, uint64_t* b) {
+        mbar_arrive_expect_tx(b, tile_bytes);
+        bulk_load(dst, a.spec + tile * tile_elems, tile_bytes, b);
+    };
+    load_twiddles<G>(tw, a.tw, t);
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (t0 < t1 && !a.inject_skip) issue(t0, bufs[0], &bar[0]);
+        if (t0 + 1 < t1) issue(t0 + 1, bufs[1], &bar[1]);
+    }
+    uint32_t phase[2] = {0u, 0u};
+    long long failed_at = -1;
     for (long long tile = t0; tile < t1; ++tile) {
-        const long long row0 = tile << a.logTR;
+        const int s = (int)((tile - t0) & 1);
+        float2* buf = bufs[s];
+        if (!cta_wait(&bar[s], phase[s], a.wait_budget)) {
+            failed_at = tile;
+            break;
+        }
+        phase[s] ^= 1u;
+        const long long row0 = tile << LOGTR;
         float2 v[E];
         // c2r pre-processing: Z[k] = (X[k] + X*[M-k]) + i (X[k] - X*[M-k]) W_N^{-k}
-        for_each_element<LOG2M, true, PI::first_radix(), E>(c, [&](int e, int b, int k) {
-            const float2* rowp = a.spec + (row0 + b) * M;
+        for_each_element<G, PI::first_radix()>(t, [&](int e, int b, int k) {
+            const float2* rowp = buf + (b << LOG2M);
             float2 X = rowp[k];
             float2 Xmc = make_float2(0.0f, 0.0f);
             if (k == 0) {
@@ -262,16 +381,15 @@ __global__ void __launch_bounds__(256) k_c2r(const __grid_constant__ C2RArgs a) 
                 Xmc = cconj(rowp[M - k]);
             }
             const float2 ep = cadd(X, Xmc);
-            const float2 w = __ldg(a.tw + (k << (kTwLog2 - LOG2M - 1)));
-            const float2 op = cmulc(csub(X, Xmc), w);
+            const float2 op = cmulc(csub(X, Xmc), tw[k]);
             v[e] = cadd(ep, cmul_i<+1>(op));
         });
-        fft<LOG2M, E, +1, true, true>(v, sm, a.tw, c);
+        fft<G, +1, true>(v, buf, tw, t);
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = cscale(v[e], scale);
         // v[e] now holds f[2j], f[2j+1] of row b at the forward plan's input positions
         if (a.out_f != nullptr) {
-            for_each_element<LOG2M, true, PF::first_radix(), E>(c, [&](int e, int b, int j) {
+            for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
                 const long long off = (row0 + b) * M + j;  // in pairs of reals
                 if constexpr (OUTDT == 0) {
                     reinterpret_cast<float2*>(a.out_f)[off] = v[e];
@@ -281,123 +399,178 @@ __global__ void __launch_bounds__(256) k_c2r(const __grid_constant__ C2RArgs a) 
             });
         }
         for (int lev = 0; lev < a.nlev; ++lev) {
-            const float t = a.levels[lev];
+            const float th = a.levels[lev];
             float2 u[E];
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                u[e] = make_float2(v[e].x >= t ? 1.0f : -1.0f, v[e].y >= t ? 1.0f : -1.0f);
+                u[e] = make_float2(v[e].x >= th ? 1.0f : -1.0f, v[e].y >= th ? 1.0f : -1.0f);
             if (a.out_maps != nullptr) {
-                for_each_element<LOG2M, true, PF::first_radix(), E>(c, [&](int e, int b, int j) {
+                for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
                     char2 m;
                     m.x = u[e].x > 0.0f ? (signed char)1 : (signed char)-1;
                     m.y = u[e].y > 0.0f ? (signed char)1 : (signed char)-1;
                     reinterpret_cast<char2*>(a.out_maps + (long long)lev * a.N)[(row0 + b) * M + j] = m;
                 });
             }
-            fft<LOG2M, E, -1, false, true>(u, sm, a.tw, c);
+            fft<G, -1, false>(u, buf, tw, t);
             __syncthreads();
-            for_each_element<LOG2M, true, PF::last_radix(), E>(
-                c, [&](int e, int b, int l) { sm[smem_slot<LOG2M, true>(c, l, b)] = u[e]; });
+            for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { buf[smem_slot<G>(l, b)] = u[e]; });
             __syncthreads();
             float2* dst = a.spec + (long long)lev * a.half;
-            for_each_element<LOG2M, true, PF::last_radix(), E>(c, [&](int e, int b, int k) {
-                const float2 zc = cconj(sm[smem_slot<LOG2M, true>(c, (M - k) & (M - 1), b)]);
-                dst[(row0 + b) * M + k] = r2c_post<LOG2M>(u[e], zc, a.tw, k);
+            for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int k) {
+                const float2 zc = cconj(buf[smem_slot<G>((M - k) & (M - 1), b)]);
+                dst[(row0 + b) * M + k] = r2c_post(u[e], zc, tw[k]);
             });
         }
+        // buf is free once every thread is past its last read: refill it with tile + 2
+        fence_proxy_async_smem();
         __syncthreads();
+        if (t == 0 && tile + 2 < t1) issue(tile + 2, buf, &bar[s]);
+    }
+    if (failed_at >= 0 && t == 0) {
+        atomicOr(a.status, kStatusTimeout);
+        const int s = (int)((failed_at - t0) & 1);
+        if (!(a.inject_skip && failed_at == t0)) mbar_wait_bounded(&bar[s], phase[s], a.wait_budget);
+        if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1], a.wait_budget);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Columns: FFT along a strided axis (+ filter / bins on the last axis pass).
+//
+// Tiles of TB adjacent columns x L rows stream through two shared-memory
+// buffers: one elected thread issues the bulk tensor loads (TMA) of tile i+2
+// into the buffer tile i has just released, so the next tile is always in
+// flight while the current one is transformed.  The FFT exchanges run inside
+// the current tile's buffer, and the results leave by a TMA store from the
+// same buffer.  Every mbarrier wait is bounded; when one runs out the CTA
+// records kStatusTimeout in the workspace status word, drains its own copies
+// and returns.
 // ---------------------------------------------------------------------------
-template <int LOG2L, int MODE, int DIR>
-__global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a) {
-    constexpr int E = ColShape<LOG2L>::E;
+template <int LOG2L, int LOGTB>
+struct ColGeo {
+    using G = Geo<LOG2L, LOGTB, false, LOG2L>;
+    static constexpr int tile_elems = G::TB * G::L;
+    // dynamic shared memory before the bins: two tile buffers, the twiddles, two mbarriers
+    static constexpr size_t fixed_bytes = (size_t)2 * tile_elems * 8 + (size_t)G::L * 8 + 16;
+};
+
+template <int LOG2L, int LOGTB, int MODE, int DIR>
+__global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks(Geo<LOG2L, LOGTB, false, LOG2L>::T))
+    k_cols(const __grid_constant__ ColArgs a) {
+    using CG = ColGeo<LOG2L, LOGTB>;
+    using G = typename CG::G;
+    constexpr int L = G::L;
+    constexpr int E = G::E;
+    constexpr int TB = G::TB;
+    constexpr int T = G::T;
+    constexpr int LB = L < 256 ? L : 256;  // rows per TMA box
     using PF = Plan<LOG2L, false>;
     using PI = Plan<LOG2L, true>;
     constexpr bool kAcc = MODE != kModePlain;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Ctx c{(int)threadIdx.x, (int)blockDim.x, a.logTB};
-    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    constexpr bool kStore = MODE != kModeBins;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int tile_elems = CG::tile_elems;
+    float2* bufs[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw) + tile_elems};
+    float2* tw = bufs[1] + tile_elems;  // L twiddles
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
     const int nb = a.bp.nbins;
-    double* dbin = reinterpret_cast<double*>(sm + (1 << (a.logTB + LOG2L)));  // nb + 1 (last: Parseval)
-    long long* ang = reinterpret_cast<long long*>(dbin + nb + 1);              // 2 * ntheta
-    float* fbin = reinterpret_cast<float*>(ang + 2 * a.bp.ntheta);             // nb + 1
-    int* thr = reinterpret_cast<int*>(fbin + nb + 1);                          // nr + 1
-    float* tab0 = reinterpret_cast<float*>(thr + a.bp.nr + 1);                 // FILTER: |kappa_0 / a|^p, L
+    double* dbin = reinterpret_cast<double*>(bar + 2);                   // nb + 1 (last: Parseval)
+    long long* ang = reinterpret_cast<long long*>(dbin + nb + 1);         // 2 * (ntheta + 1)
+    float* fbin = reinterpret_cast<float*>(ang + 2 * (a.bp.ntheta + 1));  // nb + 1
+    int* thr = reinterpret_cast<int*>(fbin + nb + 1);                     // nr + 1
+    float* tab0 = reinterpret_cast<float*>(thr + a.bp.nr + 1);            // FILTER: |kappa_0 / a|^p, L
+    const int t = threadIdx.x;
+
+    long long t0, t1;
+    chunk_of(a.ntiles, t0, t1);
+    const long long tpb = a.B >> LOGTB;
+    constexpr uint32_t tile_bytes = (uint32_t)tile_elems * (uint32_t)sizeof(float2);
+    auto issue = [&](long long ti, float2* dst, uint64_t* b) {
+        const long long ab = ti / tpb;
+        const int c0 = (int)((ti - ab * tpb) << LOGTB);
+        mbar_arrive_expect_tx(b, tile_bytes);
+#pragma unroll
+        for (int y = 0; y < L; y += LB) tma_load_3d(dst + y * TB, &a.map, c0, y, (int)ab, b);
+    };
+
+    load_twiddles<G>(tw, a.tw, t);
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
     if constexpr (MODE == kModeFilter) {
         if (!a.fp.rotated) {
-            for (int l = c.t; l < (1 << LOG2L); l += c.T) {
+            for (int l = t; l < L; l += T) {
                 const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                tab0[l] = l == (1 << (LOG2L - 1)) ? 0.0f : powf(fabsf(x) * a.fp.inv_a[0], a.fp.p);
+                tab0[l] = l == L / 2 ? 0.0f : powf(fabsf(x) * a.fp.inv_a[0], a.fp.p);
             }
         }
     }
     if constexpr (kAcc) {
-        for (int i = c.t; i <= nb; i += c.T) {
+        for (int i = t; i <= nb; i += T) {
             dbin[i] = 0.0;
             fbin[i] = 0.0f;
         }
-        for (int i = c.t; i < a.bp.ntheta; i += c.T) {
-            ang[i] = a.bp.ang_c[i];
-            ang[a.bp.ntheta + i] = a.bp.ang_s[i];
-        }
-        if (nb > 0) fill_thresholds(a.bp, thr, c.t, c.T);
-        __syncthreads();
+        fill_angles(a.bp, ang, t, T);
+        if (nb > 0) fill_thresholds(a.bp, thr, t, T);
     }
-    const long long tpb = a.B >> a.logTB;
-    long long t0, t1;
-    chunk_of(a.ntiles, t0, t1);
-    long long cur = -1;
+    __syncthreads();
+    if (t == 0) {
+        if (t0 < t1 && !a.inject_skip) issue(t0, bufs[0], &bar[0]);
+        if (t0 + 1 < t1) issue(t0 + 1, bufs[1], &bar[1]);
+    }
+
     auto flush = [&](long long batch) {
         __syncthreads();
         double* g = MODE == kModeBins ? a.gbins + batch * nb : a.gbins;
-        for (int i = c.t; i < nb; i += c.T) {
+        for (int i = t; i < nb; i += T) {
             if (dbin[i] != 0.0) atomicAdd(g + i, dbin[i]);
             dbin[i] = 0.0;
         }
-        if (MODE == kModeFilter && c.t == 0) {
+        if (MODE == kModeFilter && t == 0) {
             atomicAdd(a.gP, dbin[nb]);
             dbin[nb] = 0.0;
         }
         __syncthreads();
     };
+
+    uint32_t phase[2] = {0u, 0u};
+    long long cur = -1;
+    long long failed_at = -1;
     for (long long ti = t0; ti < t1; ++ti) {
+        const int s = (int)((ti - t0) & 1);
+        float2* buf = bufs[s];
+        if (!cta_wait(&bar[s], phase[s], a.wait_budget)) {
+            failed_at = ti;
+            break;
+        }
+        phase[s] ^= 1u;
         const long long ab = ti / tpb;
-        const long long c0 = (ti - ab * tpb) << a.logTB;
+        const long long c0 = (ti - ab * tpb) << LOGTB;
         if constexpr (MODE == kModeBins) {
             if (ab != cur) {
                 if (cur >= 0) flush(cur);
                 cur = ab;
             }
         }
-        float2* base = a.data + ab * a.bstride + c0;
         float2 v[E];
         if constexpr (MODE == kModePlain && DIR > 0) {
-            for_each_element<LOG2L, false, PI::first_radix(), E>(
-                c, [&](int e, int b, int l) { v[e] = base[(long long)l * a.B + b]; });
-            fft<LOG2L, E, +1, true, false>(v, sm, a.tw, c);
-            for_each_element<LOG2L, false, PI::last_radix(), E>(
-                c, [&](int e, int b, int l) { base[(long long)l * a.B + b] = v[e]; });
+            for_each_element<G, PI::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
+            fft<G, +1, true>(v, buf, tw, t);
+            __syncthreads();
+            for_each_element<G, PI::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
         } else {
-            for_each_element<LOG2L, false, PF::first_radix(), E>(
-                c, [&](int e, int b, int l) { v[e] = base[(long long)l * a.B + b]; });
-            fft<LOG2L, E, -1, false, false>(v, sm, a.tw, c);
+            for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
+            fft<G, -1, false>(v, buf, tw, t);
             if constexpr (MODE == kModePlain) {
-                for_each_element<LOG2L, false, PF::last_radix(), E>(
-                    c, [&](int e, int b, int l) { base[(long long)l * a.B + b] = v[e]; });
+                __syncthreads();
+                for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
             } else {
-                // Per-mode power (weight 2 for the k_last > 0 half) goes through
-                // shared memory so that each thread then owns E consecutive n0 of
-                // one column: consecutive modes share a bin, so one atomic per
-                // run of equal bins replaces one per mode.
-                constexpr int L = 1 << LOG2L;
-                float pacc = 0.0f;
                 if constexpr (MODE == kModeFilter) {
                     // a thread's column is fixed: T is a multiple of TB
-                    const int col = (int)(c0 + (c.t & ((1 << c.logTB) - 1)));
+                    const int col = (int)(c0 + (t & (TB - 1)));
                     int n1, n2;
                     if (a.ndim == 3) {
                         n1 = signed_index(col >> a.logM, a.log2n[1]);
@@ -414,10 +587,9 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
                         s_col = powf(fabsf(y) * a.fp.inv_a[1], a.fp.p);
                         if (a.ndim == 3) s_col += powf(fabsf(z) * a.fp.inv_a[2], a.fp.p);
                     }
-                    for_each_element<LOG2L, false, PF::last_radix(), E>(c, [&](int e, int b, int l) {
-                        const bool nyq = nyq_col || l == (1 << (LOG2L - 1));
+                    for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) {
                         float h = 0.0f;
-                        if (!nyq) {
+                        if (!nyq_col && l != L / 2) {
                             if (!a.fp.rotated) {
                                 h = amplitude_from_sum(a.fp, tab0[l] + s_col);
                             } else {
@@ -428,22 +600,32 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
                         v[e] = cscale(v[e], h);
                     });
                 }
+                // Per-mode power (weight 2 for the k_last > 0 half) goes through
+                // shared memory so that each thread then owns E consecutive n0 of
+                // one column (element (b, l) to thread t = (b L + l) / E at slot
+                // i TS + t + t / 32, TS = T + T / 32: conflict-free both ways);
+                // consecutive modes share a bin or a neighbouring one, so bins are
+                // stepped and one atomic per run of equal bins replaces one per mode.
+                constexpr int TS = T + (T >> 5);
+                static_assert(E * TS <= 2 * tile_elems, "power staging fits the tile buffer");
+                float pacc = 0.0f;
                 if (nb > 0 || MODE == kModeFilter) {
-                    float* ps = reinterpret_cast<float*>(sm);  // [b][L + 1] powers
-                    __syncthreads();                           // the FFT's last exchange is read
-                    for_each_element<LOG2L, false, PF::last_radix(), E>(c, [&](int e, int b, int l) {
+                    float* ps = reinterpret_cast<float*>(buf);
+                    __syncthreads();  // the FFT's last exchange is read
+                    for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) {
                         const int col = (int)(c0 + b);
                         const int klast = a.ndim == 3 ? (col & ((1 << a.logM) - 1)) : col;
                         const float w = klast == 0 ? 1.0f : 2.0f;  // k and -k share a half-spectrum slot
                         const float pw = (MODE == kModeBins ? w * a.scale : w) * cabs2(v[e]);
                         pacc += pw;
-                        ps[b * (L + 1) + l] = pw;
+                        const int flat = (b << LOG2L) + l;
+                        const int owner = flat / E;
+                        ps[(flat & (E - 1)) * TS + owner + (owner >> 5)] = pw;
                     });
                     __syncthreads();
                     if (nb > 0) {
-                        const int g0 = c.t * E;
-                        const int b = g0 >> LOG2L;
-                        const int l0 = g0 & (L - 1);
+                        const int b = (t * E) >> LOG2L;
+                        const int l0 = (t * E) & (L - 1);
                         const int col = (int)(c0 + b);
                         int n1, n2;
                         if (a.ndim == 3) {
@@ -455,12 +637,12 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
                         }
                         int cur_bin = -1;
                         float acc = 0.0f;
-                        const int rot = c.t & (E - 1);  // staggered start: spreads the banks
+                        BinRun run;
 #pragma unroll 4
                         for (int i = 0; i < E; ++i) {
-                            const int l = l0 + ((i + rot) & (E - 1));
-                            const float pw = ps[b * (L + 1) + l];
-                            const int bin = bin_index(a.bp, thr, ang, signed_index(l, LOG2L), n1, n2, a.ndim);
+                            const float pw = ps[i * TS + t + (t >> 5)];
+                            const int bin =
+                                bin_index_run(a.bp, thr, ang, signed_index(l0 + i, LOG2L), n1, n2, a.ndim, run);
                             if (bin != cur_bin) {
                                 if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
                                 cur_bin = bin;
@@ -472,27 +654,56 @@ __global__ void __launch_bounds__(512) k_cols(const __grid_constant__ ColArgs a)
                     }
                 }
                 if constexpr (MODE == kModeFilter) {
-                    if (c.T >= 32) {  // T is a power of two: whole warps
+                    if constexpr (T >= 32) {
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
-                        if ((c.t & 31) == 0) atomicAdd(fbin + nb, pacc);
+                        if ((t & 31) == 0) atomicAdd(fbin + nb, pacc);
                     } else {
                         atomicAdd(fbin + nb, pacc);
                     }
-                    fft<LOG2L, E, +1, true, false>(v, sm, a.tw, c);
-                    for_each_element<LOG2L, false, PI::last_radix(), E>(
-                        c, [&](int e, int b, int l) { base[(long long)l * a.B + b] = v[e]; });
+                    fft<G, +1, true>(v, buf, tw, t);
+                    __syncthreads();
+                    for_each_element<G, PI::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
                 }
             }
         }
+        // the tile's results are in buf: store them, then refill buf with tile i+2
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            if constexpr (kStore) {
+#pragma unroll
+                for (int y = 0; y < L; y += LB) tma_store_3d(&a.map, (int)c0, y, (int)ab, buf + y * TB);
+                bulk_commit();
+            }
+            if (ti + 2 < t1) {
+                if constexpr (kStore) bulk_wait_read_all();
+                issue(ti + 2, buf, &bar[s]);
+            }
+        }
         if constexpr (kAcc) {
-            __syncthreads();
-            for (int i = c.t; i <= nb; i += c.T) {
+            for (int i = t; i <= nb; i += T) {
                 dbin[i] += (double)fbin[i];
                 fbin[i] = 0.0f;
             }
             __syncthreads();
         }
+    }
+    if (failed_at >= 0) {
+        if (t == 0) {
+            atomicOr(a.status, kStatusTimeout);
+            // drain this CTA's own loads still in flight (bounded), then its stores
+            const int s = (int)((failed_at - t0) & 1);
+            const bool issued = !(a.inject_skip && failed_at == t0);
+            if (issued) mbar_wait_bounded(&bar[s], phase[s], a.wait_budget);
+            if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1], a.wait_budget);
+            if constexpr (kStore) bulk_wait_all();
+        }
+        __syncthreads();
+        return;
+    }
+    if constexpr (kStore) {
+        if (t == 0) bulk_wait_all();
     }
     if constexpr (MODE == kModeBins) {
         if (cur >= 0) flush(cur);

@@ -1,18 +1,30 @@
-// launch.h -- kernel tables of the pass kernels (one entry per length).
+// launch.h -- kernel tables of the pass kernels.  Each length has two tile
+// widths compiled in: the "big" tile (256 or 512 threads) and a 2-line tile
+// for lattices whose other extents are too small for the big one.
 #pragma once
+
+#include <stddef.h>
 
 namespace hf {
 
 constexpr int kRowLog2Min = 2, kRowLog2Max = 11;  // row FFT length M = n_last / 2
 constexpr int kColLog2Min = 3, kColLog2Max = 12;  // strided-axis length
 
-// Kernel entry points; nullptr when the length is outside the table.
-const void* r2c_kernel(int log2m, int src);
-const void* c2r_kernel(int log2m, int out_dtype);
-const void* cols_kernel(int log2l, int mode, int dir);
+struct KernelInfo {
+    const void* fn = nullptr;  // kernel entry point (nullptr: length outside the table)
+    int threads = 0;           // threads per CTA
+    int log2_lines = 0;        // log2 of rows (row kernels) or columns (column kernels) per tile
+    size_t fixed_smem = 0;     // dynamic shared memory before any per-call tables
+};
 
-// Elements per thread of each kernel family (threads = lines * length / E).
-int row_elems(int log2m);
-int col_elems(int log2l);
+// log2 lines per tile of each variant
+constexpr int row_logtr(int log2m, bool big) { return big ? (log2m <= 4 ? 8 : 12 - log2m) : 0; }
+constexpr int col_logtb(int log2l, bool big) {
+    return big ? (log2l <= 4 ? 8 : (log2l >= 11 ? 13 - log2l : 12 - log2l)) : 1;
+}
+
+KernelInfo r2c_kernel(int log2m, bool big, int src);
+KernelInfo c2r_kernel(int log2m, bool big, int out_dtype);
+KernelInfo cols_kernel(int log2l, bool big, int mode, int dir);
 
 }  // namespace hf

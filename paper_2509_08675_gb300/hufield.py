@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, f"libhufield_{platform.machine()}.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEOUT, ERR_TOO_LARGE = range(7)
 F32, BF16, I8 = 0, 1, 2
 PLAN_PROFILE = 1
+PLAN_INJECT_TIMEOUT = 2
 MAX_LEVELS = 8
 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.int8: I8}
@@ -94,6 +95,7 @@ def _load():
     lib.hufield_status_string.argtypes = [C.c_int]
     lib.hufield_status_string.restype = C.c_char_p
     lib.hufield_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+    lib.hufield_workspace_status.argtypes = [vp, vp]
     lib.hufield_profile_names.argtypes = []
     lib.hufield_profile_names.restype = C.c_char_p
     return lib
@@ -132,14 +134,14 @@ def _levels(levels):
 class Plan:
     """hufield_plan for one lattice shape (2D or 3D), created on the current device."""
 
-    def __init__(self, shape, profile: bool = False):
+    def __init__(self, shape, profile: bool = False, inject_timeout: bool = False):
         self.shape = tuple(int(s) for s in shape)
         if len(self.shape) not in (2, 3):
             raise HufieldError(ERR_UNSUPPORTED_DIMS, "hufield_plan_create")
         dims = _Dims(len(self.shape), 0, (C.c_int64 * 3)(*(self.shape + (1,) * (3 - len(self.shape)))))
         h = C.c_void_p()
-        _check(_lib.hufield_plan_create(C.byref(h), C.byref(dims), PLAN_PROFILE if profile else 0),
-               "hufield_plan_create")
+        flags = (PLAN_PROFILE if profile else 0) | (PLAN_INJECT_TIMEOUT if inject_timeout else 0)
+        _check(_lib.hufield_plan_create(C.byref(h), C.byref(dims), flags), "hufield_plan_create")
         self._h = h
         self.N = math.prod(self.shape)
 
@@ -254,3 +256,8 @@ def hufield_spectrum_noalloc(shape, y: torch.Tensor, nr: int, ntheta: int, accum
     dims = _Dims(len(shape), 0, (C.c_int64 * 3)(*(shape + (1,) * (3 - len(shape)))))
     _check(_lib.hufield_spectrum_noalloc(C.byref(dims), _ptr(y), _DTYPES[y.dtype], nr, ntheta, int(accumulate),
                                          _ptr(sums), _ptr(counts), _stream(stream)), "hufield_spectrum_noalloc")
+
+
+def hufield_workspace_status(ws: torch.Tensor, stream=None) -> int:
+    """Status of the most recent call on `ws` (waits for the stream): OK or ERR_TIMEOUT."""
+    return int(_lib.hufield_workspace_status(_ptr(ws), _stream(stream)))
