@@ -52,18 +52,21 @@ def algorithmic_bytes(shape, nlev, field_bytes=4):
     """Bytes each pass kind must move per launch (one field), by the pass plan:
     r2c writes the half spectrum (4 B/voxel); a strided pass reads and writes it
     (8 B/voxel per spectrum); c2r reads it, writes the field, nlev sign maps and
-    nlev map spectra; the bins pass reads the nlev map spectra."""
+    nlev map spectra; the bins pass reads the nlev map spectra; the binning
+    passes read the bin table (1 B/voxel each time), which the table pass
+    ("counts") writes once per call."""
     N = math.prod(shape)
     h = 4 * N  # half spectrum bytes
+    tab = N  # bin table: one uint16 per half-spectrum mode
     return {
         "r2c": h,
         "cols_mid_fwd": 2 * h,
-        "cols_filter": 2 * h,
+        "cols_filter": 2 * h + tab,
         "cols_mid_inv": 2 * h,
         "c2r": h + field_bytes * N + nlev * N + nlev * h,
         "cols_mid_maps": 2 * h * nlev,
-        "cols_bins": h * nlev,
-        "counts": 0,
+        "cols_bins": (h + tab) * nlev,
+        "counts": tab,
         "misc": 0,
     }
 

@@ -174,9 +174,9 @@ int hufield_ensemble(hufield_plan *plan, const hufield_filter *filt, uint64_t se
  * cudaMalloc's implicit device synchronisation).  The paper has no
  * counterpart; this is a deployment convenience.
  *   - No plan and no workspace: the lattice comes as dims, and the scratch
- *     (the half spectrum, 4 MiB) and the twiddle table (32 KiB) are file-scope
- *     static device arrays of the library.  Every GPU that loads the library
- *     holds them until the process exits.
+ *     (the half spectrum, 4 MiB; its bin table, 1 MiB) and the twiddle table
+ *     (32 KiB) are file-scope static device arrays of the library.  Every GPU
+ *     that loads the library holds them until the process exits.
  *   - Largest lattice: N = prod n[i] <= 2^20 (e.g. 1024^2, 128^2 x 64);
  *     larger lattices return HUFIELD_ERR_TOO_LARGE before anything is enqueued.
  *     Other limits and arguments as hufield_spectrum.

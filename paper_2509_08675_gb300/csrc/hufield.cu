@@ -85,19 +85,7 @@ __global__ void k_threshold(long long nblk, const void* f, Levels lv, int nlev, 
     }
 }
 
-// Number of full-lattice modes per bin, from the half spectrum (weights 1 at
-// k_last = 0, 2 elsewhere), added times `mult` to each of ndst arrays.
-struct CountArgs {
-    int ndim;
-    int log2n[3];
-    long long nmodes;  // N / 2
-    long long mult;
-    int ndst;
-    unsigned long long* dst[kMaxLevels + 1];
-    BinParams bp;
-};
-
-__global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ CountArgs a) {
+__global__ void __launch_bounds__(256) k_bin_table(const __grid_constant__ TableArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem_raw);
     long long* ang = reinterpret_cast<long long*>(cnt + a.bp.nbins);
@@ -106,36 +94,36 @@ __global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ Coun
     fill_angles(a.bp, ang, threadIdx.x, blockDim.x);
     fill_thresholds(a.bp, thr, threadIdx.x, blockDim.x);
     __syncthreads();
-    const int logM = a.log2n[a.ndim - 1] - 1;
-    const int M = 1 << logM;
-    // each thread walks runs of RL consecutive k_last of one row
-    const int RL = M < 8 ? M : 8;
-    const int logRL = M < 8 ? logM : 3;
-    const long long nruns = a.nmodes >> logRL;
+    const int L = 1 << a.log2l;
+    const int tile_log = a.logTB + a.log2l;
+    // each thread takes runs of 8 consecutive l of one column
+    const long long nruns = a.nmodes >> 3;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nruns;
          r += (long long)gridDim.x * blockDim.x) {
-        const long long m0 = r << logRL;
-        const int k0 = (int)(m0 & (M - 1));
-        const long long row = m0 >> logM;
-        int n0, n1;
+        const long long f0 = r << 3;
+        const long long tile = f0 >> tile_log;
+        const int within = (int)(f0 & ((1ll << tile_log) - 1));
+        const int b = within >> a.log2l;
+        const int l0 = within & (L - 1);
+        const int col = (int)((tile << a.logTB) + b);
+        int n1, n2, klast;
         if (a.ndim == 3) {
-            n1 = signed_index((int)(row & ((1 << a.log2n[1]) - 1)), a.log2n[1]);
-            n0 = signed_index((int)(row >> a.log2n[1]), a.log2n[0]);
+            n1 = signed_index(col >> a.logM, a.log2n[1]);
+            n2 = col & ((1 << a.logM) - 1);
+            klast = n2;
         } else {
-            n0 = signed_index((int)row, a.log2n[0]);
-            n1 = 0;
+            n1 = col;
+            n2 = 0;
+            klast = col;
         }
+        const unsigned long long w = klast == 0 ? 1ull : 2ull;
         int run_bin = -1;
         unsigned long long run = 0;
-        BinRun cache;
-        for (int k = k0; k < k0 + RL; ++k) {
-            int bin;
-            if (a.ndim == 3) {
-                bin = bin_index_run(a.bp, thr, ang, n0, n1, k, 3, cache);
-            } else {
-                bin = bin_index_run(a.bp, thr, ang, n0, k, 0, 2, cache);
-            }
-            const unsigned long long w = k == 0 ? 1 : 2;
+        unsigned short out[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int bin = bin_index(a.bp, thr, ang, signed_index(l0 + i, a.log2l), n1, n2, a.ndim);
+            out[i] = bin < 0 ? (unsigned short)0xffff : (unsigned short)bin;
             if (bin != run_bin) {
                 if (run_bin >= 0) atomicAdd(cnt + run_bin, run);
                 run_bin = bin;
@@ -144,6 +132,12 @@ __global__ void __launch_bounds__(256) k_bin_counts(const __grid_constant__ Coun
             run += w;
         }
         if (run_bin >= 0) atomicAdd(cnt + run_bin, run);
+        uint4 pk;
+        pk.x = out[0] | ((unsigned)out[1] << 16);
+        pk.y = out[2] | ((unsigned)out[3] << 16);
+        pk.z = out[4] | ((unsigned)out[5] << 16);
+        pk.w = out[6] | ((unsigned)out[7] << 16);
+        reinterpret_cast<uint4*>(a.tab)[r] = pk;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < a.bp.nbins; i += blockDim.x) {
@@ -369,32 +363,49 @@ int make_bins(const hufield_plan* p, int nr, int ntheta, BinParams& bp) {
 }
 
 // Workspace: [header 256 B: status word][spectrum: max(nlev,1) * N/2 complex64]
-//            [P: double][raw field bins: nbins doubles]
+//            [bin table: N/2 uint16, when binning][P: double][raw field bins: nbins doubles]
 constexpr size_t kWsHeader = 256;
 
 struct Workspace {
     unsigned* status;
     float2* spec;
+    unsigned short* bintab;
     double* P;
     double* raw;
 };
 
+size_t ws_spec_bytes(const hufield_plan* p, int nlev) {
+    return align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
+}
+size_t ws_table_bytes(const hufield_plan* p, int nbins) {
+    return nbins > 0 ? align256((size_t)p->half * sizeof(unsigned short)) : 0;
+}
+
 size_t ws_bytes(const hufield_plan* p, int nlev, int nbins) {
-    const size_t spec = align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
-    return kWsHeader + spec + align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0)));
+    return kWsHeader + ws_spec_bytes(p, nlev) + ws_table_bytes(p, nbins) +
+           align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0)));
 }
 
 int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Workspace& w) {
     if (!ws) return HUFIELD_ERR_INVALID_ARG;
     if (((uintptr_t)ws & 255) != 0) return HUFIELD_ERR_INVALID_ARG;
     if (bytes < ws_bytes(p, nlev, nbins)) return HUFIELD_ERR_WS_TOO_SMALL;
-    const size_t spec = align256((size_t)(nlev > 1 ? nlev : 1) * (size_t)p->half * sizeof(float2));
     char* base = reinterpret_cast<char*>(ws);
+    const size_t spec = ws_spec_bytes(p, nlev), tab = ws_table_bytes(p, nbins);
     w.status = reinterpret_cast<unsigned*>(base);
     w.spec = reinterpret_cast<float2*>(base + kWsHeader);
-    w.P = reinterpret_cast<double*>(base + kWsHeader + spec);
+    w.bintab = tab ? reinterpret_cast<unsigned short*>(base + kWsHeader + spec) : nullptr;
+    w.P = reinterpret_cast<double*>(base + kWsHeader + spec + tab);
     w.raw = w.P + 1;
     return HUFIELD_OK;
+}
+
+// Tile width (log2) of the axis-0 pass: its FILTER and BINS kernels and the
+// bin table share it.
+int axis0_logtb(const hufield_plan* p) {
+    const long long B = p->half >> p->log2n[0];
+    const bool big = B >= (1ll << col_logtb(p->log2n[0], true));
+    return col_logtb(p->log2n[0], big);
 }
 
 bool aligned(const void* ptr) { return ((uintptr_t)ptr & 255) == 0; }
@@ -446,7 +457,8 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
 
 // Strided pass along axis 0 over `nbatch` spectra of N/2 modes each.
 int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const FilterParams* fp,
-               const BinParams& bp, double* gbins, double* gP, unsigned* status, cudaStream_t s) {
+               const BinParams& bp, const unsigned short* bintab, double* gbins, double* gP, unsigned* status,
+               cudaStream_t s) {
     ColArgs ca{};
     ca.status = status;
     ca.wait_budget = p->wait_budget;
@@ -461,13 +473,12 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     for (int d = 0; d < 3; ++d) ca.log2n[d] = p->log2n[d];
     if (fp) ca.fp = *fp;
     ca.bp = bp;
+    ca.bintab = bintab;
     ca.gbins = gbins;
     ca.gP = gP;
     ca.scale = (float)(1.0 / (double)p->N);
     const size_t extra = mode == kModePlain ? 0
                                             : (size_t)(bp.nbins + 1) * (sizeof(double) + sizeof(float)) +
-                                                  (size_t)2 * (bp.ntheta + 1) * sizeof(long long) +
-                                                  (size_t)(bp.nr + 1) * sizeof(int) +
                                                   (mode == kModeFilter ? sizeof(float) << p->log2n[0] : 0);
     Launch L;
     KernelInfo k;
@@ -480,24 +491,30 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
 }
 
 
-int bin_counts(hufield_plan* p, const BinParams& bp, long long mult, int ndst, long long** dst,
-               cudaStream_t s) {
-    CountArgs ca{};
-    ca.ndim = p->ndim;
-    for (int d = 0; d < 3; ++d) ca.log2n[d] = p->log2n[d];
-    ca.nmodes = p->half;
-    ca.mult = mult;
-    ca.ndst = ndst;
-    for (int d = 0; d < ndst; ++d) ca.dst[d] = reinterpret_cast<unsigned long long*>(dst[d]);
-    ca.bp = bp;
+// Bin table of the lattice (tile order of the axis-0 pass) and the mode
+// counts per bin, added times `mult` to each of ndst arrays.
+int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, long long mult, int ndst,
+                    long long** dst, cudaStream_t s) {
+    TableArgs ta{};
+    ta.tab = tab;
+    ta.nmodes = p->half;
+    ta.log2l = p->log2n[0];
+    ta.logTB = axis0_logtb(p);
+    ta.ndim = p->ndim;
+    ta.logM = p->logM;
+    for (int d = 0; d < 3; ++d) ta.log2n[d] = p->log2n[d];
+    ta.mult = mult;
+    ta.ndst = ndst;
+    for (int d = 0; d < ndst; ++d) ta.dst[d] = reinterpret_cast<unsigned long long*>(dst[d]);
+    ta.bp = bp;
     Launch L;
     L.block = 256;
     L.smem = (size_t)bp.nbins * sizeof(unsigned long long) + (size_t)2 * (bp.ntheta + 1) * sizeof(long long) +
              (size_t)(bp.nr + 1) * sizeof(int);
-    L.grid = occupancy_grid(reinterpret_cast<const void*>(&k_bin_counts), L.block, L.smem,
+    L.grid = occupancy_grid(reinterpret_cast<const void*>(&k_bin_table), L.block, L.smem,
                             ((p->half >> 3) + L.block - 1) / L.block, p->nsm);
     if (L.grid <= 0) return HUFIELD_ERR_CUDA;
-    HF_CUDA(launch(p, kPassCounts, reinterpret_cast<const void*>(&k_bin_counts), L, &ca, s));
+    HF_CUDA(launch(p, kPassCounts, reinterpret_cast<const void*>(&k_bin_table), L, &ta, s));
     return HUFIELD_OK;
 }
 
@@ -513,7 +530,7 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     HF_CUDA(cudaMemsetAsync(w.P, 0, sizeof(double) * (size_t)(1 + b.nbins), s));
     int rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
     if (rc) return rc;
-    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, w.raw, w.P, w.status, s);
+    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, w.bintab, w.raw, w.P, w.status, s);
     if (rc) return rc;
     if (p->ndim == 3) {
         rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s);
@@ -549,7 +566,7 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
             rc = mid_pass(p, -1, w.spec, nlev, kPassMidMaps, w.status, s);
             if (rc) return rc;
         }
-        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, sums_m, nullptr, w.status, s);
+        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, w.bintab, sums_m, nullptr, w.status, s);
         if (rc) return rc;
     }
     return HUFIELD_OK;
@@ -669,7 +686,7 @@ int hufield_forward(hufield_plan* p, uint64_t seed, uint32_t field_idx, void* ws
     if (rc) return rc;
     BinParams none{};
     none.ntheta = 1;
-    return axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, w.status, s);
+    return axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, nullptr, w.status, s);
 }
 
 int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx,
@@ -725,12 +742,12 @@ int hufield_spectrum(hufield_plan* p, const void* y, int32_t dtype, int32_t nr, 
         HF_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * bp.nbins, s));
     }
     long long* dst[1] = {reinterpret_cast<long long*>(counts)};
-    rc = bin_counts(p, bp, 1, 1, dst, s);
+    rc = build_bin_table(p, bp, w.bintab, 1, 1, dst, s);
     if (rc) return rc;
     const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
     rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, w.status, s);
     if (rc) return rc;
-    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, sums, nullptr, w.status, s);
+    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, w.bintab, sums, nullptr, w.status, s);
 }
 
 int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field0, int32_t nfields,
@@ -765,7 +782,7 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     long long* dst[kMaxLevels + 1];
     dst[0] = reinterpret_cast<long long*>(counts_f);
     for (int t = 0; t < nlev; ++t) dst[1 + t] = reinterpret_cast<long long*>(counts_m) + (long long)t * bp.nbins;
-    rc = bin_counts(p, bp, nfields, 1 + nlev, dst, s);
+    rc = build_bin_table(p, bp, w.bintab, nfields, 1 + nlev, dst, s);
     if (rc) return rc;
     const size_t esize = out_dtype == HUFIELD_BF16 ? 2 : 4;
     for (int e = 0; e < nfields; ++e) {
@@ -836,12 +853,14 @@ constexpr long long kStaticMaxVoxels = 1ll << 20;  // half spectrum: 2^19 comple
 static __device__ __align__(256) float2 g_static_spec[kStaticMaxVoxels / 2];
 static __device__ __align__(256) float2 g_static_tw[kTwN];
 static __device__ __align__(256) unsigned g_static_status[64];
+static __device__ __align__(256) unsigned short g_static_bintab[kStaticMaxVoxels / 2];
 
 struct StaticScratch {
     bool ready = false;
     float2* spec = nullptr;
     float2* tw = nullptr;
     unsigned* status = nullptr;
+    unsigned short* bintab = nullptr;
     int nsm = 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
 };
@@ -861,6 +880,8 @@ int static_setup(int dev, cudaStream_t s, StaticScratch& out) {
         if (cudaGetSymbolAddress(&spec, g_static_spec) != cudaSuccess) return HUFIELD_ERR_CUDA;
         if (cudaGetSymbolAddress(&tw, g_static_tw) != cudaSuccess) return HUFIELD_ERR_CUDA;
         if (cudaGetSymbolAddress(&status, g_static_status) != cudaSuccess) return HUFIELD_ERR_CUDA;
+        void* bintab = nullptr;
+        if (cudaGetSymbolAddress(&bintab, g_static_bintab) != cudaSuccess) return HUFIELD_ERR_CUDA;
         PFN_cuTensorMapEncodeTiled_v12000 enc = encode_entry();
         if (!enc) return HUFIELD_ERR_CUDA;
         int nsm = 0;
@@ -870,6 +891,7 @@ int static_setup(int dev, cudaStream_t s, StaticScratch& out) {
         st.spec = reinterpret_cast<float2*>(spec);
         st.tw = reinterpret_cast<float2*>(tw);
         st.status = reinterpret_cast<unsigned*>(status);
+        st.bintab = reinterpret_cast<unsigned short*>(bintab);
         st.nsm = nsm;
         st.encode = enc;
         st.ready = true;
@@ -921,10 +943,10 @@ extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y,
         HF_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * bp.nbins, s));
     }
     long long* dst[1] = {reinterpret_cast<long long*>(counts)};
-    rc = bin_counts(&p, bp, 1, 1, dst, s);
+    rc = build_bin_table(&p, bp, st.bintab, 1, 1, dst, s);
     if (rc) return rc;
     const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
     rc = forward_rows_and_mid(&p, src, y, 0, 0, st.spec, st.status, s);
     if (rc) return rc;
-    return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, sums, nullptr, st.status, s);
+    return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, st.bintab, sums, nullptr, st.status, s);
 }

@@ -67,6 +67,7 @@ struct ColArgs {
     int log2n[3];
     FilterParams fp;
     BinParams bp;
+    const unsigned short* bintab;  // FILTER/BINS: bin of every mode in tile order (tile, b, l); 0xFFFF = dropped
     double* gbins;          // FILTER: raw field bins [nbins]; BINS: [A][nbins]
     double* gP;             // FILTER: Parseval sum
     float scale;            // BINS: 1 / N
@@ -179,44 +180,6 @@ __device__ __forceinline__ int bin_index(const BinParams& bp, const int* thr, co
     int a0 = v0, a1 = v1;
     fold_vector(a0, a1);
     return rb * bp.ntheta + sector_from_scratch(bp, ang, a0, a1);
-}
-
-// Bins of a run of modes: the radial bin and the sector of the previous
-// mode are stepped to the current one with exact integer compares (the
-// thresholds and the edge cross products), which is cheap because
-// neighbouring modes lie in the same or a neighbouring bin.
-struct BinRun {
-    int rb = -1;  // radial bin (nr = outside); -1: none yet
-    int sec = 0;
-};
-
-__device__ __forceinline__ int bin_index_run(const BinParams& bp, const int* thr, const long long* ang, int n0, int n1,
-                                             int n2, int ndim, BinRun& st) {
-    const int v0 = n0 << bp.shift[0];
-    const int v1 = n1 << bp.shift[1];
-    const int v2 = ndim == 3 ? (n2 << bp.shift[2]) : 0;
-    const int Q = 4 * (v0 * v0 + v1 * v1 + v2 * v2);
-    int b = st.rb;
-    if (b < 0) {
-        b = radial_from_scratch(bp, thr, Q);
-    } else {
-        while (b < bp.nr && Q >= thr[b + 1]) ++b;
-        while (b > 0 && Q < thr[b]) --b;
-    }
-    st.rb = b;
-    if (b >= bp.nr) return -1;
-    if (bp.ntheta == 1) return b;
-    int a0 = v0, a1 = v1;
-    fold_vector(a0, a1);
-    int s = st.sec;
-    if (a0 == 0 && a1 == 0) {
-        s = 0;
-    } else {
-        while (s + 1 < bp.ntheta && cross_edge(ang, bp.ntheta, s + 1, a0, a1) >= 0) ++s;
-        while (s > 0 && cross_edge(ang, bp.ntheta, s, a0, a1) < 0) --s;
-    }
-    st.sec = s;
-    return b * bp.ntheta + s;
 }
 
 // Angle table (ntheta + 1 edges) from the parameter block into shared memory.
@@ -475,11 +438,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
     float2* tw = bufs[1] + tile_elems;  // L twiddles
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
     const int nb = a.bp.nbins;
-    double* dbin = reinterpret_cast<double*>(bar + 2);                   // nb + 1 (last: Parseval)
-    long long* ang = reinterpret_cast<long long*>(dbin + nb + 1);         // 2 * (ntheta + 1)
-    float* fbin = reinterpret_cast<float*>(ang + 2 * (a.bp.ntheta + 1));  // nb + 1
-    int* thr = reinterpret_cast<int*>(fbin + nb + 1);                     // nr + 1
-    float* tab0 = reinterpret_cast<float*>(thr + a.bp.nr + 1);            // FILTER: |kappa_0 / a|^p, L
+    double* dbin = reinterpret_cast<double*>(bar + 2);   // nb + 1 (last: Parseval)
+    float* fbin = reinterpret_cast<float*>(dbin + nb + 1);  // nb + 1
+    float* tab0 = fbin + nb + 1;                          // FILTER: |kappa_0 / a|^p, L
     const int t = threadIdx.x;
 
     long long t0, t1;
@@ -513,8 +474,6 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
             dbin[i] = 0.0;
             fbin[i] = 0.0f;
         }
-        fill_angles(a.bp, ang, t, T);
-        if (nb > 0) fill_thresholds(a.bp, thr, t, T);
     }
     __syncthreads();
     if (t == 0) {
@@ -553,6 +512,27 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
             if (ab != cur) {
                 if (cur >= 0) flush(cur);
                 cur = ab;
+            }
+        }
+        // the bins of the E modes this thread will own after the staging
+        // (tile order: element (b, l) at b L + l, thread t owns t E .. t E + E - 1)
+        uint32_t binw[E / 2 > 0 ? E / 2 : 1];
+        if constexpr (kAcc) {
+            if (nb > 0) {
+                const unsigned short* src = a.bintab + (ti - ab * tpb) * tile_elems + t * E;
+                if constexpr (E >= 8) {
+#pragma unroll
+                    for (int q = 0; q < E / 8; ++q) {
+                        const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
+                        binw[4 * q] = w4.x;
+                        binw[4 * q + 1] = w4.y;
+                        binw[4 * q + 2] = w4.z;
+                        binw[4 * q + 3] = w4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < E / 2; ++q) binw[q] = __ldg(reinterpret_cast<const uint32_t*>(src) + q);
+                }
             }
         }
         float2 v[E];
@@ -604,8 +584,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
                 // shared memory so that each thread then owns E consecutive n0 of
                 // one column (element (b, l) to thread t = (b L + l) / E at slot
                 // i TS + t + t / 32, TS = T + T / 32: conflict-free both ways);
-                // consecutive modes share a bin or a neighbouring one, so bins are
-                // stepped and one atomic per run of equal bins replaces one per mode.
+                // their bins come precomputed from the bin table, and consecutive
+                // modes mostly share a bin, so one atomic per run of equal bins
+                // replaces one per mode.
                 constexpr int TS = T + (T >> 5);
                 static_assert(E * TS <= 2 * tile_elems, "power staging fits the tile buffer");
                 float pacc = 0.0f;
@@ -624,25 +605,13 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
                     });
                     __syncthreads();
                     if (nb > 0) {
-                        const int b = (t * E) >> LOG2L;
-                        const int l0 = (t * E) & (L - 1);
-                        const int col = (int)(c0 + b);
-                        int n1, n2;
-                        if (a.ndim == 3) {
-                            n1 = signed_index(col >> a.logM, a.log2n[1]);
-                            n2 = col & ((1 << a.logM) - 1);
-                        } else {
-                            n1 = col;
-                            n2 = 0;
-                        }
                         int cur_bin = -1;
                         float acc = 0.0f;
-                        BinRun run;
-#pragma unroll 4
+#pragma unroll
                         for (int i = 0; i < E; ++i) {
                             const float pw = ps[i * TS + t + (t >> 5)];
-                            const int bin =
-                                bin_index_run(a.bp, thr, ang, signed_index(l0 + i, LOG2L), n1, n2, a.ndim, run);
+                            const int raw = (int)((binw[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+                            const int bin = raw == 0xffff ? -1 : raw;
                             if (bin != cur_bin) {
                                 if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
                                 cur_bin = bin;
@@ -711,5 +680,27 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
         flush(0);
     }
 }
+
+// ---------------------------------------------------------------------------
+// Bin table: the bin of every half-spectrum mode, in the tile order of the
+// axis-0 pass (tile of TB columns, element (b, l) at b L + l), 0xFFFF for
+// modes with |kappa| >= 1; and the number of full-lattice modes per bin
+// (weight 1 at k_last = 0, 2 elsewhere), added times `mult` to each of ndst
+// count arrays.  The bins depend only on the lattice, so one table serves
+// every field of a call and both binning passes.
+// ---------------------------------------------------------------------------
+struct TableArgs {
+    unsigned short* tab;
+    long long nmodes;  // N / 2
+    int log2l;         // axis-0 length
+    int logTB;         // axis-0 tile width
+    int ndim;
+    int logM;
+    int log2n[3];
+    long long mult;
+    int ndst;
+    unsigned long long* dst[kMaxLevels + 1];
+    BinParams bp;
+};
 
 }  // namespace hf
