@@ -71,6 +71,22 @@ def algorithmic_bytes(shape, nlev, field_bytes=4):
     }
 
 
+def replica_field0(rank: int, nfields: int) -> int:
+    """First field index of a rank's ensemble: ranks generate disjoint fields."""
+    return rank * nfields
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    """The slowest rank's time (weak scaling): all-reduce MAX, identity on one rank."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -254,6 +270,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     fdt = torch.float32 if args.dtype == "f32" else torch.bfloat16
     filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
     plan = hf.Plan(shape, profile=True)
+    hf.hufield_plan_set_bins(plan, nr, nt)  # plan-time bin table and counts, as a production caller would
     ws = plan.workspace(nlev, nb)
     out_f = torch.empty((nf,) + tuple(shape), dtype=fdt, device="cuda")
     maps = torch.empty((nf, nlev) + tuple(shape), dtype=torch.int8, device="cuda")
@@ -263,7 +280,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     cm = torch.zeros(nlev * nb, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    field0 = rank * nf
+    field0 = replica_field0(rank, nf)
 
     def step(i):
         hf.hufield_ensemble(plan, filt, 1000 + i, field0, nf, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, ws,
@@ -302,10 +319,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     prof = hf.hufield_profile_read(plan)
     if hf.hufield_workspace_status(ws) != hf.OK:
         raise RuntimeError("device-side timeout during the timed steps")
-    if dist is not None:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(dist, tot_ms, "cuda")
     value = world * args.steps * nf * N / (tot_ms / 1e3)
 
     # roofline of the dominant pass (live per-launch CUDA-event times of the timed steps)
@@ -375,10 +389,7 @@ def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws
         comp.synchronize()
     dt = time.perf_counter() - t0
     hf.hufield_profile_read(plan)
-    if dist is not None:
-        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dist, dt, "cuda")
     d2h = (out_f.numel() * out_f.element_size() + maps.numel() + sum(t.numel() * t.element_size()
                                                                       for t in (sf, cf, sm, cm)))
     return {"value": world * steps * nf * N / dt, "unit": "voxels/s", "h2d_bytes_per_step": 0,

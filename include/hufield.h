@@ -37,7 +37,8 @@
  *   - Every buffer argument named out_*, ws, sums, counts, f or y is a DEVICE
  *     pointer owned by the caller; levels is a HOST pointer.  Device buffers
  *     must be 256-byte aligned.  The library allocates device memory only in
- *     hufield_plan_create (a 32 KB twiddle table) and never on a hot call.
+ *     hufield_plan_create (a 32 KB twiddle table) and hufield_plan_set_bins,
+ *     never on a hot call.
  *   - All hot calls are asynchronous on the given CUDA stream (a cudaStream_t
  *     passed as void*, NULL = legacy default stream) and return after
  *     enqueueing the work.  A stream-ordered caller may reuse ws once the call
@@ -108,6 +109,14 @@ typedef struct {
  * for a lattice outside the set above. */
 int hufield_plan_create(hufield_plan **plan, const hufield_dims *dims, uint32_t flags);
 int hufield_plan_destroy(hufield_plan *plan);
+
+/* Plan-time bins: builds, on the plan's device, the bin of every mode for
+ * (nr, ntheta) and the number of modes per bin (allocating N bytes plus
+ * 8 nr ntheta bytes, freed with the plan), so that later calls with the
+ * same nr and ntheta reuse them instead of building them per call (the bins
+ * depend only on the lattice).  nr = 0 drops them.  Synchronises the device;
+ * call it outside stream capture. */
+int hufield_plan_set_bins(hufield_plan *plan, int32_t nr, int32_t ntheta);
 
 /* Bytes of device workspace a call needs: nlev sign maps (0 for
  * hufield_generate, 1 for hufield_spectrum) and nbins = nr * ntheta bins
@@ -189,6 +198,43 @@ int hufield_ensemble(hufield_plan *plan, const hufield_filter *filt, uint64_t se
  *     on the GPU race, so serialise them (one stream, or events). */
 int hufield_spectrum_noalloc(const hufield_dims *dims, const void *y, int32_t dtype, int32_t nr, int32_t ntheta,
                              int32_t accumulate, double *sums, int64_t *counts, void *stream);
+
+/* ---- Ragged batches ------------------------------------------------------
+ * Many fields of different lattices and filters in one launch: the whole
+ * path (as hufield_pipeline with one level and radial bins) for every item.
+ * Items are grouped by lattice into size classes, each with its own plan
+ * (bins cached), workspace slice and stream; hufield_batch_run captures the
+ * whole batch into one CUDA graph, with the classes as parallel branches, and
+ * replays it on later runs with the same buffers (one graph launch per run).
+ * Outputs lie end to end in item order (see hufield_batch_layout). */
+typedef struct {
+    hufield_dims dims;
+    hufield_filter filt;
+    uint64_t seed;
+    uint32_t field_idx;
+    float level;    /* sign-map level */
+    int32_t nr;     /* radial bins (no angular sectors) */
+} hufield_batch_item;
+
+typedef struct hufield_batch hufield_batch;
+
+/* Plan a batch of n >= 1 items on the current device (copies the items;
+ * flags must be 0).  Allocates the size-class plans and streams. */
+int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, int32_t n, uint32_t flags);
+
+/* Output layout (host arrays of n entries, either may be NULL): item i's
+ * field is out_f[f_offset[i] .. + N_i) (and its map the same range of
+ * out_maps), its bins [bin_offset[i] .. + nr_i) of each bin array.  totals
+ * (may be NULL) receives {sum of N_i, sum of nr_i, workspace bytes}. */
+int hufield_batch_layout(const hufield_batch *batch, int64_t *f_offset, int64_t *bin_offset, int64_t totals[3]);
+
+/* Run the batch (asynchronous on `stream`): out_f FP32 fields, out_maps int8
+ * sign maps (either may be NULL), field and map bins (overwritten).  The
+ * first run, and any run with other buffers, captures the graph. */
+int hufield_batch_run(hufield_batch *batch, float *out_f, int8_t *out_maps, double *sums_f, int64_t *counts_f,
+                      double *sums_m, int64_t *counts_m, void *ws, size_t ws_bytes, void *stream);
+
+int hufield_batch_destroy(hufield_batch *batch);
 
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,

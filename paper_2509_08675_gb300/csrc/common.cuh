@@ -148,9 +148,8 @@ struct FilterParams {
     float kstar;        // analytic maximiser of K^s exp(-(K-k0)^2/(2w^2))
     float log2_kstar;
     float two_k0;
-    float inv_2w2;      // 1 / (2 w^2)
-    float half_s_ln2;   // s ln2 / 2   (H = exp(0.5 ln chi))
-    float half;         // 0.5 (kept in the struct to keep FMAs uniform)
+    float half_s;       // s / 2                 H = 2^(s/2 (log2 K - log2 K*) - c d),
+    float c_d;          // log2(e) / (4 w^2)     d = (K - k0)^2 - (K* - k0)^2
 };
 
 // Binning parameters; the angle table lives in shared memory at run time.

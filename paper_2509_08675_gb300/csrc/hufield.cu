@@ -146,6 +146,19 @@ __global__ void __launch_bounds__(256) k_bin_table(const __grid_constant__ Table
     }
 }
 
+// dst[d][b] += mult * counts[b] for each destination (cached counts of a plan).
+struct AddCountsArgs {
+    const long long* counts;
+    int nbins;
+    long long mult;
+    int ndst;
+    long long* dst[kMaxLevels + 1];
+};
+__global__ void k_add_counts(const __grid_constant__ AddCountsArgs a) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nbins; b += gridDim.x * blockDim.x)
+        for (int d = 0; d < a.ndst; ++d) a.dst[d][b] += a.mult * a.counts[b];
+}
+
 // sums_f[b] += raw[b] * N / P  (S_f(n) = N |G(n)|^2 / sum |G|^2)
 __global__ void k_finalize_field(const double* raw, const double* P, int nbins, double N, double* sums) {
     const double s = N / *P;
@@ -188,6 +201,10 @@ struct hufield_plan {
     int nsm;
     float2* tw;
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;  // driver entry point (no libcuda link)
+    // bins cached by hufield_plan_set_bins: table (tile order of the axis-0 pass) and counts
+    int cache_nr = 0, cache_nt = 0;
+    unsigned short* cache_tab = nullptr;
+    long long* cache_counts = nullptr;
     long long wait_budget = 0;                            // SM cycles per bounded mbarrier wait
     bool inject_timeout = false;                          // test hook (HUFIELD_PLAN_INJECT_TIMEOUT)
 };
@@ -335,9 +352,8 @@ FilterParams make_filter(const hufield_plan* p, const hufield_filter* f) {
     fp.kstar = (float)ks;
     fp.log2_kstar = (float)log2(ks);
     fp.two_k0 = (float)(2.0 * k0);
-    fp.inv_2w2 = (float)(1.0 / (2.0 * w * w));
-    fp.half_s_ln2 = (float)(0.5 * s * log(2.0));
-    fp.half = 0.5f;
+    fp.half_s = (float)(0.5 * s);
+    fp.c_d = (float)(1.0 / (4.0 * w * w * log(2.0)));
     return fp;
 }
 
@@ -491,6 +507,32 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
 }
 
 
+int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, long long mult, int ndst,
+                    long long** dst, cudaStream_t s);
+
+// The bins a call uses: the plan's cached table and counts when they match
+// (nr, ntheta), else a table built into the workspace.  Adds mult times the
+// counts to each of ndst arrays; returns the table to read in `tab`.
+int bins_for_call(hufield_plan* p, const BinParams& bp, unsigned short* ws_tab, long long mult, int ndst,
+                  long long** dst, const unsigned short** tab, cudaStream_t s) {
+    if (p->cache_tab && p->cache_nr == bp.nr && p->cache_nt == bp.ntheta) {
+        AddCountsArgs ac{};
+        ac.counts = p->cache_counts;
+        ac.nbins = bp.nbins;
+        ac.mult = mult;
+        ac.ndst = ndst;
+        for (int d = 0; d < ndst; ++d) ac.dst[d] = dst[d];
+        HF_CUDA(profiled(p, kPassMisc, s, [&] {
+            k_add_counts<<<(bp.nbins + 255) / 256, 256, 0, s>>>(ac);
+            return cudaGetLastError();
+        }));
+        *tab = p->cache_tab;
+        return HUFIELD_OK;
+    }
+    *tab = ws_tab;
+    return build_bin_table(p, bp, ws_tab, mult, ndst, dst, s);
+}
+
 // Bin table of the lattice (tile order of the axis-0 pass) and the mode
 // counts per bin, added times `mult` to each of ndst arrays.
 int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, long long mult, int ndst,
@@ -522,7 +564,7 @@ int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, l
 // sums/counts.  nbins == 0 skips every spectrum.
 int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx, int out_dtype,
               void* out_f, const float* levels, int nlev, int8_t* out_maps, const BinParams* bp, double* sums_f,
-              double* sums_m, const Workspace& w, cudaStream_t s) {
+              double* sums_m, const unsigned short* tab, const Workspace& w, cudaStream_t s) {
     const FilterParams fp = make_filter(p, f);
     BinParams none{};
     none.ntheta = 1;
@@ -530,7 +572,7 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     HF_CUDA(cudaMemsetAsync(w.P, 0, sizeof(double) * (size_t)(1 + b.nbins), s));
     int rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
     if (rc) return rc;
-    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, w.bintab, w.raw, w.P, w.status, s);
+    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, w.raw, w.P, w.status, s);
     if (rc) return rc;
     if (p->ndim == 3) {
         rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s);
@@ -566,7 +608,7 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
             rc = mid_pass(p, -1, w.spec, nlev, kPassMidMaps, w.status, s);
             if (rc) return rc;
         }
-        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, w.bintab, sums_m, nullptr, w.status, s);
+        rc = axis0_pass(p, kModeBins, w.spec, nlev, nullptr, b, tab, sums_m, nullptr, w.status, s);
         if (rc) return rc;
     }
     return HUFIELD_OK;
@@ -650,9 +692,41 @@ int hufield_plan_destroy(hufield_plan* p) {
         cudaEventDestroy(r.stop);
     }
     for (auto e : p->pool) cudaEventDestroy(e);
+    cudaFree(p->cache_tab);
+    cudaFree(p->cache_counts);
     cudaFree(p->tw);
     delete p;
     return HUFIELD_OK;
+}
+
+int hufield_plan_set_bins(hufield_plan* p, int32_t nr, int32_t ntheta) {
+    if (!p) return HUFIELD_ERR_INVALID_ARG;
+    cudaFree(p->cache_tab);
+    cudaFree(p->cache_counts);
+    p->cache_tab = nullptr;
+    p->cache_counts = nullptr;
+    p->cache_nr = p->cache_nt = 0;
+    if (nr == 0) return HUFIELD_OK;
+    BinParams bp;
+    int rc = make_bins(p, nr, ntheta, bp);
+    if (rc) return rc;
+    if (cudaMalloc(&p->cache_tab, sizeof(unsigned short) * (size_t)p->half) != cudaSuccess ||
+        cudaMalloc(&p->cache_counts, sizeof(long long) * (size_t)bp.nbins) != cudaSuccess ||
+        cudaMemset(p->cache_counts, 0, sizeof(long long) * (size_t)bp.nbins) != cudaSuccess) {
+        cudaFree(p->cache_tab);
+        cudaFree(p->cache_counts);
+        p->cache_tab = nullptr;
+        p->cache_counts = nullptr;
+        return HUFIELD_ERR_CUDA;
+    }
+    long long* dst[1] = {p->cache_counts};
+    rc = build_bin_table(p, bp, p->cache_tab, 1, 1, dst, nullptr);
+    if (rc == HUFIELD_OK && cudaDeviceSynchronize() != cudaSuccess) rc = HUFIELD_ERR_CUDA;
+    if (rc == HUFIELD_OK) {
+        p->cache_nr = nr;
+        p->cache_nt = ntheta;
+    }
+    return rc;
 }
 
 size_t hufield_workspace_bytes(const hufield_plan* p, int32_t nlev, int32_t nbins) {
@@ -700,8 +774,8 @@ int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     rc = carve(p, ws, bytes, 0, 0, w);
     if (rc) return rc;
     HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), (cudaStream_t)stream));
-    return run_field(p, f, seed, field_idx, out_dtype, out_f, nullptr, 0, nullptr, nullptr, nullptr, nullptr, w,
-                     (cudaStream_t)stream);
+    return run_field(p, f, seed, field_idx, out_dtype, out_f, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     w, (cudaStream_t)stream);
 }
 
 int hufield_threshold(hufield_plan* p, const void* f, int32_t dtype, const float* levels, int32_t nlev,
@@ -742,12 +816,13 @@ int hufield_spectrum(hufield_plan* p, const void* y, int32_t dtype, int32_t nr, 
         HF_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * bp.nbins, s));
     }
     long long* dst[1] = {reinterpret_cast<long long*>(counts)};
-    rc = build_bin_table(p, bp, w.bintab, 1, 1, dst, s);
+    const unsigned short* tab = nullptr;
+    rc = bins_for_call(p, bp, w.bintab, 1, 1, dst, &tab, s);
     if (rc) return rc;
     const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
     rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, w.status, s);
     if (rc) return rc;
-    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, w.bintab, sums, nullptr, w.status, s);
+    return axis0_pass(p, kModeBins, w.spec, 1, nullptr, bp, tab, sums, nullptr, w.status, s);
 }
 
 int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field0, int32_t nfields,
@@ -782,13 +857,15 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     long long* dst[kMaxLevels + 1];
     dst[0] = reinterpret_cast<long long*>(counts_f);
     for (int t = 0; t < nlev; ++t) dst[1 + t] = reinterpret_cast<long long*>(counts_m) + (long long)t * bp.nbins;
-    rc = build_bin_table(p, bp, w.bintab, nfields, 1 + nlev, dst, s);
+    const unsigned short* tab = nullptr;
+    rc = bins_for_call(p, bp, w.bintab, nfields, 1 + nlev, dst, &tab, s);
     if (rc) return rc;
     const size_t esize = out_dtype == HUFIELD_BF16 ? 2 : 4;
     for (int e = 0; e < nfields; ++e) {
         void* fo = out_f ? reinterpret_cast<char*>(out_f) + (size_t)e * (size_t)p->N * esize : nullptr;
         int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * (size_t)p->N : nullptr;
-        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, w, s);
+        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, tab, w,
+                       s);
         if (rc) return rc;
     }
     return HUFIELD_OK;
@@ -950,3 +1027,192 @@ extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y,
     if (rc) return rc;
     return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, st.bintab, sums, nullptr, st.status, s);
 }
+
+// ---------------------------------------------------------------------------
+// Ragged batches (hufield_batch_*): one plan, stream and workspace slice per
+// size class; the whole batch is captured into one CUDA graph (classes as
+// parallel branches, items of a class in sequence) and replayed.
+// ---------------------------------------------------------------------------
+struct hufield_batch {
+    struct Class {
+        hufield_plan* plan = nullptr;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t join = nullptr;
+        std::vector<int> members;
+        size_t ws_off = 0, ws_bytes = 0;
+    };
+    std::vector<hufield_batch_item> items;
+    std::vector<Class> classes;
+    std::vector<long long> f_off, bin_off;
+    long long f_total = 0, bin_total = 0;
+    size_t ws_total = 0;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* key[8] = {};  // buffers the graph was captured with
+};
+
+namespace {
+
+void batch_free(hufield_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto& c : b->classes) {
+        if (c.plan) hufield_plan_destroy(c.plan);
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.join) cudaEventDestroy(c.join);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+bool same_dims(const hufield_dims& a, const hufield_dims& b) {
+    if (a.ndim != b.ndim) return false;
+    for (int d = 0; d < a.ndim; ++d)
+        if (a.n[d] != b.n[d]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int32_t n, uint32_t flags) {
+    if (!out || !items || n < 1 || flags != 0) return HUFIELD_ERR_INVALID_ARG;
+    *out = nullptr;
+    hufield_batch* b = new (std::nothrow) hufield_batch();
+    if (!b) return HUFIELD_ERR_CUDA;
+    b->items.assign(items, items + n);
+    std::vector<int> cls(n, -1);
+    std::vector<hufield_dims> cdims;
+    for (int i = 0; i < n; ++i) {
+        for (size_t c = 0; c < cdims.size(); ++c)
+            if (same_dims(cdims[c], items[i].dims)) cls[i] = (int)c;
+        if (cls[i] < 0) {
+            cls[i] = (int)cdims.size();
+            cdims.push_back(items[i].dims);
+        }
+    }
+    b->classes.resize(cdims.size());
+    int rc = HUFIELD_OK;
+    for (size_t c = 0; c < cdims.size() && rc == HUFIELD_OK; ++c) rc = hufield_plan_create(&b->classes[c].plan, &cdims[c], 0);
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    b->f_off.resize(n);
+    b->bin_off.resize(n);
+    std::vector<int> class_nr(b->classes.size(), 0);
+    std::vector<bool> uniform(b->classes.size(), true);
+    for (int i = 0; i < n; ++i) {
+        auto& C = b->classes[cls[i]];
+        const hufield_batch_item& it = items[i];
+        int crc = check_filter(C.plan, &it.filt);
+        if (!crc && !(isfinite(it.level))) crc = HUFIELD_ERR_INVALID_ARG;
+        BinParams bp;
+        if (!crc) crc = make_bins(C.plan, it.nr, 1, bp);
+        if (crc) {
+            batch_free(b);
+            return crc;
+        }
+        C.members.push_back(i);
+        b->f_off[i] = b->f_total;
+        b->bin_off[i] = b->bin_total;
+        b->f_total += C.plan->N;
+        b->bin_total += it.nr;
+        if (class_nr[cls[i]] == 0) class_nr[cls[i]] = it.nr;
+        if (class_nr[cls[i]] != it.nr) uniform[cls[i]] = false;
+        const size_t need = ws_bytes(C.plan, 1, it.nr);
+        if (need > C.ws_bytes) C.ws_bytes = need;
+    }
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        auto& C = b->classes[c];
+        C.ws_off = b->ws_total;
+        b->ws_total += align256(C.ws_bytes);
+        if (uniform[c] && hufield_plan_set_bins(C.plan, class_nr[c], 1) != HUFIELD_OK) rc = HUFIELD_ERR_CUDA;
+        if (cudaStreamCreateWithFlags(&C.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&C.join, cudaEventDisableTiming) != cudaSuccess)
+            rc = HUFIELD_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = HUFIELD_ERR_CUDA;
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return HUFIELD_OK;
+}
+
+int hufield_batch_layout(const hufield_batch* b, int64_t* f_offset, int64_t* bin_offset, int64_t totals[3]) {
+    if (!b) return HUFIELD_ERR_INVALID_ARG;
+    for (size_t i = 0; i < b->items.size(); ++i) {
+        if (f_offset) f_offset[i] = b->f_off[i];
+        if (bin_offset) bin_offset[i] = b->bin_off[i];
+    }
+    if (totals) {
+        totals[0] = b->f_total;
+        totals[1] = b->bin_total;
+        totals[2] = (int64_t)b->ws_total;
+    }
+    return HUFIELD_OK;
+}
+
+int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* sums_f, int64_t* counts_f,
+                      double* sums_m, int64_t* counts_m, void* ws, size_t bytes, void* stream) {
+    if (!b || !sums_f || !counts_f || !sums_m || !counts_m || !ws) return HUFIELD_ERR_INVALID_ARG;
+    if (!aligned(ws) || (out_f && !aligned(out_f)) || (out_maps && !aligned(out_maps))) return HUFIELD_ERR_INVALID_ARG;
+    if (bytes < b->ws_total) return HUFIELD_ERR_WS_TOO_SMALL;
+    const void* key[8] = {out_f, out_maps, sums_f, counts_f, sums_m, counts_m, ws, (const void*)bytes};
+    bool same = b->exec != nullptr;
+    for (int k = 0; k < 8 && same; ++k) same = key[k] == b->key[k];
+    if (!same) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        HF_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
+        int rc = cudaEventRecord(b->fork, b->origin) == cudaSuccess ? HUFIELD_OK : HUFIELD_ERR_CUDA;
+        for (auto& C : b->classes) {
+            if (rc) break;
+            if (cudaStreamWaitEvent(C.stream, b->fork, 0) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
+            for (int i : C.members) {
+                if (rc) break;
+                const hufield_batch_item& it = b->items[i];
+                const long long fo = b->f_off[i], bo = b->bin_off[i];
+                rc = hufield_ensemble(C.plan, &it.filt, it.seed, it.field_idx, 1, HUFIELD_F32, out_f ? out_f + fo : nullptr,
+                                      &it.level, 1, out_maps ? out_maps + fo : nullptr, it.nr, 1, 0, sums_f + bo,
+                                      counts_f + bo, sums_m + bo, counts_m + bo,
+                                      reinterpret_cast<char*>(ws) + C.ws_off, C.ws_bytes, C.stream);
+            }
+            if (!rc && (cudaEventRecord(C.join, C.stream) != cudaSuccess ||
+                        cudaStreamWaitEvent(b->origin, C.join, 0) != cudaSuccess))
+                rc = HUFIELD_ERR_CUDA;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);
+        if (rc || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : HUFIELD_ERR_CUDA;
+        }
+        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return HUFIELD_ERR_CUDA;
+        }
+        b->graph = g;
+        for (int k = 0; k < 8; ++k) b->key[k] = key[k];
+    }
+    HF_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return HUFIELD_OK;
+}
+
+int hufield_batch_destroy(hufield_batch* b) {
+    if (!b) return HUFIELD_ERR_INVALID_ARG;
+    batch_free(b);
+    return HUFIELD_OK;
+}
+
+}  // extern "C"

@@ -93,10 +93,9 @@ __device__ __forceinline__ float amplitude_from_sum(const FilterParams& fp, floa
     if (!(S > 0.0f)) return 0.0f;
     const float log2K = log2f(S) * fp.inv_p;
     const float K = exp2f(log2K);
-    // (K - k0)^2 - (K* - k0)^2 = (K - K*)(K + K* - 2 k0)
+    // (K - k0)^2 - (K* - k0)^2 = (K - K*)(K + K* - 2 k0); A = exp(ln(chi) / 2) as one power of two
     const float d = (K - fp.kstar) * (K + fp.kstar - fp.two_k0);
-    const float half_lnchi = fp.half_s_ln2 * (log2K - fp.log2_kstar) - d * fp.inv_2w2 * 0.5f;
-    return expf(half_lnchi);
+    return exp2f(fmaf(fp.half_s, log2K - fp.log2_kstar, -fp.c_d * d));
 }
 
 // A(kappa) for a rotated filter (the norm is not separable).

@@ -43,6 +43,11 @@ class _Filter(C.Structure):
                 ("nyquist", C.c_int32)]
 
 
+class _BatchItem(C.Structure):
+    _fields_ = [("dims", _Dims), ("filt", _Filter), ("seed", C.c_uint64), ("field_idx", C.c_uint32),
+                ("level", C.c_float), ("nr", C.c_int32)]
+
+
 @dataclass
 class Filter:
     """hufield_filter: wavenumbers in units of the Nyquist wavenumber."""
@@ -96,6 +101,11 @@ def _load():
     lib.hufield_status_string.restype = C.c_char_p
     lib.hufield_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
     lib.hufield_workspace_status.argtypes = [vp, vp]
+    lib.hufield_plan_set_bins.argtypes = [vp, i32, i32]
+    lib.hufield_batch_plan.argtypes = [C.POINTER(vp), C.POINTER(_BatchItem), i32, u32]
+    lib.hufield_batch_layout.argtypes = [vp, vp, vp, vp]
+    lib.hufield_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.hufield_batch_destroy.argtypes = [vp]
     lib.hufield_profile_names.argtypes = []
     lib.hufield_profile_names.restype = C.c_char_p
     return lib
@@ -261,3 +271,52 @@ def hufield_spectrum_noalloc(shape, y: torch.Tensor, nr: int, ntheta: int, accum
 def hufield_workspace_status(ws: torch.Tensor, stream=None) -> int:
     """Status of the most recent call on `ws` (waits for the stream): OK or ERR_TIMEOUT."""
     return int(_lib.hufield_workspace_status(_ptr(ws), _stream(stream)))
+
+
+def hufield_plan_set_bins(plan: Plan, nr: int, ntheta: int = 1):
+    """Cache the bins of (nr, ntheta) in the plan (see include/hufield.h)."""
+    _check(_lib.hufield_plan_set_bins(plan.handle, nr, ntheta), "hufield_plan_set_bins")
+
+
+class Batch:
+    """hufield_batch: a ragged batch of fields run as one CUDA graph launch.
+
+    items: sequence of (shape, Filter, seed, field_idx, level, nr)."""
+
+    def __init__(self, items):
+        arr = (_BatchItem * len(items))()
+        for i, (shape, filt, seed, field_idx, level, nr) in enumerate(items):
+            shape = tuple(int(v) for v in shape)
+            arr[i].dims = _Dims(len(shape), 0, (C.c_int64 * 3)(*(shape + (1,) * (3 - len(shape)))))
+            arr[i].filt = filt._c()
+            arr[i].seed = seed
+            arr[i].field_idx = field_idx
+            arr[i].level = level
+            arr[i].nr = nr
+        h = C.c_void_p()
+        _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), 0), "hufield_batch_plan")
+        self._h = h
+        self.n = len(items)
+        f_off = (C.c_int64 * self.n)()
+        b_off = (C.c_int64 * self.n)()
+        tot = (C.c_int64 * 3)()
+        _check(_lib.hufield_batch_layout(h, f_off, b_off, tot), "hufield_batch_layout")
+        self.f_offset = list(f_off)
+        self.bin_offset = list(b_off)
+        self.total_voxels, self.total_bins, self.ws_bytes = tot[0], tot[1], tot[2]
+
+    def close(self):
+        if self._h:
+            _lib.hufield_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hufield_batch_run(batch: Batch, out_f, out_maps, sums_f, counts_f, sums_m, counts_m, ws, stream=None):
+    _check(_lib.hufield_batch_run(batch._h, _ptr(out_f), _ptr(out_maps), _ptr(sums_f), _ptr(counts_f), _ptr(sums_m),
+                                  _ptr(counts_m), _ptr(ws), ws.numel(), _stream(stream)), "hufield_batch_run")

@@ -1,0 +1,61 @@
+"""Ragged batch (hufield_batch_*): every item of a batch of mixed 2D/3D
+lattices and filters matches the oracle, on the first run (graph capture) and
+on a replay."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests import inputs
+from tests.gpu_common import check_bins, check_field, check_maps, dev_zeros, filters, np_
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(16, 16), (32, 32), (64, 64), (8, 8, 8), (16, 16, 16), (32, 32, 32)]
+
+
+def _items(hf, count, seed):
+    rng = np.random.default_rng(seed)
+    items, oitems = [], []
+    for i in range(count):
+        shape = SHAPES[int(rng.integers(len(SHAPES)))]
+        fk = inputs.random_filter(len(shape), seed * 1000 + i)
+        gf, of = filters(hf, **fk)
+        level = float(np.float32(rng.uniform(-1, 1)))
+        nr = min(128, min(shape) // 2)
+        items.append((shape, gf, 7, i, level, nr))
+        oitems.append((shape, of, 7, i, level, nr))
+    return items, oitems
+
+
+def test_batch_matches_oracle_and_replays(hf):
+    items, oitems = _items(hf, 14, 1)
+    batch = hf.Batch(items)
+    out_f = dev_zeros(batch.total_voxels, torch.float32)
+    maps = dev_zeros(batch.total_voxels, torch.int8)
+    sf, cf = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
+    sm, cm = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+    for run in range(2):
+        out_f.zero_()
+        hf.hufield_batch_run(batch, out_f, maps, sf, cf, sm, cm, ws)
+        torch.cuda.synchronize()
+        f_all, m_all = np_(out_f), np_(maps)
+        for i, (shape, of, seed, field, level, nr) in enumerate(oitems):
+            N = int(np.prod(shape))
+            fo, bo = batch.f_offset[i], batch.bin_offset[i]
+            want = oracle.pipeline(shape, of, seed, field, levels=(level,), nr=nr, ntheta=1)
+            check_field(f_all[fo:fo + N].reshape(shape), want["f"])
+            flips = check_maps(m_all[fo:fo + N].reshape((1,) + shape), want["maps"], want["f"], (level,))
+            check_bins(np_(sf)[bo:bo + nr], want["sums_f"], np_(cf)[bo:bo + nr], want["counts_f"])
+            check_bins(np_(sm)[bo:bo + nr], want["sums_m"][0], np_(cm)[bo:bo + nr], want["counts_m"][0],
+                       flips=flips[0], N=N)
+    batch.close()
+
+
+def test_batch_rejects_bad_items(hf):
+    gf, _ = filters(hf, p=2.0, axes=(1.0, 1.0), k0=0.3, width=0.1, supp=2.0)
+    with pytest.raises(hf.HufieldError):
+        hf.Batch([((16, 16), gf, 0, 0, 0.0, 0)])
+    with pytest.raises(hf.HufieldError):
+        hf.Batch([((12, 16), gf, 0, 0, 0.0, 8)])

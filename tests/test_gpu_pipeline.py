@@ -120,3 +120,25 @@ def test_field_bins_equal_spectrum_of_stored_field(hf):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(np_(c), got["counts_f"])
     np.testing.assert_allclose(np_(s), got["sums_f"], rtol=2e-5, atol=1e-9 * got["sums_f"].max())
+
+
+@pytest.mark.parametrize("shape,nr,nt", [((128, 64), 16, 6), ((32, 16, 64), 16, 1)])
+def test_plan_cached_bins(hf, shape, nr, nt):
+    # bins cached at plan time give the same results as bins built per call;
+    # a call with other (nr, ntheta) falls back to building them
+    levels = (0.0, 0.5)
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C1 if len(shape) == 2 else inputs.C2))
+    plain = hf.Plan(shape)
+    cached = hf.Plan(shape)
+    hf.hufield_plan_set_bins(cached, nr, nt)
+    a = run_pipeline(hf, plain, gf, shape, 3, 1, levels, nr, nt, nfields=2)
+    b = run_pipeline(hf, cached, gf, shape, 3, 1, levels, nr, nt, nfields=2)
+    np.testing.assert_array_equal(a["counts_f"], b["counts_f"])
+    np.testing.assert_array_equal(a["counts_m"], b["counts_m"])
+    np.testing.assert_allclose(b["sums_f"], a["sums_f"], rtol=1e-6, atol=1e-9 * a["sums_f"].max())
+    np.testing.assert_allclose(b["sums_m"], a["sums_m"], rtol=1e-6)
+    want = oracle.pipeline(shape, of, 3, 2, levels=levels, nr=nr, ntheta=nt)
+    check_field(b["f"][1], want["f"])
+    other = run_pipeline(hf, cached, gf, shape, 3, 1, levels, nr // 2, nt, nfields=1)
+    want = oracle.pipeline(shape, of, 3, 1, levels=levels, nr=nr // 2, ntheta=nt)
+    check_bins(other["sums_f"], want["sums_f"], other["counts_f"], want["counts_f"])
