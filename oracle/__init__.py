@@ -114,6 +114,11 @@ def _lib():
             lib.or_spectrum_modes.argtypes = [C.c_int, i64p, f64p, f64p]
             lib.or_pipeline.argtypes = [C.c_int, i64p, fp, C.c_uint64, C.c_uint32, C.c_double, f64p, C.c_int,
                                         C.c_int, C.c_int, f64p, i8p, f64p, i64p, f64p, i64p]
+            lib.or_kspace_noise.argtypes = [C.c_int, i64p, C.c_uint64, C.c_uint32, f64p]
+            lib.or_generate_kspace.argtypes = [C.c_int, i64p, fp, C.c_uint64, C.c_uint32, C.c_double, f64p,
+                                               C.c_void_p]
+            lib.or_pipeline_noise.argtypes = [C.c_int, i64p, fp, C.c_uint64, C.c_uint32, C.c_int, C.c_double,
+                                              f64p, C.c_int, C.c_int, C.c_int, f64p, i8p, f64p, i64p, f64p, i64p]
             lib.or_noise_dft_at.argtypes = [C.c_int, i64p, C.c_uint64, C.c_uint32, C.c_int, i64p, f64p]
             _LIB = lib
         return _LIB
@@ -177,13 +182,28 @@ def filter_grid(shape, filt: Filter) -> np.ndarray:
     return out.reshape(shape)
 
 
+def kspace_noise(shape, seed: int, field_idx: int = 0) -> np.ndarray:
+    """Hermitian k-space white-noise coefficients on the full lattice (FFT order)."""
+    N = int(np.prod(shape))
+    out = np.zeros(2 * N, np.float64)
+    _lib().or_kspace_noise(len(shape), _dims(shape), seed, field_idx, out)
+    return out.view(np.complex128).reshape(shape)
+
+
+def _noise_mode(noise: str) -> int:
+    if noise not in ("real", "kspace"):
+        raise ValueError(f"noise must be 'real' or 'kspace', not {noise!r}")
+    return 1 if noise == "kspace" else 0
+
+
 def generate(shape, filt: Filter, seed: int, field_idx: int = 0, sigma_f: float = 1.0,
-             return_spectrum: bool = False):
+             return_spectrum: bool = False, noise: str = "real"):
     N = int(np.prod(shape))
     f = np.zeros(N, np.float64)
     spec = np.zeros(2 * N, np.float64) if return_spectrum else None
-    _lib().or_generate(len(shape), _dims(shape), C.byref(filt._c()), seed, field_idx, sigma_f, f,
-                       spec.ctypes.data if spec is not None else None)
+    fn = _lib().or_generate_kspace if _noise_mode(noise) else _lib().or_generate
+    fn(len(shape), _dims(shape), C.byref(filt._c()), seed, field_idx, sigma_f, f,
+       spec.ctypes.data if spec is not None else None)
     if return_spectrum:
         return f.reshape(shape), spec.view(np.complex128).reshape(shape)
     return f.reshape(shape)
@@ -231,7 +251,7 @@ def spectrum_modes(y: np.ndarray) -> np.ndarray:
 
 
 def pipeline(shape, filt: Filter, seed: int, field_idx: int = 0, levels=(0.0,), nr: int = 128,
-             ntheta: int = 1, sigma_f: float = 1.0):
+             ntheta: int = 1, sigma_f: float = 1.0, noise: str = "real"):
     """Field, sign maps, binned S of the field and of each map (all FP64)."""
     N = int(np.prod(shape))
     nlev = len(levels)
@@ -243,8 +263,8 @@ def pipeline(shape, filt: Filter, seed: int, field_idx: int = 0, levels=(0.0,), 
     sm = np.zeros(max(nlev, 1) * nb, np.float64)
     cm = np.zeros(max(nlev, 1) * nb, np.int64)
     lev = np.ascontiguousarray(np.asarray(levels, dtype=np.float64).reshape(-1)) if nlev else np.zeros(1)
-    _lib().or_pipeline(len(shape), _dims(shape), C.byref(filt._c()), seed, field_idx, sigma_f, lev, nlev,
-                       nr, ntheta, f, maps, sf, cf, sm, cm)
+    _lib().or_pipeline_noise(len(shape), _dims(shape), C.byref(filt._c()), seed, field_idx, _noise_mode(noise),
+                             sigma_f, lev, nlev, nr, ntheta, f, maps, sf, cf, sm, cm)
     return {
         "f": f.reshape(shape),
         "maps": maps[: nlev * N].reshape((nlev,) + tuple(shape)),

@@ -12,7 +12,9 @@
  * fusion or reordering:
  *   noise      white noise on the real lattice (Sec. II.B: i.i.d. Gaussian
  *              coefficients; a forward FFT of real white noise gives them
- *              with the Hermitian pairing a real field needs)
+ *              with the Hermitian pairing a real field needs), or drawn
+ *              directly as Hermitian complex Gaussian coefficients in
+ *              k-space (the literal form of the same sentence)
  *   fft        own iterative radix-2 complex DFT, applied axis by axis
  *   filter     A(k) = sqrt(chi(k)), Eq. (8); chi from the generalized
  *              superellipse norm, Eq. (12), and the target spectrum, Eq. (13)
@@ -270,16 +272,12 @@ void or_filter_grid(int ndim, const int64_t *n, const or_filter *f, double *H) {
 /* normalise (Eq. (15)).  Outputs the normalised field f (length N) and,    */
 /* when spec != NULL, the filtered spectrum A F (interleaved complex).      */
 /* ------------------------------------------------------------------------ */
-void or_generate(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, uint32_t field_idx,
-                 double sigma_f, double *out_f, double *spec) {
+/* Filter the spectrum a (interleaved complex, overwritten), invert and
+ * normalise: the steps after the noise's coefficients are known. */
+static void filter_inverse_normalise(int ndim, const int64_t *n, const or_filter *f, double sigma_f, double *a,
+                                     double *out_f, double *spec) {
     int64_t N = 1;
     for (int d = 0; d < ndim; ++d) N *= n[d];
-    double *z = (double *)malloc(sizeof(double) * N);
-    double *a = (double *)malloc(sizeof(double) * 2 * N);
-    or_noise(N, seed, field_idx, z);
-    for (int64_t i = 0; i < N; ++i) { a[2 * i] = z[i]; a[2 * i + 1] = 0.0; }
-    free(z);
-    or_fftn(ndim, n, a, -1);
     double *H = (double *)malloc(sizeof(double) * N);
     or_filter_grid(ndim, n, f, H);
     for (int64_t i = 0; i < N; ++i) { a[2 * i] *= H[i]; a[2 * i + 1] *= H[i]; }
@@ -298,6 +296,19 @@ void or_generate(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, 
     var /= (double)N;
     double scale = sigma_f / sqrt(var);
     for (int64_t i = 0; i < N; ++i) out_f[i] = (a[2 * i] / (double)N - mean) * scale;
+}
+
+void or_generate(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, uint32_t field_idx,
+                 double sigma_f, double *out_f, double *spec) {
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    double *z = (double *)malloc(sizeof(double) * N);
+    double *a = (double *)malloc(sizeof(double) * 2 * N);
+    or_noise(N, seed, field_idx, z);
+    for (int64_t i = 0; i < N; ++i) { a[2 * i] = z[i]; a[2 * i + 1] = 0.0; }
+    free(z);
+    or_fftn(ndim, n, a, -1);
+    filter_inverse_normalise(ndim, n, f, sigma_f, a, out_f, spec);
     free(a);
 }
 
@@ -325,6 +336,104 @@ void or_inverse_realness(int ndim, const int64_t *n, const or_filter *f, uint64_
 /* Sign map, Sec. II.B: f >= t gives +1, else -1. */
 void or_threshold(int64_t N, const double *f, double t, int8_t *m) {
     for (int64_t i = 0; i < N; ++i) m[i] = f[i] >= t ? (int8_t)1 : (int8_t)-1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* k-space white noise: the Fourier coefficients of real white noise drawn   */
+/* directly (Sec. II.B: i.i.d. complex Gaussian coefficients on the lattice, */
+/* paired so that the field is real), instead of a forward DFT of real-space */
+/* noise.  Same distribution, different numbers.                            */
+/*                                                                           */
+/* Half-spectrum mode q, in r2c order q = row (N_last/2 + 1) + k_last (row   */
+/* the C-order index over the other axes, all indices in [0, N_d)), takes    */
+/* Philox block q >> 1 with counter (q>>1 lo, q>>1 hi, field_idx, 1): the    */
+/* pair (x0, x1) for even q, (x2, x3) for odd q, u = (x + 1/2) 2^-32,        */
+/* Z = sqrt(-2 ln u_a) exp(2 pi i u_b) and X = sqrt(N/2) Z, so E|X|^2 = N as */
+/* for the DFT of unit white noise.  On the planes k_last = 0 and            */
+/* k_last = N_last/2 the mode -n lies in the same half: the one with the     */
+/* smaller q is drawn and the other is its conjugate; a self-conjugate mode  */
+/* (every component 0 or N_d/2) is real, sqrt(N) Re Z.  Every other mode of  */
+/* the full lattice is the conjugate of its mirror in the half.              */
+/* ------------------------------------------------------------------------ */
+static void kspace_draw(uint64_t seed, uint32_t field_idx, uint64_t q, double N, double *re, double *im) {
+    uint32_t ctr[4] = {(uint32_t)(q >> 1), (uint32_t)(q >> 33), field_idx, 1u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    or_philox4x32_10(ctr, key, x);
+    int pair = (int)(q & 1);
+    double u0 = ((double)x[2 * pair] + 0.5) * ldexp(1.0, -32);
+    double u1 = ((double)x[2 * pair + 1] + 0.5) * ldexp(1.0, -32);
+    double r = sqrt(-2.0 * log(u0));
+    double amp = sqrt(N / 2.0);
+    *re = amp * r * cos(2.0 * OR_PI * u1);
+    *im = amp * r * sin(2.0 * OR_PI * u1);
+}
+
+/* Half-spectrum index of a mode with k_last = idx[ndim-1] <= N_last/2. */
+static uint64_t half_index(int ndim, const int64_t *n, const int64_t *idx) {
+    uint64_t row = 0;
+    for (int d = 0; d < ndim - 1; ++d) row = row * (uint64_t)n[d] + (uint64_t)idx[d];
+    return row * (uint64_t)(n[ndim - 1] / 2 + 1) + (uint64_t)idx[ndim - 1];
+}
+
+/* Coefficient of a mode in the half (k_last <= N_last/2). */
+static void kspace_half_value(int ndim, const int64_t *n, const int64_t *idx, uint64_t seed, uint32_t field_idx,
+                              double N, double *re, double *im) {
+    int64_t kl = idx[ndim - 1], half = n[ndim - 1] / 2;
+    uint64_t q = half_index(ndim, n, idx);
+    if (kl != 0 && kl != half) {
+        kspace_draw(seed, field_idx, q, N, re, im);
+        return;
+    }
+    int64_t mirror[3];
+    for (int d = 0; d < ndim; ++d) mirror[d] = (n[d] - idx[d]) % n[d];
+    uint64_t qm = half_index(ndim, n, mirror);
+    if (qm < q) {
+        kspace_draw(seed, field_idx, qm, N, re, im);
+        *im = -*im;
+    } else if (qm == q) {
+        kspace_draw(seed, field_idx, q, N, re, im);
+        *re *= sqrt(2.0);
+        *im = 0.0;
+    } else {
+        kspace_draw(seed, field_idx, q, N, re, im);
+    }
+}
+
+/* The full lattice of k-space noise coefficients, interleaved complex. */
+void or_kspace_noise(int ndim, const int64_t *n, uint64_t seed, uint32_t field_idx, double *X) {
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+#pragma omp parallel for schedule(static)
+    for (int64_t lin = 0; lin < N; ++lin) {
+        int64_t idx[3] = {0, 0, 0};
+        unravel(ndim, n, lin, idx);
+        for (int d = 0; d < ndim; ++d) idx[d] = (idx[d] + n[d]) % n[d];  /* unsigned indices */
+        double re, im;
+        if (idx[ndim - 1] <= n[ndim - 1] / 2) {
+            kspace_half_value(ndim, n, idx, seed, field_idx, (double)N, &re, &im);
+        } else {
+            int64_t mirror[3];
+            for (int d = 0; d < ndim; ++d) mirror[d] = (n[d] - idx[d]) % n[d];
+            kspace_half_value(ndim, n, mirror, seed, field_idx, (double)N, &re, &im);
+            im = -im;
+        }
+        X[2 * lin] = re;
+        X[2 * lin + 1] = im;
+    }
+}
+
+/* or_generate with k-space noise: the coefficients above take the place of
+ * the forward DFT of the real-space noise; filter, inverse and
+ * normalisation are the same steps. */
+void or_generate_kspace(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, uint32_t field_idx,
+                        double sigma_f, double *out_f, double *spec) {
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    double *a = (double *)malloc(sizeof(double) * 2 * N);
+    or_kspace_noise(ndim, n, seed, field_idx, a);
+    filter_inverse_normalise(ndim, n, f, sigma_f, a, out_f, spec);
+    free(a);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -414,14 +523,18 @@ void or_spectrum_modes(int ndim, const int64_t *n, const double *y, double *S) {
     free(a);
 }
 
-/* Full pipeline: f, nlev sign maps, binned S of f and of every map. */
-void or_pipeline(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, uint32_t field_idx,
-                 double sigma_f, const double *levels, int nlev, int nr, int ntheta,
-                 double *out_f, int8_t *out_maps, double *sums_f, int64_t *counts_f,
-                 double *sums_m, int64_t *counts_m) {
+/* Full pipeline: f, nlev sign maps, binned S of f and of every map; the
+ * noise is drawn in real space (kspace = 0) or in k-space (kspace = 1). */
+void or_pipeline_noise(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, uint32_t field_idx,
+                       int kspace, double sigma_f, const double *levels, int nlev, int nr, int ntheta,
+                       double *out_f, int8_t *out_maps, double *sums_f, int64_t *counts_f,
+                       double *sums_m, int64_t *counts_m) {
     int64_t N = 1;
     for (int d = 0; d < ndim; ++d) N *= n[d];
-    or_generate(ndim, n, f, seed, field_idx, sigma_f, out_f, NULL);
+    if (kspace)
+        or_generate_kspace(ndim, n, f, seed, field_idx, sigma_f, out_f, NULL);
+    else
+        or_generate(ndim, n, f, seed, field_idx, sigma_f, out_f, NULL);
     or_spectrum_bins(ndim, n, out_f, nr, ntheta, sums_f, counts_f);
     double *mv = (double *)malloc(sizeof(double) * N);
     int nb = nr * ntheta;
@@ -432,6 +545,14 @@ void or_pipeline(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, 
         or_spectrum_bins(ndim, n, mv, nr, ntheta, sums_m + (int64_t)t * nb, counts_m + (int64_t)t * nb);
     }
     free(mv);
+}
+
+void or_pipeline(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, uint32_t field_idx,
+                 double sigma_f, const double *levels, int nlev, int nr, int ntheta,
+                 double *out_f, int8_t *out_maps, double *sums_f, int64_t *counts_f,
+                 double *sums_m, int64_t *counts_m) {
+    or_pipeline_noise(ndim, n, f, seed, field_idx, 0, sigma_f, levels, nlev, nr, ntheta, out_f, out_maps, sums_f,
+                      counts_f, sums_m, counts_m);
 }
 
 /* Forward DFT of the noise at a list of modes, one by one from the
