@@ -344,23 +344,26 @@ void or_threshold(int64_t N, const double *f, double t, int8_t *m) {
 /* paired so that the field is real), instead of a forward DFT of real-space */
 /* noise.  Same distribution, different numbers.                            */
 /*                                                                           */
-/* Half-spectrum mode q, in r2c order q = row (N_last/2 + 1) + k_last (row   */
-/* the C-order index over the other axes, all indices in [0, N_d)), takes    */
-/* Philox block q >> 1 with counter (q>>1 lo, q>>1 hi, field_idx, 1): the    */
-/* pair (x0, x1) for even q, (x2, x3) for odd q, u = (x + 1/2) 2^-32,        */
-/* Z = sqrt(-2 ln u_a) exp(2 pi i u_b) and X = sqrt(N/2) Z, so E|X|^2 = N as */
-/* for the DFT of unit white noise.  On the planes k_last = 0 and            */
-/* k_last = N_last/2 the mode -n lies in the same half: the one with the     */
-/* smaller q is drawn and the other is its conjugate; a self-conjugate mode  */
-/* (every component 0 or N_d/2) is real, sqrt(N) Re Z.  Every other mode of  */
-/* the full lattice is the conjugate of its mirror in the half.              */
+/* Half-spectrum mode (row, k_last), row the C-order index over the other   */
+/* axes and k_last in [0, N_last/2] (all indices in [0, N_d)), takes Philox  */
+/* block J = row (N_last/4 + 1) + (k_last >> 1) with counter (J lo, J hi,    */
+/* field_idx, 1): the pair (x0, x1) for even k_last, (x2, x3) for odd,       */
+/* u = (x + 1/2) 2^-32, Z = sqrt(-2 ln u_a) exp(2 pi i u_b) and              */
+/* X = sqrt(N/2) Z, so E|X|^2 = N as for the DFT of unit white noise.  On    */
+/* the planes k_last = 0 and k_last = N_last/2 the mode -n lies in the same  */
+/* half: the one with the smaller row is drawn and the other is its          */
+/* conjugate; a self-conjugate mode (every component 0 or N_d/2) is real,    */
+/* sqrt(N) Re Z.  Every other mode of the full lattice is the conjugate of   */
+/* its mirror in the half.                                                   */
 /* ------------------------------------------------------------------------ */
-static void kspace_draw(uint64_t seed, uint32_t field_idx, uint64_t q, double N, double *re, double *im) {
-    uint32_t ctr[4] = {(uint32_t)(q >> 1), (uint32_t)(q >> 33), field_idx, 1u};
+static void kspace_draw(uint64_t seed, uint32_t field_idx, uint64_t row, int64_t kl, int64_t nlast, double N,
+                        double *re, double *im) {
+    uint64_t J = row * (uint64_t)(nlast / 4 + 1) + (uint64_t)(kl >> 1);
+    uint32_t ctr[4] = {(uint32_t)J, (uint32_t)(J >> 32), field_idx, 1u};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t x[4];
     or_philox4x32_10(ctr, key, x);
-    int pair = (int)(q & 1);
+    int pair = (int)(kl & 1);
     double u0 = ((double)x[2 * pair] + 0.5) * ldexp(1.0, -32);
     double u1 = ((double)x[2 * pair + 1] + 0.5) * ldexp(1.0, -32);
     double r = sqrt(-2.0 * log(u0));
@@ -369,34 +372,34 @@ static void kspace_draw(uint64_t seed, uint32_t field_idx, uint64_t q, double N,
     *im = amp * r * sin(2.0 * OR_PI * u1);
 }
 
-/* Half-spectrum index of a mode with k_last = idx[ndim-1] <= N_last/2. */
-static uint64_t half_index(int ndim, const int64_t *n, const int64_t *idx) {
+/* C-order index over every axis but the last. */
+static uint64_t row_index(int ndim, const int64_t *n, const int64_t *idx) {
     uint64_t row = 0;
     for (int d = 0; d < ndim - 1; ++d) row = row * (uint64_t)n[d] + (uint64_t)idx[d];
-    return row * (uint64_t)(n[ndim - 1] / 2 + 1) + (uint64_t)idx[ndim - 1];
+    return row;
 }
 
 /* Coefficient of a mode in the half (k_last <= N_last/2). */
 static void kspace_half_value(int ndim, const int64_t *n, const int64_t *idx, uint64_t seed, uint32_t field_idx,
                               double N, double *re, double *im) {
-    int64_t kl = idx[ndim - 1], half = n[ndim - 1] / 2;
-    uint64_t q = half_index(ndim, n, idx);
-    if (kl != 0 && kl != half) {
-        kspace_draw(seed, field_idx, q, N, re, im);
+    int64_t kl = idx[ndim - 1], nlast = n[ndim - 1];
+    uint64_t row = row_index(ndim, n, idx);
+    if (kl != 0 && kl != nlast / 2) {
+        kspace_draw(seed, field_idx, row, kl, nlast, N, re, im);
         return;
     }
     int64_t mirror[3];
     for (int d = 0; d < ndim; ++d) mirror[d] = (n[d] - idx[d]) % n[d];
-    uint64_t qm = half_index(ndim, n, mirror);
-    if (qm < q) {
-        kspace_draw(seed, field_idx, qm, N, re, im);
+    uint64_t rm = row_index(ndim, n, mirror);
+    if (rm < row) {
+        kspace_draw(seed, field_idx, rm, kl, nlast, N, re, im);
         *im = -*im;
-    } else if (qm == q) {
-        kspace_draw(seed, field_idx, q, N, re, im);
+    } else if (rm == row) {
+        kspace_draw(seed, field_idx, row, kl, nlast, N, re, im);
         *re *= sqrt(2.0);
         *im = 0.0;
     } else {
-        kspace_draw(seed, field_idx, q, N, re, im);
+        kspace_draw(seed, field_idx, row, kl, nlast, N, re, im);
     }
 }
 

@@ -33,37 +33,43 @@ def test_hermitian_pairing_gives_a_real_field(shape):
 
 def test_half_spectrum_draw_closed_form():
     # interior modes of the half: |X|^2 / (N/2) = -2 ln u_a and arg X = 2 pi u_b, with
-    # (u_a, u_b) the first pair of Philox block q >> 1 for even q, the second for odd q
-    shape = (8, 16)
-    N, half = 128, 8
-    X = oracle.kspace_noise(shape, seed=0x1234_5678_9ABC, field_idx=3)
-    key = [(0x1234_5678_9ABC) & 0xFFFFFFFF, (0x1234_5678_9ABC) >> 32]
-    for n0 in range(8):
-        for kl in range(1, half):
-            q = n0 * (half + 1) + kl
-            x = oracle.philox4x32_10([q >> 1, 0, 3, 1], key).astype(np.float64)
-            u = (x + 0.5) / 2.0 ** 32
-            ua, ub = (u[0], u[1]) if q % 2 == 0 else (u[2], u[3])
-            z = X[n0, kl]
-            assert abs(abs(z) ** 2 / (N / 2) - (-2.0 * math.log(ua))) < 1e-12 * max(1.0, abs(z) ** 2)
-            d = np.angle(z * np.exp(-2j * np.pi * ub))
-            assert abs(d) < 1e-12
+    # (u_a, u_b) the first pair of Philox block J = row (N_last/4 + 1) + k_last // 2
+    # (counter word 3 = 1) for even k_last, the second for odd k_last
+    seed = 0x1234_5678_9ABC
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for shape in ((8, 16), (4, 8, 32)):
+        N, nlast = int(np.prod(shape)), shape[-1]
+        X = oracle.kspace_noise(shape, seed=seed, field_idx=3)
+        for idx in np.ndindex(*shape[:-1]):
+            row = int(np.ravel_multi_index(idx, shape[:-1]))
+            for kl in range(1, nlast // 2):
+                J = row * (nlast // 4 + 1) + kl // 2
+                x = oracle.philox4x32_10([J, 0, 3, 1], key).astype(np.float64)
+                u = (x + 0.5) / 2.0 ** 32
+                ua, ub = (u[0], u[1]) if kl % 2 == 0 else (u[2], u[3])
+                z = X[idx + (kl,)]
+                assert abs(abs(z) ** 2 / (N / 2) - (-2.0 * math.log(ua))) < 1e-12 * max(1.0, abs(z) ** 2)
+                assert abs(np.angle(z * np.exp(-2j * np.pi * ub))) < 1e-12
 
 
-def test_hermitian_plane_takes_the_smaller_index():
-    # on k_last = 0 the mode with the smaller half-spectrum index is the drawn one
+def test_hermitian_plane_takes_the_smaller_row():
+    # on k_last = 0 the mode with the smaller row index is the drawn one
     shape = (8, 16)
     X = oracle.kspace_noise(shape, seed=2)
     key = [2, 0]
     for n0 in (1, 2, 3):
-        q = n0 * 9
-        x = oracle.philox4x32_10([q >> 1, 0, 0, 1], key).astype(np.float64)
+        J = n0 * 5
+        x = oracle.philox4x32_10([J, 0, 0, 1], key).astype(np.float64)
         u = (x + 0.5) / 2.0 ** 32
-        ua, ub = (u[0], u[1]) if q % 2 == 0 else (u[2], u[3])
-        r = math.sqrt(64.0) * math.sqrt(-2.0 * math.log(ua))
-        want = r * np.exp(2j * np.pi * ub)
+        r = math.sqrt(64.0) * math.sqrt(-2.0 * math.log(u[0]))
+        want = r * np.exp(2j * np.pi * u[1])
         assert abs(X[n0, 0] - want) < 1e-12 * r
         assert abs(X[8 - n0, 0] - np.conj(want)) < 1e-12 * r
+    # self-conjugate (4, 0): sqrt(N) Re Z of its own draw
+    x = oracle.philox4x32_10([4 * 5, 0, 0, 1], key).astype(np.float64)
+    u = (x + 0.5) / 2.0 ** 32
+    want = math.sqrt(128.0) * math.sqrt(-2.0 * math.log(u[0])) * math.cos(2 * math.pi * u[1])
+    assert abs(X[4, 0] - want) < 1e-12 * max(1.0, abs(want))
 
 
 def test_moments_of_the_coefficients():
