@@ -48,20 +48,21 @@ TRAFFIC = {}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
-def algorithmic_bytes(shape, nlev, field_bytes=4):
+def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False):
     """Bytes each pass kind must move per launch (one field), by the pass plan:
     r2c writes the half spectrum (4 B/voxel); a strided pass reads and writes it
-    (8 B/voxel per spectrum); c2r reads it, writes the field, nlev sign maps and
-    nlev map spectra; the bins pass reads the nlev map spectra; the binning
-    passes read the bin table (1 B/voxel each time), which the table pass
-    ("counts") writes once per call."""
+    (8 B/voxel per spectrum; the filter pass of k-space noise only writes it);
+    c2r reads it, writes the field, nlev sign maps and nlev map spectra; the
+    bins pass reads the nlev map spectra; the binning passes read the bin table
+    (1 B/voxel each time), which the table pass ("counts") writes once per
+    call."""
     N = math.prod(shape)
     h = 4 * N  # half spectrum bytes
     tab = N  # bin table: one uint16 per half-spectrum mode
     return {
         "r2c": h,
         "cols_mid_fwd": 2 * h,
-        "cols_filter": 2 * h + tab,
+        "cols_filter": (1 if kspace else 2) * h + tab,
         "cols_mid_inv": 2 * h,
         "c2r": h + field_bytes * N + nlev * N + nlev * h,
         "cols_mid_maps": 2 * h * nlev,
@@ -143,13 +144,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_sample(wl, nfields_total):
+def cpu_oracle_sample(wl, nfields_total, noise="real"):
     """The FP64 oracle on one field of the workload (a bounded sample)."""
     import oracle
 
     of = oracle.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
     t0 = time.perf_counter()
-    oracle.pipeline(wl["shape"], of, 0, 0, levels=wl["levels"], nr=wl["nr"], ntheta=wl["ntheta"])
+    oracle.pipeline(wl["shape"], of, 0, 0, levels=wl["levels"], nr=wl["nr"], ntheta=wl["ntheta"], noise=noise)
     dt = time.perf_counter() - t0
     N = math.prod(wl["shape"])
     return {"value": N / dt, "unit": "voxels/s", "cores": oracle.num_threads(), "kind": "oracle",
@@ -170,7 +171,8 @@ def run_reference(args, wl, name):
         of = oracle.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"],
                            supp=wl["supp"])
         t0 = time.perf_counter()
-        oracle.pipeline(wl["shape"], of, i, 0, levels=wl["levels"], nr=wl["nr"], ntheta=wl["ntheta"])
+        oracle.pipeline(wl["shape"], of, i, 0, levels=wl["levels"], nr=wl["nr"], ntheta=wl["ntheta"],
+                        noise=args.noise)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     tot = sum(times)
@@ -179,7 +181,8 @@ def run_reference(args, wl, name):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "shape": list(wl["shape"]), "step_sample": "1 field per step"},
+            "config": {"workload": name, "shape": list(wl["shape"]), "noise": args.noise,
+                       "step_sample": "1 field per step"},
             "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
                              "sample": f"1 field of {'x'.join(map(str, wl['shape']))} per step"},
             "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -198,6 +201,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
     ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
+    ap.add_argument("--noise", default="real", choices=["real", "kspace"],
+                    help="white noise in real space (forward FFT) or drawn as k-space coefficients")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.fields > 0:
@@ -237,7 +242,7 @@ def main():
         del r2
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(wl, wl["nfields"])
+        cpu = cpu_oracle_sample(wl, wl["nfields"], args.noise)
     if rank == 0:
         shape, nlev = wl["shape"], len(wl["levels"])
         line = {"metric": METRIC, "value": res["value"], "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
@@ -245,7 +250,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "shape": list(shape), "fields_per_step": wl["nfields"],
                            "levels": list(wl["levels"]), "bins": [wl["nr"], wl["ntheta"]],
-                           "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
+                           "noise": args.noise, "l2": "flushed between timed steps",
+                           "parallelism": f"replicas x{world}"},
                 "roofline": res["roofline"],
                 "pipeline": res["pipeline"],
                 "passes": res["passes"],
@@ -269,7 +275,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     N = math.prod(shape)
     fdt = torch.float32 if args.dtype == "f32" else torch.bfloat16
     filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
-    plan = hf.Plan(shape, profile=True)
+    plan = hf.Plan(shape, profile=True, kspace=args.noise == "kspace")
     hf.hufield_plan_set_bins(plan, nr, nt)  # plan-time bin table and counts, as a production caller would
     ws = plan.workspace(nlev, nb)
     out_f = torch.empty((nf,) + tuple(shape), dtype=fdt, device="cuda")
@@ -323,7 +329,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     value = world * args.steps * nf * N / (tot_ms / 1e3)
 
     # roofline of the dominant pass (live per-launch CUDA-event times of the timed steps)
-    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2)
+    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2, args.noise == "kspace")
     peak, peak_kind = peaks()
     passes = {}
     for k, (ms, cnt) in prof.items():

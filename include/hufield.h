@@ -83,6 +83,21 @@ typedef struct hufield_plan hufield_plan;
  * workspace status word (see hufield_workspace_status).  Outputs are then
  * undefined.  Not for production use. */
 #define HUFIELD_PLAN_INJECT_TIMEOUT 2u
+/* Plan flag: draw the white noise directly as its Fourier coefficients
+ * (Sec. II.B: i.i.d. complex Gaussian coefficients on the lattice, paired
+ * X(-n) = conj X(n) so that the field is real) instead of as real-space noise
+ * followed by a forward FFT.  The field has the same distribution but other
+ * numbers, and the path skips every forward pass.  Half-spectrum mode
+ * (row, k_last), row the C-order index over the axes before the last, takes
+ * Philox4x32-10 block J = row (n_last/4 + 1) + (k_last >> 1) with key = seed
+ * and counter (J lo, J hi, field_idx, 1): words (x0, x1) for even k_last,
+ * (x2, x3) for odd, u = (x + 1/2) 2^-32 and X = sqrt(N/2) sqrt(-2 ln u_a)
+ * exp(2 pi i u_b).  On k_last = 0 the mode whose mirror -n has the smaller
+ * row is the mirror's conjugate; a self-conjugate mode is sqrt(N) times the
+ * real part of its unit draw.  Affects hufield_generate, hufield_pipeline and
+ * hufield_ensemble; hufield_noise and hufield_forward keep the real-space
+ * noise. */
+#define HUFIELD_PLAN_KSPACE_NOISE 4u
 
 typedef struct {
     int32_t ndim;   /* 2 or 3 */
@@ -91,8 +106,8 @@ typedef struct {
 } hufield_dims;
 
 typedef struct {
-    float p;        /* superellipse exponent, Eq. (12); p > 0 */
-    float axes[3];  /* semi-axes a, b, c of Eq. (12); > 0 (axes[2] ignored in 2D) */
+    float p;        /* superellipse exponent, Eq. (12); 0 < p <= 1024 */
+    float axes[3];  /* semi-axes a, b, c of Eq. (12); in [2^-20, 2^20] (axes[2] ignored in 2D) */
     float rot;      /* rotation of the semi-axes in the 0-1 plane, radians */
     float k0;       /* band centre in units of k_Nyquist (ignored when form = 1) */
     float width;    /* Gaussian width w (sigma of Eq. 13) in units of k_Nyquist; > 0 */
@@ -104,8 +119,9 @@ typedef struct {
 
 /* Plan for one lattice.  Allocates the twiddle table on the current CUDA
  * device and chooses launch shapes; the plan must be used on that device.
- * flags is 0 or a combination of HUFIELD_PLAN_PROFILE and
- * HUFIELD_PLAN_INJECT_TIMEOUT.  Returns HUFIELD_ERR_UNSUPPORTED_DIMS
+ * flags is 0 or a combination of HUFIELD_PLAN_PROFILE,
+ * HUFIELD_PLAN_INJECT_TIMEOUT and HUFIELD_PLAN_KSPACE_NOISE (any other bit:
+ * HUFIELD_ERR_INVALID_ARG).  Returns HUFIELD_ERR_UNSUPPORTED_DIMS
  * for a lattice outside the set above. */
 int hufield_plan_create(hufield_plan **plan, const hufield_dims *dims, uint32_t flags);
 int hufield_plan_destroy(hufield_plan *plan);

@@ -116,13 +116,33 @@ struct Plan {
     static constexpr int last_radix() { return radix(NS - 1); }
 };
 
+// Stage twiddle tables of a plan.  Stage s >= 1 (Ns = 2^log2_before(s), radix
+// R) reads W_{Ns R}^{k r}, k = j mod Ns, r = 1..R-1; its table holds that value
+// at [r Ns + k] (r-major), so the lanes of a warp, which differ in k, read
+// consecutive or identical words: no bank conflicts.
+template <int LOG2L, bool REV>
+struct TwTables {
+    using P = Plan<LOG2L, REV>;
+    static constexpr int stage_size(int s) { return 1 << (P::log2_before(s) + P::bits(s)); }
+    static constexpr int offset(int s) { return s <= 1 ? 0 : offset(s - 1) + stage_size(s - 1); }
+    static constexpr int size() { return P::NS <= 1 ? 0 : offset(P::NS - 1) + stage_size(P::NS - 1); }
+};
+
+// True when a plan and its reverse have the same stages (one table serves both).
+template <int LOG2L>
+constexpr bool palindromic() {
+    using F = Plan<LOG2L, false>;
+    for (int s = 0; s < F::NS; ++s)
+        if (F::bits(s) != F::bits(F::NS - 1 - s)) return false;
+    return true;
+}
+
 // Elements per thread for a line length: 16, never more than the line itself.
 constexpr int elems_for(int log2l) { return log2l >= 4 ? 16 : (1 << log2l); }
 
 // Compile-time geometry of a CTA: TB = 2^LOGTB lines of L = 2^LOG2L, E
-// elements per thread, T threads.  TWLOG: log2 of the length of the CTA's
-// twiddle table W_{2^TWLOG}^q in shared memory (>= LOG2L).
-template <int LOG2L_, int LOGTB_, bool ROW_, int TWLOG_>
+// elements per thread, T threads.
+template <int LOG2L_, int LOGTB_, bool ROW_>
 struct Geo {
     static constexpr int LOG2L = LOG2L_;
     static constexpr int L = 1 << LOG2L_;
@@ -131,9 +151,7 @@ struct Geo {
     static constexpr bool ROW = ROW_;
     static constexpr int E = elems_for(LOG2L_);
     static constexpr int T = (TB * L) / E;
-    static constexpr int TWLOG = TWLOG_;
     static_assert(T >= 1 && T <= 512, "threads per CTA");
-    static_assert(TWLOG_ >= LOG2L_, "twiddle table too short");
 };
 
 // Butterfly (line b, index j) of a thread's i-th radix-2^LR butterfly.
@@ -177,6 +195,14 @@ __device__ __forceinline__ void for_each_element(int t, F&& f) {
     }
 }
 
+// Position l of element e, known only at run time, in the layout of
+// for_each_element<G, R> for the COL geometry.
+template <class G, int R>
+__device__ __forceinline__ int col_element_l(int t, int e) {
+    static_assert(!G::ROW, "column geometry");
+    return ((t + G::T * (e / R)) >> G::LOGTB) + (e % R) * (G::L / R);
+}
+
 template <class G, int DIR, bool REV, int S>
 struct Stages {
     using P = Plan<G::LOG2L, REV>;
@@ -189,8 +215,8 @@ struct Stages {
     __device__ __forceinline__ static void run(float2 (&v)[E], float2* sm, const float2* tw, int t) {
         constexpr int NB = E / R;
         if constexpr (LNS > 0) {
-            // twiddles W_{Ns R}^{k r} = tw[k r 2^TWLOG / (Ns R)], k = j mod Ns
-            constexpr int shift = G::TWLOG - (LNS + LR);
+            // twiddles W_{Ns R}^{k r}, k = j mod Ns, from the stage's r-major table
+            constexpr int off = TwTables<G::LOG2L, REV>::offset(S);
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
                 int b, j;
@@ -198,7 +224,7 @@ struct Stages {
                 const int k = j & ((1 << LNS) - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = tw[(k * r) << shift];
+                    const float2 w = tw[off + (r << LNS) + k];
                     v[i * R + r] = DIR < 0 ? cmul(v[i * R + r], w) : cmulc(v[i * R + r], w);
                 }
             }
@@ -225,19 +251,54 @@ struct Stages {
 };
 
 // Full transform.  On entry v holds the plan's IN positions, on exit its OUT
-// positions.  sm (TB * L slots) holds the exchanges and tw the CTA's twiddle
-// table (shared memory); contains __syncthreads(), so every thread of the CTA
-// must call it.
+// positions.  sm (TB * L slots) holds the exchanges and tw the plan's stage
+// twiddle tables (shared memory, load_stage_twiddles); contains
+// __syncthreads(), so every thread of the CTA must call it.
 template <class G, int DIR, bool REV>
 __device__ __forceinline__ void fft(float2 (&v)[G::E], float2* sm, const float2* tw, int t) {
     Stages<G, DIR, REV, 0>::run(v, sm, tw, t);
 }
 
-// The CTA's twiddle table: tw_s[q] = W_{2^TWLOG}^q from the plan's 4096-entry
-// table, q < 2^TWLOG.
-template <class G>
-__device__ __forceinline__ void load_twiddles(float2* tw_s, const float2* __restrict__ tw, int t) {
-    for (int q = t; q < (1 << G::TWLOG); q += G::T) tw_s[q] = __ldg(tw + (q << (kTwLog2 - G::TWLOG)));
+// The twiddles of a packed real transform of length 2L: tw_s[k] = W_{2L}^k,
+// k < L, from the plan's 4096-entry table.
+template <int LOG2L>
+__device__ __forceinline__ void load_half_twiddles(float2* tw_s, const float2* __restrict__ tw, int t, int T) {
+    for (int k = t; k < (1 << LOG2L); k += T) tw_s[k] = __ldg(tw + (k << (kTwLog2 - LOG2L - 1)));
+}
+
+// The stage tables of plan (LOG2L, REV) from the plan's 4096-entry table.
+template <int LOG2L, bool REV, int S = 1>
+__device__ __forceinline__ void load_stage_twiddles(float2* tw_s, const float2* __restrict__ tw, int t, int T) {
+    using P = Plan<LOG2L, REV>;
+    if constexpr (S < P::NS) {
+        constexpr int lns = P::log2_before(S), lr = P::bits(S);
+        constexpr int off = TwTables<LOG2L, REV>::offset(S);
+        for (int q = t; q < (1 << (lns + lr)); q += T) {
+            const int r = q >> lns, k = q & ((1 << lns) - 1);
+            tw_s[off + q] = __ldg(tw + ((k * r) << (kTwLog2 - lns - lr)));
+        }
+        load_stage_twiddles<LOG2L, REV, S + 1>(tw_s, tw, t, T);
+    }
+}
+
+// Stage tables for the forward plan and its reverse: the reverse's start at
+// the returned pointer (the same tables when the plan is palindromic).
+template <int LOG2L>
+__device__ __forceinline__ float2* load_plan_twiddles(float2* tw_s, const float2* __restrict__ tw, int t, int T) {
+    load_stage_twiddles<LOG2L, false>(tw_s, tw, t, T);
+    if constexpr (palindromic<LOG2L>()) {
+        return tw_s;
+    } else {
+        float2* rev = tw_s + TwTables<LOG2L, false>::size();
+        load_stage_twiddles<LOG2L, true>(rev, tw, t, T);
+        return rev;
+    }
+}
+
+// Shared-memory slots of the stage tables of a plan and its reverse.
+template <int LOG2L>
+constexpr int plan_twiddle_slots() {
+    return TwTables<LOG2L, false>::size() + (palindromic<LOG2L>() ? 0 : TwTables<LOG2L, true>::size());
 }
 
 }  // namespace hf

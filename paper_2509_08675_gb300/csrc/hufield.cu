@@ -22,6 +22,7 @@ KernelInfo r2c_kernel_src(int log2m, bool big, int src);
 KernelInfo cols_kernel_plain(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_filter(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_bins(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_kspace(int log2l, bool big, int mode, int dir);
 
 KernelInfo r2c_kernel(int log2m, bool big, int src) {
     return src == kSrcNoise ? r2c_kernel_noise(log2m, big, src) : r2c_kernel_src(log2m, big, src);
@@ -30,6 +31,7 @@ KernelInfo cols_kernel(int log2l, bool big, int mode, int dir) {
     switch (mode) {
         case kModePlain: return cols_kernel_plain(log2l, big, mode, dir);
         case kModeFilter: return cols_kernel_filter(log2l, big, mode, dir);
+        case kModeKspace: return cols_kernel_kspace(log2l, big, mode, dir);
         default: return cols_kernel_bins(log2l, big, mode, dir);
     }
 }
@@ -207,6 +209,7 @@ struct hufield_plan {
     long long* cache_counts = nullptr;
     long long wait_budget = 0;                            // SM cycles per bounded mbarrier wait
     bool inject_timeout = false;                          // test hook (HUFIELD_PLAN_INJECT_TIMEOUT)
+    bool kspace = false;                                  // HUFIELD_PLAN_KSPACE_NOISE
 };
 
 namespace {
@@ -216,6 +219,12 @@ struct Launch {
     size_t smem = 0;
 };
 
+// Filter parameter ranges: the log-domain superellipse sum keeps every term
+// p log2 |kappa_i / a_i| far from its zero sentinel within these.
+constexpr float kMaxExponent = 1024.0f;
+constexpr float kMinAxis = 1.0f / 1048576.0f, kMaxAxis = 1048576.0f;
+// Resident CTAs per SM of the strided (column) passes.
+constexpr int kColCtasPerSm = 2;
 // Bound of one mbarrier wait: ~1 s at the GB300's 2.07 GHz SM clock.
 constexpr long long kWaitBudget = 2000000000ll;
 // Bound used by the timeout test hook (~2 ms).
@@ -240,7 +249,7 @@ int ilog2(long long v) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-int occupancy_grid(const void* fn, int block, size_t smem, long long work, int nsm) {
+int occupancy_grid(const void* fn, int block, size_t smem, long long work, int nsm, int cap = 0) {
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return 0;
@@ -248,6 +257,7 @@ int occupancy_grid(const void* fn, int block, size_t smem, long long work, int n
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess) return 0;
     if (per_sm <= 0) return 0;
+    if (cap > 0 && per_sm > cap) per_sm = cap;
     long long g = (long long)per_sm * nsm;
     if (g > work) g = work;
     return (int)(g < 1 ? 1 : g);
@@ -267,7 +277,10 @@ KernelInfo pick_row(int log2m, long long nrows, KernelInfo (*table)(int, bool, i
 }
 
 // Column kernels: tiles of TB columns x L rows, double-buffered in shared
-// memory; TB >= 2 keeps a TMA box row at 16 bytes or more.
+// memory; TB >= 2 keeps a TMA box row at 16 bytes or more.  At most two CTAs
+// per SM: with more, the tiles in flight (and the lines the L2 fetches
+// around them) outgrow the L2 and the strided passes re-read HBM (measured
+// on 512^3: 0.208 ms per pass at two CTAs, 0.248 ms at three).
 bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, size_t extra_smem,
                 KernelInfo& k, Launch& L) {
     const bool big = B >= (1ll << col_logtb(log2l, true));
@@ -275,12 +288,15 @@ bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
     L.smem = k.fixed_smem + extra_smem;
-    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm);
+    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm, kColCtasPerSm);
     return L.grid > 0;
 }
 
 // Tensor map over data viewed as (B, L, A) 8-byte elements with row stride B
-// and batch stride bstride elements; box (TB, min(L, 256), 1).
+// and batch stride bstride elements; box (TB, min(L, 256), 1).  The L2 fetches
+// 128 bytes around each box row of 64 bytes or more (the next tile's columns,
+// which the same CTA loads next) and 64 bytes around narrower ones (a 4096^2
+// spectrum is L2-resident; wider fetches there only add traffic).
 bool col_map(const hufield_plan* p, CUtensorMap* map, void* data, long long B, int log2l, long long A,
              long long bstride, int logTB) {
     const cuuint64_t dims[3] = {(cuuint64_t)B, (cuuint64_t)1 << log2l, (cuuint64_t)A};
@@ -288,7 +304,9 @@ bool col_map(const hufield_plan* p, CUtensorMap* map, void* data, long long B, i
     const cuuint32_t box[3] = {(cuuint32_t)1 << logTB, (cuuint32_t)(log2l < 8 ? 1 << log2l : 256), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return p->encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, data, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     (sizeof(float2) << logTB) >= 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                     : CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -328,10 +346,11 @@ int check_filter(const hufield_plan* p, const hufield_filter* f) {
     const float vals[] = {f->p, f->axes[0], f->axes[1], f->axes[2], f->rot, f->k0, f->width, f->supp, f->sigma_f};
     for (float v : vals)
         if (!finite(v)) return HUFIELD_ERR_INVALID_ARG;
-    if (!(f->p > 0.0f) || !(f->width > 0.0f) || !(f->supp >= 0.0f) || !(f->sigma_f > 0.0f))
+    if (!(f->p > 0.0f) || !(f->p <= kMaxExponent) || !(f->width > 0.0f) || !(f->supp >= 0.0f) ||
+        !(f->sigma_f > 0.0f))
         return HUFIELD_ERR_INVALID_ARG;
     for (int d = 0; d < p->ndim; ++d)
-        if (!(f->axes[d] > 0.0f)) return HUFIELD_ERR_INVALID_ARG;
+        if (!(f->axes[d] >= kMinAxis) || !(f->axes[d] <= kMaxAxis)) return HUFIELD_ERR_INVALID_ARG;
     if (f->form != 0 && f->form != 1) return HUFIELD_ERR_INVALID_ARG;
     if (f->nyquist != 0) return HUFIELD_ERR_INVALID_ARG;
     return HUFIELD_OK;
@@ -474,8 +493,11 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
 // Strided pass along axis 0 over `nbatch` spectra of N/2 modes each.
 int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const FilterParams* fp,
                const BinParams& bp, const unsigned short* bintab, double* gbins, double* gP, unsigned* status,
-               cudaStream_t s) {
+               cudaStream_t s, uint64_t seed = 0, uint32_t field_idx = 0) {
     ColArgs ca{};
+    ca.seed = seed;
+    ca.field_idx = field_idx;
+    ca.kscale = (float)sqrt(0.5 * (double)p->N);
     ca.status = status;
     ca.wait_budget = p->wait_budget;
     ca.inject_skip = p->inject_timeout ? 1 : 0;
@@ -495,13 +517,17 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     ca.scale = (float)(1.0 / (double)p->N);
     const size_t extra = mode == kModePlain ? 0
                                             : (size_t)(bp.nbins + 1) * (sizeof(double) + sizeof(float)) +
-                                                  (mode == kModeFilter ? sizeof(float) << p->log2n[0] : 0);
+                                                  (mode == kModeFilter || mode == kModeKspace
+                                                       ? sizeof(float) << p->log2n[0]
+                                                       : 0);
     Launch L;
     KernelInfo k;
     if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, extra, k, L)) return HUFIELD_ERR_CUDA;
     ca.ntiles = ca.A * (ca.B >> k.log2_lines);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
-    const int kind = mode == kModeFilter ? kPassFilter : mode == kModeBins ? kPassBins : kPassMidFwd;
+    const int kind = (mode == kModeFilter || mode == kModeKspace) ? kPassFilter
+                     : mode == kModeBins                           ? kPassBins
+                                                                   : kPassMidFwd;
     HF_CUDA(launch(p, kind, k.fn, L, &ca, s));
     return HUFIELD_OK;
 }
@@ -570,9 +596,15 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     none.ntheta = 1;
     const BinParams& b = bp ? *bp : none;
     HF_CUDA(cudaMemsetAsync(w.P, 0, sizeof(double) * (size_t)(1 + b.nbins), s));
-    int rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
-    if (rc) return rc;
-    rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, w.raw, w.P, w.status, s);
+    int rc;
+    if (p->kspace) {
+        // the noise coefficients are drawn inside the axis-0 pass: no forward passes
+        rc = axis0_pass(p, kModeKspace, w.spec, 1, &fp, b, tab, w.raw, w.P, w.status, s, seed, field_idx);
+    } else {
+        rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
+        if (rc) return rc;
+        rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, w.raw, w.P, w.status, s);
+    }
     if (rc) return rc;
     if (p->ndim == 3) {
         rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s);
@@ -640,7 +672,8 @@ const char* hufield_status_string(int status) {
 }
 
 int hufield_plan_create(hufield_plan** out, const hufield_dims* dims, uint32_t flags) {
-    if (!out || !dims || (flags & ~(HUFIELD_PLAN_PROFILE | HUFIELD_PLAN_INJECT_TIMEOUT)) != 0)
+    if (!out || !dims ||
+        (flags & ~(HUFIELD_PLAN_PROFILE | HUFIELD_PLAN_INJECT_TIMEOUT | HUFIELD_PLAN_KSPACE_NOISE)) != 0)
         return HUFIELD_ERR_INVALID_ARG;
     *out = nullptr;
     if (dims->ndim != 2 && dims->ndim != 3) return HUFIELD_ERR_UNSUPPORTED_DIMS;
@@ -655,6 +688,7 @@ int hufield_plan_create(hufield_plan** out, const hufield_dims* dims, uint32_t f
     if (!p) return HUFIELD_ERR_CUDA;
     p->profile = (flags & HUFIELD_PLAN_PROFILE) != 0;
     p->inject_timeout = (flags & HUFIELD_PLAN_INJECT_TIMEOUT) != 0;
+    p->kspace = (flags & HUFIELD_PLAN_KSPACE_NOISE) != 0;
     p->wait_budget = p->inject_timeout ? kInjectWaitBudget : kWaitBudget;
     p->encode = encode_entry();
     if (!p->encode) {

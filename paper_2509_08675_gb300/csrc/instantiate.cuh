@@ -9,16 +9,16 @@ namespace hf {
 
 template <int LOG2M, int LOGTR, int SRC>
 KernelInfo r2c_info() {
-    using G = Geo<LOG2M, LOGTR, true, LOG2M + 1>;
+    using G = Geo<LOG2M, LOGTR, true>;
     return {reinterpret_cast<const void*>(&k_r2c<LOG2M, LOGTR, SRC>), G::T, LOGTR,
-            (size_t)G::TB * G::L * 8 + (size_t)2 * G::L * 8};
+            (size_t)G::TB * G::L * 8 + (size_t)G::L * 8 + (size_t)TwTables<LOG2M, false>::size() * 8};
 }
 
 template <int LOG2M, int LOGTR, int OUTDT>
 KernelInfo c2r_info() {
-    using G = Geo<LOG2M, LOGTR, true, LOG2M + 1>;
+    using G = Geo<LOG2M, LOGTR, true>;
     return {reinterpret_cast<const void*>(&k_c2r<LOG2M, LOGTR, OUTDT>), G::T, LOGTR,
-            (size_t)2 * G::TB * G::L * 8 + (size_t)2 * G::L * 8 + 16};
+            (size_t)2 * G::TB * G::L * 8 + (size_t)G::L * 8 + (size_t)plan_twiddle_slots<LOG2M>() * 8 + 16};
 }
 
 template <int LOG2L, int LOGTB, int MODE, int DIR>

@@ -25,7 +25,7 @@
 namespace hf {
 
 enum NoiseSource { kSrcNoise = 0, kSrcF32 = 1, kSrcBF16 = 2, kSrcI8 = 3 };
-enum ColMode { kModePlain = 0, kModeFilter = 1, kModeBins = 2 };
+enum ColMode { kModePlain = 0, kModeFilter = 1, kModeBins = 2, kModeKspace = 3 };
 
 struct RowArgs {
     const void* src;        // real input rows (kSrcF32/BF16/I8)
@@ -74,6 +74,10 @@ struct ColArgs {
     unsigned* status;       // workspace status word (kStatusTimeout)
     long long wait_budget;  // clock cycles allowed per mbarrier wait
     int inject_skip;        // test hook: 1 = the first tile's load is never issued (its wait must time out)
+    // KSPACE: the noise coefficients are drawn in the pass instead of loaded
+    unsigned long long seed;
+    unsigned int field_idx;
+    float kscale;           // sqrt(N / 2)
 };
 
 // Minimum resident CTAs per SM asked of the compiler: keeps the kernels of
@@ -85,26 +89,59 @@ __device__ __forceinline__ int signed_index(int i, int log2n) {
     return i < (1 << (log2n - 1)) ? i : i - (1 << log2n);
 }
 
-// |t|^p for t >= 0 (one term of the superellipse sum, Eq. 12).
-__device__ __forceinline__ float pow_term(float t, float p) { return t > 0.0f ? exp2f(p * log2f(t)) : 0.0f; }
+// Filter amplitude, Eqs. (8), (12), (13), evaluated in the log domain so that
+// S = sum |kappa'_i / a_i|^p neither underflows nor overflows for any p: each
+// term enters as u_i = p log2 |kappa'_i / a_i| and log2 S = m + log2 sum
+// 2^(u_i - m), m = max u_i.  fast_lg2/fast_ex2 are the hardware
+// approximations (absolute error ~2^-22 in a log2, relative ~2^-22 in a power
+// of two).  A narrow band (small w) multiplies the relative error of K by
+// about 2 |K - k0| K / (w^2 ln 4) in log2 A, so K itself comes from the
+// library exp2f, and the per-axis terms that are tabulated (once per CTA or
+// tile) from log2f; an error in log2 S is divided by p in log2 K.
+constexpr float kLog2Zero = -1e30f;  // u of a zero term (kappa'_i = 0)
 
-// A = sqrt(chi) from S = K^p (Eqs. 8, 12, 13): zero at K = 0.
-__device__ __forceinline__ float amplitude_from_sum(const FilterParams& fp, float S) {
-    if (!(S > 0.0f)) return 0.0f;
-    const float log2K = log2f(S) * fp.inv_p;
+__device__ __forceinline__ float fast_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// u = p log2 t for t > 0; kLog2Zero for t = 0 (hardware log2; plog2_exact: library log2f).
+__device__ __forceinline__ float plog2(float t, float p) { return t > 0.0f ? p * fast_lg2(t) : kLog2Zero; }
+__device__ __forceinline__ float plog2_exact(float t, float p) { return t > 0.0f ? p * log2f(t) : kLog2Zero; }
+
+// log2(2^a + 2^b) without forming either power.
+__device__ __forceinline__ float log2_sum2(float a, float b) {
+    const float m = fmaxf(a, b);
+    return m + fast_lg2(1.0f + fast_ex2(fminf(a, b) - m));
+}
+
+// A = sqrt(chi) from log2 S, S = K^p: zero at K = 0.  With
+// (K - k0)^2 - (K* - k0)^2 = (K - K*)(K + K* - 2 k0), A = exp(ln(chi) / 2) is
+// one power of two.
+__device__ __forceinline__ float amplitude_from_log2s(const FilterParams& fp, float l2s) {
+    if (l2s < 0.5f * kLog2Zero) return 0.0f;
+    const float log2K = l2s * fp.inv_p;
     const float K = exp2f(log2K);
-    // (K - k0)^2 - (K* - k0)^2 = (K - K*)(K + K* - 2 k0); A = exp(ln(chi) / 2) as one power of two
     const float d = (K - fp.kstar) * (K + fp.kstar - fp.two_k0);
-    return exp2f(fmaf(fp.half_s, log2K - fp.log2_kstar, -fp.c_d * d));
+    return fast_ex2(fmaf(fp.half_s, log2K - fp.log2_kstar, -fp.c_d * d));
 }
 
 // A(kappa) for a rotated filter (the norm is not separable).
 __device__ __forceinline__ float filter_amplitude(const FilterParams& fp, float x, float y, float z, int ndim) {
     const float xr = fmaf(fp.cr, x, fp.sr * y);
     const float yr = fmaf(fp.cr, y, -fp.sr * x);
-    float S = pow_term(fabsf(xr) * fp.inv_a[0], fp.p) + pow_term(fabsf(yr) * fp.inv_a[1], fp.p);
-    if (ndim == 3) S += pow_term(fabsf(z) * fp.inv_a[2], fp.p);
-    return amplitude_from_sum(fp, S);
+    const float u0 = plog2(fabsf(xr) * fp.inv_a[0], fp.p);
+    const float u1 = plog2(fabsf(yr) * fp.inv_a[1], fp.p);
+    const float u2 = ndim == 3 ? plog2(fabsf(z) * fp.inv_a[2], fp.p) : kLog2Zero;
+    const float m = fmaxf(fmaxf(u0, u1), u2);
+    if (m < 0.5f * kLog2Zero) return 0.0f;
+    return amplitude_from_log2s(fp, m + fast_lg2(fast_ex2(u0 - m) + fast_ex2(u1 - m) + fast_ex2(u2 - m)));
 }
 
 // ---------------------------------------------------------------------------
@@ -205,6 +242,18 @@ __device__ __forceinline__ void chunk_of(long long ntiles, long long& t0, long l
     t1 = ntiles * ((long long)blockIdx.x + 1) / G;
 }
 
+// k-space noise: Philox block J of counter word 3 = 1 gives the coefficients
+// of the mode pair (k_last even, k_last + 1) of one row, each sqrt(N/2) Z
+// with Z = sqrt(-2 ln u_a) exp(2 pi i u_b) from the pair's two words.
+__device__ __forceinline__ void kspace_pair(unsigned long long seed, unsigned int field_idx, float kscale,
+                                            unsigned long long J, float2& z0, float2& z1) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)J, (uint32_t)(J >> 32), field_idx, 1u), (uint32_t)seed,
+                                  (uint32_t)(seed >> 32));
+    const float4 z = box_muller(x);
+    z0 = make_float2(z.x * kscale, z.y * kscale);
+    z1 = make_float2(z.z * kscale, z.w * kscale);
+}
+
 // One elected thread polls the mbarrier (bounded); the CTA then agrees.
 // Returns false (for every thread) when the wait ran out.
 __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, long long budget) {
@@ -226,17 +275,19 @@ __device__ __forceinline__ float2 r2c_post(float2 Z, float2 Zm_conj, float2 w) {
 // Rows: real input -> half spectrum.
 // ---------------------------------------------------------------------------
 template <int LOG2M, int LOGTR, int SRC>
-__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blocks(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T))
+__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG2M, LOGTR, true>::T))
     k_r2c(const __grid_constant__ RowArgs a) {
-    using G = Geo<LOG2M, LOGTR, true, LOG2M + 1>;
+    using G = Geo<LOG2M, LOGTR, true>;
     constexpr int M = G::L;
     constexpr int E = G::E;
     using PF = Plan<LOG2M, false>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* sm = reinterpret_cast<float2*>(smem_raw);  // TR * M exchange
-    float2* tw = sm + G::TB * M;                        // 2M twiddles
+    float2* tw = sm + G::TB * M;                        // W_{2M}^k, k < M
+    float2* twf = tw + M;                               // stage tables of the forward plan
     const int t = threadIdx.x;
-    load_twiddles<G>(tw, a.tw, t);
+    load_half_twiddles<LOG2M>(tw, a.tw, t, G::T);
+    load_stage_twiddles<LOG2M, false>(twf, a.tw, t, G::T);
     long long t0, t1;
     chunk_of(a.nrows >> LOGTR, t0, t1);
     constexpr int nq = (G::TB * M) / 2;  // blocks of four reals per tile
@@ -268,7 +319,7 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
         __syncthreads();
         float2 v[E];
         for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int l) { v[e] = sm[smem_slot<G>(l, b)]; });
-        fft<G, -1, false>(v, sm, tw, t);
+        fft<G, -1, false>(v, sm, twf, t);
         __syncthreads();
         for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { sm[smem_slot<G>(l, b)] = v[e]; });
         __syncthreads();
@@ -286,9 +337,9 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
 // transformed; the current buffer then serves as the FFT exchange area.
 // ---------------------------------------------------------------------------
 template <int LOG2M, int LOGTR, int OUTDT>
-__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blocks(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T))
+__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG2M, LOGTR, true>::T))
     k_c2r(const __grid_constant__ C2RArgs a) {
-    using G = Geo<LOG2M, LOGTR, true, LOG2M + 1>;
+    using G = Geo<LOG2M, LOGTR, true>;
     constexpr int M = G::L;
     constexpr int E = G::E;
     using PF = Plan<LOG2M, false>;
@@ -296,8 +347,9 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int tile_elems = G::TB * M;
     float2* bufs[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw) + tile_elems};
-    float2* tw = bufs[1] + tile_elems;  // 2M twiddles
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + 2 * M);
+    float2* tw = bufs[1] + tile_elems;  // W_{2M}^k, k < M
+    float2* twf = tw + M;               // stage tables: forward plan, then its reverse
+    uint64_t* bar = reinterpret_cast<uint64_t*>(twf + plan_twiddle_slots<LOG2M>());
     constexpr uint32_t tile_bytes = (uint32_t)tile_elems * (uint32_t)sizeof(float2);
     const int t = threadIdx.x;
     // f = sigma_f * u / sqrt(sum |G|^2), u the unnormalised inverse (the mean
@@ -309,7 +361,8 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
         mbar_arrive_expect_tx(b, tile_bytes);
         bulk_load(dst, a.spec + tile * tile_elems, tile_bytes, b);
     };
-    load_twiddles<G>(tw, a.tw, t);
+    load_half_twiddles<LOG2M>(tw, a.tw, t, G::T);
+    float2* twi = load_plan_twiddles<LOG2M>(twf, a.tw, t, G::T);
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -346,7 +399,7 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
             const float2 op = cmulc(csub(X, Xmc), tw[k]);
             v[e] = cadd(ep, cmul_i<+1>(op));
         });
-        fft<G, +1, true>(v, buf, tw, t);
+        fft<G, +1, true>(v, buf, twi, t);
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = cscale(v[e], scale);
         // v[e] now holds f[2j], f[2j+1] of row b at the forward plan's input positions
@@ -374,7 +427,7 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
                     reinterpret_cast<char2*>(a.out_maps + (long long)lev * a.N)[(row0 + b) * M + j] = m;
                 });
             }
-            fft<G, -1, false>(u, buf, tw, t);
+            fft<G, -1, false>(u, buf, twf, t);
             __syncthreads();
             for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { buf[smem_slot<G>(l, b)] = u[e]; });
             __syncthreads();
@@ -409,16 +462,81 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true, LOG2M + 1>::T, min_blo
 // records kStatusTimeout in the workspace status word, drains its own copies
 // and returns.
 // ---------------------------------------------------------------------------
+// The k-space noise coefficients of a tile's modes, in the layout the
+// forward axis-0 FFT leaves (the inverse plan's input positions).  Mode
+// (n0, col) lies in row n0 A1 + n1 (A1 = N1, n1 = col >> logM in 3D; A1 = 1,
+// n1 = 0 in 2D) at k_last = col & (M - 1).  The columns 2c and 2c + 1 of a
+// row share a Philox block, and they sit in lanes t and t ^ 1 with the same
+// n0 in every slot: each lane draws the blocks of half of the slots and
+// hands the other column's coefficient to its neighbour.  On k_last = 0 the
+// mode whose mirror -n has the smaller row takes the conjugate of the
+// mirror's draw, and a self-conjugate mode keeps sqrt(2) times its real part.
+template <class G>
+__device__ __forceinline__ void kspace_tile(float2 (&v)[G::E], const ColArgs& a, int c0, int t) {
+    constexpr int E = G::E;
+    constexpr int L = G::L;
+    using PF = Plan<G::LOG2L, false>;
+    const int col = c0 + (t & (G::TB - 1));
+    const int h = col & 1;
+    const int M = 1 << a.logM;
+    const int n1 = col >> a.logM;
+    const int klast = col & (M - 1);
+    const int a1log = a.ndim == 3 ? a.log2n[1] : 0;
+    const unsigned long long bpr = (unsigned long long)(M / 2 + 1);  // Philox blocks per row
+    int ls[E];
+    for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { ls[e] = l; });
+    constexpr unsigned mask = G::T >= 32 ? 0xffffffffu : (1u << G::T) - 1u;
+#pragma unroll
+    for (int k = 0; k < E / 2; ++k) {
+        const int l = h ? ls[k + E / 2] : ls[k];
+        const unsigned long long row = ((unsigned long long)l << a1log) + (unsigned long long)n1;
+        float2 z0, z1;
+        kspace_pair(a.seed, a.field_idx, a.kscale, row * bpr + (unsigned long long)(klast >> 1), z0, z1);
+        const float2 mine = h ? z1 : z0;
+        const float2 other = h ? z0 : z1;
+        float2 recv;
+        recv.x = __shfl_xor_sync(mask, other.x, 1);
+        recv.y = __shfl_xor_sync(mask, other.y, 1);
+        v[k] = h ? recv : mine;
+        v[k + E / 2] = h ? mine : recv;
+    }
+    if (klast == 0) {
+        const int n1m = (-n1) & ((1 << a1log) - 1);
+        unsigned need = 0;  // bit e: the mirror's row is the smaller, draw it
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int lm = (-ls[e]) & (L - 1);
+            const unsigned long long row = ((unsigned long long)ls[e] << a1log) + (unsigned long long)n1;
+            const unsigned long long rowm = ((unsigned long long)lm << a1log) + (unsigned long long)n1m;
+            if (rowm < row) need |= 1u << e;
+            if (rowm == row) v[e] = make_float2(v[e].x * 1.41421356237309505f, 0.0f);
+        }
+        // one copy of the draw in the code (this branch is rare): loop over the set bits
+        while (need) {
+            const int e = __ffs(need) - 1;
+            need &= need - 1;
+            const int lm = (-col_element_l<G, PF::last_radix()>(threadIdx.x, e)) & (L - 1);
+            const unsigned long long rowm = ((unsigned long long)lm << a1log) + (unsigned long long)n1m;
+            float2 z0, z1;
+            kspace_pair(a.seed, a.field_idx, a.kscale, rowm * bpr, z0, z1);
+            const float2 w = cconj(z0);
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+                if (q == e) v[q] = w;
+        }
+    }
+}
+
 template <int LOG2L, int LOGTB>
 struct ColGeo {
-    using G = Geo<LOG2L, LOGTB, false, LOG2L>;
+    using G = Geo<LOG2L, LOGTB, false>;
     static constexpr int tile_elems = G::TB * G::L;
-    // dynamic shared memory before the bins: two tile buffers, the twiddles, two mbarriers
-    static constexpr size_t fixed_bytes = (size_t)2 * tile_elems * 8 + (size_t)G::L * 8 + 16;
+    // dynamic shared memory before the bins: two tile buffers, the stage twiddles, two mbarriers
+    static constexpr size_t fixed_bytes = (size_t)2 * tile_elems * 8 + (size_t)plan_twiddle_slots<LOG2L>() * 8 + 16;
 };
 
 template <int LOG2L, int LOGTB, int MODE, int DIR>
-__global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks(Geo<LOG2L, LOGTB, false, LOG2L>::T))
+__global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LOG2L, LOGTB, false>::T))
     k_cols(const __grid_constant__ ColArgs a) {
     using CG = ColGeo<LOG2L, LOGTB>;
     using G = typename CG::G;
@@ -431,15 +549,18 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
     using PI = Plan<LOG2L, true>;
     constexpr bool kAcc = MODE != kModePlain;
     constexpr bool kStore = MODE != kModeBins;
+    constexpr bool kFilt = MODE == kModeFilter || MODE == kModeKspace;
+    constexpr bool kLoad = MODE != kModeKspace;
+    static_assert(TB >= 2, "k-space mode pairs rely on two columns per tile");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int tile_elems = CG::tile_elems;
     float2* bufs[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw) + tile_elems};
-    float2* tw = bufs[1] + tile_elems;  // L twiddles
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
+    float2* twf = bufs[1] + tile_elems;  // stage tables: forward plan, then its reverse
+    uint64_t* bar = reinterpret_cast<uint64_t*>(twf + plan_twiddle_slots<LOG2L>());
     const int nb = a.bp.nbins;
     double* dbin = reinterpret_cast<double*>(bar + 2);   // nb + 1 (last: Parseval)
     float* fbin = reinterpret_cast<float*>(dbin + nb + 1);  // nb + 1
-    float* tab0 = fbin + nb + 1;                          // FILTER: |kappa_0 / a|^p, L
+    float* tab0 = fbin + nb + 1;                          // FILTER: p log2 |kappa_0 / a|, L
     const int t = threadIdx.x;
 
     long long t0, t1;
@@ -454,17 +575,17 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
         for (int y = 0; y < L; y += LB) tma_load_3d(dst + y * TB, &a.map, c0, y, (int)ab, b);
     };
 
-    load_twiddles<G>(tw, a.tw, t);
+    float2* twi = load_plan_twiddles<LOG2L>(twf, a.tw, t, T);
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    if constexpr (MODE == kModeFilter) {
+    if constexpr (kFilt) {
         if (!a.fp.rotated) {
             for (int l = t; l < L; l += T) {
                 const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                tab0[l] = l == L / 2 ? 0.0f : powf(fabsf(x) * a.fp.inv_a[0], a.fp.p);
+                tab0[l] = plog2_exact(fabsf(x) * a.fp.inv_a[0], a.fp.p);
             }
         }
     }
@@ -475,7 +596,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
         }
     }
     __syncthreads();
-    if (t == 0) {
+    if (kLoad && t == 0) {
         if (t0 < t1 && !a.inject_skip) issue(t0, bufs[0], &bar[0]);
         if (t0 + 1 < t1) issue(t0 + 1, bufs[1], &bar[1]);
     }
@@ -487,7 +608,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
             if (dbin[i] != 0.0) atomicAdd(g + i, dbin[i]);
             dbin[i] = 0.0;
         }
-        if (MODE == kModeFilter && t == 0) {
+        if (kFilt && t == 0) {
             atomicAdd(a.gP, dbin[nb]);
             dbin[nb] = 0.0;
         }
@@ -500,11 +621,18 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
     for (long long ti = t0; ti < t1; ++ti) {
         const int s = (int)((ti - t0) & 1);
         float2* buf = bufs[s];
-        if (!cta_wait(&bar[s], phase[s], a.wait_budget)) {
-            failed_at = ti;
-            break;
+        if constexpr (kLoad) {
+            if (!cta_wait(&bar[s], phase[s], a.wait_budget)) {
+                failed_at = ti;
+                break;
+            }
+            phase[s] ^= 1u;
+        } else {
+            // buf is free once the store of two tiles ago has read it; the
+            // barrier before the first write of buf (power staging) makes
+            // every thread wait for this
+            if (t == 0) bulk_wait_read_1();
         }
-        phase[s] ^= 1u;
         const long long ab = ti / tpb;
         const long long c0 = (ti - ab * tpb) << LOGTB;
         if constexpr (MODE == kModeBins) {
@@ -537,66 +665,77 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
         float2 v[E];
         if constexpr (MODE == kModePlain && DIR > 0) {
             for_each_element<G, PI::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
-            fft<G, +1, true>(v, buf, tw, t);
+            fft<G, +1, true>(v, buf, twi, t);
             __syncthreads();
             for_each_element<G, PI::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
         } else {
-            for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
-            fft<G, -1, false>(v, buf, tw, t);
+            if constexpr (MODE == kModeKspace) {
+                kspace_tile<G>(v, a, (int)c0, t);
+            } else {
+                for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
+                fft<G, -1, false>(v, buf, twf, t);
+            }
             if constexpr (MODE == kModePlain) {
                 __syncthreads();
                 for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
             } else {
-                if constexpr (MODE == kModeFilter) {
-                    // a thread's column is fixed: T is a multiple of TB
-                    const int col = (int)(c0 + (t & (TB - 1)));
+                // A thread's column is fixed (T is a multiple of TB), and so is
+                // the weight of its modes' power: 2 for the k_last > 0 half,
+                // where k and -k share a half-spectrum slot.
+                const int col = (int)(c0 + (t & (TB - 1)));
+                const int klast = a.ndim == 3 ? (col & ((1 << a.logM) - 1)) : col;
+                const float wcol = (klast == 0 ? 1.0f : 2.0f) * (MODE == kModeBins ? a.scale : 1.0f);
+                [[maybe_unused]] bool nyq_col = false;
+                [[maybe_unused]] float y = 0.0f, z = 0.0f, u_col = 0.0f;
+                if constexpr (kFilt) {
                     int n1, n2;
                     if (a.ndim == 3) {
                         n1 = signed_index(col >> a.logM, a.log2n[1]);
-                        n2 = col & ((1 << a.logM) - 1);
+                        n2 = klast;
                     } else {
                         n1 = col;
                         n2 = 0;
                     }
-                    const bool nyq_col = a.ndim == 3 && n1 == -(1 << (a.log2n[1] - 1));
-                    const float y = (float)n1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
-                    const float z = a.ndim == 3 ? (float)n2 * __int_as_float((127 + 1 - a.log2n[2]) << 23) : 0.0f;
-                    float s_col = 0.0f;  // separable case: the column's terms of the sum
-                    if (!a.fp.rotated) {
-                        s_col = powf(fabsf(y) * a.fp.inv_a[1], a.fp.p);
-                        if (a.ndim == 3) s_col += powf(fabsf(z) * a.fp.inv_a[2], a.fp.p);
-                    }
-                    for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) {
-                        float h = 0.0f;
-                        if (!nyq_col && l != L / 2) {
-                            if (!a.fp.rotated) {
-                                h = amplitude_from_sum(a.fp, tab0[l] + s_col);
-                            } else {
-                                const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                                h = filter_amplitude(a.fp, x, y, z, a.ndim);
-                            }
+                    nyq_col = a.ndim == 3 && n1 == -(1 << (a.log2n[1] - 1));
+                    y = (float)n1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
+                    z = a.ndim == 3 ? (float)n2 * __int_as_float((127 + 1 - a.log2n[2]) << 23) : 0.0f;
+                    if (!a.fp.rotated) {  // separable case: the column's terms of the sum
+                        u_col = plog2_exact(fabsf(y) * a.fp.inv_a[1], a.fp.p);
+                        if (a.ndim == 3) {
+                            const float u2 = plog2_exact(fabsf(z) * a.fp.inv_a[2], a.fp.p);
+                            const float m = fmaxf(u_col, u2);
+                            u_col = m + log2f(1.0f + exp2f(fminf(u_col, u2) - m));
                         }
-                        v[e] = cscale(v[e], h);
-                    });
+                    }
                 }
-                // Per-mode power (weight 2 for the k_last > 0 half) goes through
-                // shared memory so that each thread then owns E consecutive n0 of
-                // one column (element (b, l) to thread t = (b L + l) / E at slot
-                // i TS + t + t / 32, TS = T + T / 32: conflict-free both ways);
-                // their bins come precomputed from the bin table, and consecutive
-                // modes mostly share a bin, so one atomic per run of equal bins
-                // replaces one per mode.
+                // The filter (Eqs. 12-13) scales each mode; its power then goes
+                // through shared memory so that each thread owns E consecutive
+                // n0 of one column (element (b, l) to thread t = (b L + l) / E at
+                // slot i TS + t + t / 32, TS = T + T / 32: conflict-free both
+                // ways); their bins come precomputed from the bin table, and
+                // consecutive modes mostly share a bin, so one atomic per run of
+                // equal bins replaces one per mode.
                 constexpr int TS = T + (T >> 5);
                 static_assert(E * TS <= 2 * tile_elems, "power staging fits the tile buffer");
                 float pacc = 0.0f;
-                if (nb > 0 || MODE == kModeFilter) {
+                if (nb > 0 || kFilt) {
                     float* ps = reinterpret_cast<float*>(buf);
                     __syncthreads();  // the FFT's last exchange is read
                     for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) {
-                        const int col = (int)(c0 + b);
-                        const int klast = a.ndim == 3 ? (col & ((1 << a.logM) - 1)) : col;
-                        const float w = klast == 0 ? 1.0f : 2.0f;  // k and -k share a half-spectrum slot
-                        const float pw = (MODE == kModeBins ? w * a.scale : w) * cabs2(v[e]);
+                        if constexpr (kFilt) {
+                            float h = 0.0f;
+                            if (!nyq_col && l != L / 2) {
+                                if (!a.fp.rotated) {
+                                    h = amplitude_from_log2s(a.fp, log2_sum2(tab0[l], u_col));
+                                } else {
+                                    const float x =
+                                        (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                                    h = filter_amplitude(a.fp, x, y, z, a.ndim);
+                                }
+                            }
+                            v[e] = cscale(v[e], h);
+                        }
+                        const float pw = wcol * cabs2(v[e]);
                         pacc += pw;
                         const int flat = (b << LOG2L) + l;
                         const int owner = flat / E;
@@ -621,7 +760,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
                         if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
                     }
                 }
-                if constexpr (MODE == kModeFilter) {
+                if constexpr (kFilt) {
                     if constexpr (T >= 32) {
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
@@ -629,7 +768,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
                     } else {
                         atomicAdd(fbin + nb, pacc);
                     }
-                    fft<G, +1, true>(v, buf, tw, t);
+                    fft<G, +1, true>(v, buf, twi, t);
                     __syncthreads();
                     for_each_element<G, PI::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
                 }
@@ -644,7 +783,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
                 for (int y = 0; y < L; y += LB) tma_store_3d(&a.map, (int)c0, y, (int)ab, buf + y * TB);
                 bulk_commit();
             }
-            if (ti + 2 < t1) {
+            if (kLoad && ti + 2 < t1) {
                 if constexpr (kStore) bulk_wait_read_all();
                 issue(ti + 2, buf, &bar[s]);
             }
@@ -675,7 +814,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false, LOG2L>::T, min_blocks
     }
     if constexpr (MODE == kModeBins) {
         if (cur >= 0) flush(cur);
-    } else if constexpr (MODE == kModeFilter) {
+    } else if constexpr (kFilt) {
         flush(0);
     }
 }

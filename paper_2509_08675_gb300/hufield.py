@@ -22,6 +22,7 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEO
 F32, BF16, I8 = 0, 1, 2
 PLAN_PROFILE = 1
 PLAN_INJECT_TIMEOUT = 2
+PLAN_KSPACE_NOISE = 4
 MAX_LEVELS = 8
 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.int8: I8}
@@ -144,16 +145,18 @@ def _levels(levels):
 class Plan:
     """hufield_plan for one lattice shape (2D or 3D), created on the current device."""
 
-    def __init__(self, shape, profile: bool = False, inject_timeout: bool = False):
+    def __init__(self, shape, profile: bool = False, inject_timeout: bool = False, kspace: bool = False):
         self.shape = tuple(int(s) for s in shape)
         if len(self.shape) not in (2, 3):
             raise HufieldError(ERR_UNSUPPORTED_DIMS, "hufield_plan_create")
         dims = _Dims(len(self.shape), 0, (C.c_int64 * 3)(*(self.shape + (1,) * (3 - len(self.shape)))))
         h = C.c_void_p()
-        flags = (PLAN_PROFILE if profile else 0) | (PLAN_INJECT_TIMEOUT if inject_timeout else 0)
+        flags = ((PLAN_PROFILE if profile else 0) | (PLAN_INJECT_TIMEOUT if inject_timeout else 0)
+                 | (PLAN_KSPACE_NOISE if kspace else 0))
         _check(_lib.hufield_plan_create(C.byref(h), C.byref(dims), flags), "hufield_plan_create")
         self._h = h
         self.N = math.prod(self.shape)
+        self.kspace = kspace
 
     @property
     def handle(self):
@@ -175,8 +178,8 @@ class Plan:
         return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
 
-def hufield_plan_create(shape, profile: bool = False) -> Plan:
-    return Plan(shape, profile)
+def hufield_plan_create(shape, profile: bool = False, kspace: bool = False) -> Plan:
+    return Plan(shape, profile, kspace=kspace)
 
 
 def hufield_plan_destroy(plan: Plan):

@@ -19,7 +19,8 @@ def test_bad_filters_rejected(hf):
     ws = plan.workspace(0, 0)
     out = torch.empty((32, 32), device="cuda")
     bad = [dict(p=0.0), dict(p=float("nan")), dict(width=0.0), dict(supp=-1.0), dict(axes=(1.0, 0.0)),
-           dict(sigma_f=0.0), dict(k0=float("inf")), dict(form=2), dict(nyquist=1), dict(rot=float("nan"))]
+           dict(sigma_f=0.0), dict(k0=float("inf")), dict(form=2), dict(nyquist=1), dict(rot=float("nan")),
+           dict(p=1025.0), dict(axes=(1.0, 2.0 ** 21)), dict(axes=(2.0 ** -21, 1.0))]
     for kw in bad:
         with pytest.raises(hf.HufieldError) as e:
             hf.hufield_generate(plan, hf.Filter(**kw), 0, 0, out, ws)

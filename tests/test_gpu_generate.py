@@ -38,6 +38,31 @@ def test_generate_parity(hf, shape, fk):
     check_field(np_(out), want)
 
 
+# exponents across the paper's range (p from 0.5 to 50) and beyond: the terms
+# |kappa_i / a_i|^p of Eq. (12) span hundreds of decades at p = 50 (p = 100
+# keeps the FP64 oracle's terms above its underflow on these lattices)
+WIDE_P = [
+    ((256, 256), dict(p=0.5, axes=(1.0, 0.5), k0=0.2, width=0.05, supp=2.0)),
+    ((256, 256), dict(p=20.0, axes=(1.0, 0.5), k0=0.2, width=0.05, supp=2.0)),
+    ((256, 256), dict(p=50.0, axes=(1.0, 1.0), k0=0.15, width=0.04, supp=4.0)),
+    ((256, 256), dict(p=50.0, axes=(1.0, 0.5), rot=0.4, k0=0.15, width=0.04, supp=4.0)),
+    ((128, 128), dict(p=50.0, axes=(1.0, 1.0), width=0.05, supp=20.0, form=1)),
+    ((32, 64, 32), dict(p=30.0, axes=(1.0, 1.0, 0.5), k0=0.2, width=0.05, supp=2.0)),
+    ((32, 32, 32), dict(p=100.0, axes=(1.0, 2.0, 0.5), k0=0.3, width=0.08, supp=2.0)),
+]
+
+
+@pytest.mark.parametrize("shape,fk", WIDE_P, ids=lambda v: str(v.get("p")) if isinstance(v, dict) else None)
+def test_generate_wide_exponents(hf, shape, fk):
+    gf, of = filters(hf, **fk)
+    plan = hf.Plan(shape)
+    ws = plan.workspace(0, 0)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    hf.hufield_generate(plan, gf, 4, 1, out, ws)
+    torch.cuda.synchronize()
+    check_field(np_(out), oracle.generate(shape, of, 4, 1))
+
+
 @pytest.mark.parametrize("shape", [(256, 256), (32, 16, 64)])
 def test_generate_sigma_f_and_seeds(hf, shape):
     gf, of = filters(hf, p=3.0, axes=(1.0, 0.8, 1.2), k0=0.3, width=0.1, supp=2.0)
