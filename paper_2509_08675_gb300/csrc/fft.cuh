@@ -179,6 +179,24 @@ __device__ __forceinline__ int smem_slot(int l, int b) {
     }
 }
 
+// Slot of element l of line b in the exchange that follows a stage whose
+// outputs are SH bits apart at its largest stride (SH = log2(Ns R)).  ROW:
+// smem_slot.  COL: [l][b] with the bits of l that select a bank (the low
+// 4 - LOGTB bits, for 8-byte elements) XOR-ed by the bits of l from SH up.
+// A stage writes its outputs at (j / Ns) Ns R + (j mod Ns) + r Ns: when Ns is
+// below the lanes' span of j, the lanes' positions differ only from bit SH
+// up, and the XOR spreads them over the banks; the next stage reads runs of
+// consecutive l, which the XOR only permutes within 2^SH.
+template <class G, int SH>
+__device__ __forceinline__ int exchange_slot(int l, int b) {
+    if constexpr (G::ROW || G::LOGTB >= 4 || SH >= G::LOG2L) {
+        return smem_slot<G>(l, b);
+    } else {
+        constexpr int mask = (16 >> G::LOGTB) - 1;
+        return ((l ^ ((l >> SH) & mask)) << G::LOGTB) + b;
+    }
+}
+
 // Element positions of the data a thread holds before stage 0 (IN) or after
 // the last stage (OUT) of a plan: the i-th butterfly of radix R holds
 // elements j + r L/R, r = 0..R-1, in v[i R + r].
@@ -240,11 +258,11 @@ struct Stages {
                 const int k = j & ((1 << LNS) - 1);
                 const int base = ((j >> LNS) << (LNS + LR)) + k;
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[smem_slot<G>(base + (r << LNS), b)] = v[i * R + r];
+                for (int r = 0; r < R; ++r) sm[exchange_slot<G, LNS + LR>(base + (r << LNS), b)] = v[i * R + r];
             }
             __syncthreads();
             constexpr int R2 = P::radix(S + 1);
-            for_each_element<G, R2>(t, [&](int e, int b, int l) { v[e] = sm[smem_slot<G>(l, b)]; });
+            for_each_element<G, R2>(t, [&](int e, int b, int l) { v[e] = sm[exchange_slot<G, LNS + LR>(l, b)]; });
             Stages<G, DIR, REV, S + 1>::run(v, sm, tw, t);
         }
     }

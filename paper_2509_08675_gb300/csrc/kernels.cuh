@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     using PI = Plan<LOG2M, true>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int tile_elems = G::TB * M;
-    float2* bufs[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw) + tile_elems};
-    float2* tw = bufs[1] + tile_elems;  // W_{2M}^k, k < M
+    float2* const buf0 = reinterpret_cast<float2*>(smem_raw);  // two tile buffers: buf0 + s tile_elems
+    float2* tw = buf0 + 2 * tile_elems;  // W_{2M}^k, k < M
     float2* twf = tw + M;               // stage tables: forward plan, then its reverse
     uint64_t* bar = reinterpret_cast<uint64_t*>(twf + plan_twiddle_slots<LOG2M>());
     constexpr uint32_t tile_bytes = (uint32_t)tile_elems * (uint32_t)sizeof(float2);
@@ -370,19 +370,19 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     }
     __syncthreads();
     if (t == 0) {
-        if (t0 < t1 && !a.inject_skip) issue(t0, bufs[0], &bar[0]);
-        if (t0 + 1 < t1) issue(t0 + 1, bufs[1], &bar[1]);
+        if (t0 < t1 && !a.inject_skip) issue(t0, buf0, &bar[0]);
+        if (t0 + 1 < t1) issue(t0 + 1, buf0 + tile_elems, &bar[1]);
     }
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phases = 0u;  // bit s: parity of the next completion of bar[s]
     long long failed_at = -1;
     for (long long tile = t0; tile < t1; ++tile) {
         const int s = (int)((tile - t0) & 1);
-        float2* buf = bufs[s];
-        if (!cta_wait(&bar[s], phase[s], a.wait_budget)) {
+        float2* buf = buf0 + s * tile_elems;
+        if (!cta_wait(&bar[s], (phases >> s) & 1u, a.wait_budget)) {
             failed_at = tile;
             break;
         }
-        phase[s] ^= 1u;
+        phases ^= 1u << s;
         const long long row0 = tile << LOGTR;
         float2 v[E];
         // c2r pre-processing: Z[k] = (X[k] + X*[M-k]) + i (X[k] - X*[M-k]) W_N^{-k}
@@ -445,8 +445,8 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     if (failed_at >= 0 && t == 0) {
         atomicOr(a.status, kStatusTimeout);
         const int s = (int)((failed_at - t0) & 1);
-        if (!(a.inject_skip && failed_at == t0)) mbar_wait_bounded(&bar[s], phase[s], a.wait_budget);
-        if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1], a.wait_budget);
+        if (!(a.inject_skip && failed_at == t0)) mbar_wait_bounded(&bar[s], (phases >> s) & 1u, a.wait_budget);
+        if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], (phases >> (s ^ 1)) & 1u, a.wait_budget);
     }
 }
 
@@ -527,6 +527,57 @@ __device__ __forceinline__ void kspace_tile(float2 (&v)[G::E], const ColArgs& a,
     }
 }
 
+// Layout of the power staging (see k_cols): value i of thread o at slot
+// i TS + o + (o / 32) PAD.  TS = T + (T / 32) PAD + q exceeds the largest
+// o-part, so the map is one-to-one, and q makes TS = 1 mod 32 (reads, i fixed
+// and o running over a warp, are conflict-free for any PAD).  PAD in [0, 40)
+// is the one whose write pattern has the fewest bank conflicts, simulated at
+// compile time for the first warps of a tile, every element slot of the FFT's
+// output layout (radix R last), 4-byte words, 32 banks.
+template <class G>
+constexpr int staging_stride(int pad) {
+    if (G::T < 32) return G::T + 1;
+    const int base = G::T + (G::T / 32) * pad;
+    return base + (((1 - base) % 32) + 32) % 32;
+}
+template <class G, int R>
+constexpr int staging_cost(int pad) {
+    constexpr int T = G::T, E = G::E, L = G::L;
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    const int ts = staging_stride<G>(pad);
+    int cost = 0;
+    const int warps = T / 32 < 4 ? T / 32 : 4;
+    for (int w = 0; w < warps; ++w) {
+        for (int e = 0; e < E; ++e) {
+            int count[32] = {};
+            int worst = 0;
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = 32 * w + lane + T * (e >> LR);
+                const int b = g & (G::TB - 1), j = g >> G::LOGTB;
+                const int l = j + (e & (R - 1)) * (L / R);
+                const int flat = b * L + l, o = flat / E;
+                const int bank = ((flat % E) * ts + o + (o >> 5) * pad) & 31;
+                worst = ++count[bank] > worst ? count[bank] : worst;
+            }
+            cost += worst;
+        }
+    }
+    return cost;
+}
+template <class G, int R>
+constexpr int staging_pad() {
+    int best = 0, best_cost = staging_cost<G, R>(0);
+    for (int pad = 1; pad < 40 && G::T >= 32; ++pad) {
+        if (G::E * staging_stride<G>(pad) > 2 * G::TB * G::L) break;  // must fit the tile buffer (2 x float)
+        const int c = staging_cost<G, R>(pad);
+        if (c < best_cost) {
+            best = pad;
+            best_cost = c;
+        }
+    }
+    return best;
+}
+
 template <int LOG2L, int LOGTB>
 struct ColGeo {
     using G = Geo<LOG2L, LOGTB, false>;
@@ -554,8 +605,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
     static_assert(TB >= 2, "k-space mode pairs rely on two columns per tile");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int tile_elems = CG::tile_elems;
-    float2* bufs[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw) + tile_elems};
-    float2* twf = bufs[1] + tile_elems;  // stage tables: forward plan, then its reverse
+    float2* const buf0 = reinterpret_cast<float2*>(smem_raw);  // two tile buffers: buf0 + s tile_elems
+    float2* twf = buf0 + 2 * tile_elems;  // stage tables: forward plan, then its reverse
     uint64_t* bar = reinterpret_cast<uint64_t*>(twf + plan_twiddle_slots<LOG2L>());
     const int nb = a.bp.nbins;
     double* dbin = reinterpret_cast<double*>(bar + 2);   // nb + 1 (last: Parseval)
@@ -597,8 +648,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
     }
     __syncthreads();
     if (kLoad && t == 0) {
-        if (t0 < t1 && !a.inject_skip) issue(t0, bufs[0], &bar[0]);
-        if (t0 + 1 < t1) issue(t0 + 1, bufs[1], &bar[1]);
+        if (t0 < t1 && !a.inject_skip) issue(t0, buf0, &bar[0]);
+        if (t0 + 1 < t1) issue(t0 + 1, buf0 + tile_elems, &bar[1]);
     }
 
     auto flush = [&](long long batch) {
@@ -615,18 +666,18 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
         __syncthreads();
     };
 
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phases = 0u;  // bit s: parity of the next completion of bar[s]
     long long cur = -1;
     long long failed_at = -1;
     for (long long ti = t0; ti < t1; ++ti) {
         const int s = (int)((ti - t0) & 1);
-        float2* buf = bufs[s];
+        float2* buf = buf0 + s * tile_elems;
         if constexpr (kLoad) {
-            if (!cta_wait(&bar[s], phase[s], a.wait_budget)) {
+            if (!cta_wait(&bar[s], (phases >> s) & 1u, a.wait_budget)) {
                 failed_at = ti;
                 break;
             }
-            phase[s] ^= 1u;
+            phases ^= 1u << s;
         } else {
             // buf is free once the store of two tiles ago has read it; the
             // barrier before the first write of buf (power staging) makes
@@ -710,12 +761,16 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
                 }
                 // The filter (Eqs. 12-13) scales each mode; its power then goes
                 // through shared memory so that each thread owns E consecutive
-                // n0 of one column (element (b, l) to thread t = (b L + l) / E at
-                // slot i TS + t + t / 32, TS = T + T / 32: conflict-free both
-                // ways); their bins come precomputed from the bin table, and
-                // consecutive modes mostly share a bin, so one atomic per run of
-                // equal bins replaces one per mode.
-                constexpr int TS = T + (T >> 5);
+                // n0 of one column (element (b, l) to thread o = (b L + l) / E,
+                // value i = (b L + l) mod E, at slot i TS + o + (o / 32) PAD with
+                // TS and PAD chosen at compile time so that the writes are
+                // conflict-free; the reads, i fixed and o running over a warp,
+                // always are); their bins come precomputed from the bin
+                // table, and consecutive modes mostly share a bin, so one atomic
+                // per run of equal bins replaces one per mode.
+                constexpr int PAD = staging_pad<G, PF::last_radix()>();
+                constexpr int TS = staging_stride<G>(PAD);
+                static_assert(T - 1 + ((T - 1) >> 5) * PAD < TS, "staging slots are one-to-one");
                 static_assert(E * TS <= 2 * tile_elems, "power staging fits the tile buffer");
                 float pacc = 0.0f;
                 if (nb > 0 || kFilt) {
@@ -739,7 +794,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
                         pacc += pw;
                         const int flat = (b << LOG2L) + l;
                         const int owner = flat / E;
-                        ps[(flat & (E - 1)) * TS + owner + (owner >> 5)] = pw;
+                        ps[(flat & (E - 1)) * TS + owner + (owner >> 5) * PAD] = pw;
                     });
                     __syncthreads();
                     if (nb > 0) {
@@ -747,7 +802,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
                         float acc = 0.0f;
 #pragma unroll
                         for (int i = 0; i < E; ++i) {
-                            const float pw = ps[i * TS + t + (t >> 5)];
+                            const float pw = ps[i * TS + t + (t >> 5) * PAD];
                             const int raw = (int)((binw[i >> 1] >> (16 * (i & 1))) & 0xffffu);
                             const int bin = raw == 0xffff ? -1 : raw;
                             if (bin != cur_bin) {
@@ -802,8 +857,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
             // drain this CTA's own loads still in flight (bounded), then its stores
             const int s = (int)((failed_at - t0) & 1);
             const bool issued = !(a.inject_skip && failed_at == t0);
-            if (issued) mbar_wait_bounded(&bar[s], phase[s], a.wait_budget);
-            if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1], a.wait_budget);
+            if (issued) mbar_wait_bounded(&bar[s], (phases >> s) & 1u, a.wait_budget);
+            if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], (phases >> (s ^ 1)) & 1u, a.wait_budget);
             if constexpr (kStore) bulk_wait_all();
         }
         __syncthreads();
