@@ -118,12 +118,12 @@ struct Plan {
 
 // Stage twiddle tables of a plan.  Stage s >= 1 (Ns = 2^log2_before(s), radix
 // R) reads W_{Ns R}^{k r}, k = j mod Ns, r = 1..R-1; its table holds that value
-// at [r Ns + k] (r-major), so the lanes of a warp, which differ in k, read
-// consecutive or identical words: no bank conflicts.
+// at [(r - 1) Ns + k] (r-major), so the lanes of a warp, which differ in k,
+// read consecutive or identical words: no bank conflicts.
 template <int LOG2L, bool REV>
 struct TwTables {
     using P = Plan<LOG2L, REV>;
-    static constexpr int stage_size(int s) { return 1 << (P::log2_before(s) + P::bits(s)); }
+    static constexpr int stage_size(int s) { return ((1 << P::bits(s)) - 1) << P::log2_before(s); }
     static constexpr int offset(int s) { return s <= 1 ? 0 : offset(s - 1) + stage_size(s - 1); }
     static constexpr int size() { return P::NS <= 1 ? 0 : offset(P::NS - 1) + stage_size(P::NS - 1); }
 };
@@ -242,7 +242,7 @@ struct Stages {
                 const int k = j & ((1 << LNS) - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = tw[off + (r << LNS) + k];
+                    const float2 w = tw[off + ((r - 1) << LNS) + k];
                     v[i * R + r] = DIR < 0 ? cmul(v[i * R + r], w) : cmulc(v[i * R + r], w);
                 }
             }
@@ -291,8 +291,8 @@ __device__ __forceinline__ void load_stage_twiddles(float2* tw_s, const float2* 
     if constexpr (S < P::NS) {
         constexpr int lns = P::log2_before(S), lr = P::bits(S);
         constexpr int off = TwTables<LOG2L, REV>::offset(S);
-        for (int q = t; q < (1 << (lns + lr)); q += T) {
-            const int r = q >> lns, k = q & ((1 << lns) - 1);
+        for (int q = t; q < TwTables<LOG2L, REV>::stage_size(S); q += T) {
+            const int r = (q >> lns) + 1, k = q & ((1 << lns) - 1);
             tw_s[off + q] = __ldg(tw + ((k * r) << (kTwLog2 - lns - lr)));
         }
         load_stage_twiddles<LOG2L, REV, S + 1>(tw_s, tw, t, T);

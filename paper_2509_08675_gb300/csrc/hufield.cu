@@ -161,12 +161,6 @@ __global__ void k_add_counts(const __grid_constant__ AddCountsArgs a) {
         for (int d = 0; d < a.ndst; ++d) a.dst[d][b] += a.mult * a.counts[b];
 }
 
-// sums_f[b] += raw[b] * N / P  (S_f(n) = N |G(n)|^2 / sum |G|^2)
-__global__ void k_finalize_field(const double* raw, const double* P, int nbins, double N, double* sums) {
-    const double s = N / *P;
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sums[b] += raw[b] * s;
-}
-
 __global__ void k_bins_mean(const double* sums, const long long* counts, int nbins, double* out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nbins) out[b] = counts[b] ? sums[b] / (double)counts[b] : 0.0;
@@ -398,15 +392,19 @@ int make_bins(const hufield_plan* p, int nr, int ntheta, BinParams& bp) {
 }
 
 // Workspace: [header 256 B: status word][spectrum: max(nlev,1) * N/2 complex64]
-//            [bin table: N/2 uint16, when binning][P: double][raw field bins: nbins doubles]
+//            [bin table: N/2 uint16, when binning]
+//            [two accumulator sets, each P: double, raw field bins: nbins doubles]
+// Field e of a call accumulates into set e & 1; its c2r pass finishes the
+// bins and clears the other set for field e + 1, so a call clears both sets
+// once instead of once per field.
 constexpr size_t kWsHeader = 256;
 
 struct Workspace {
     unsigned* status;
     float2* spec;
     unsigned short* bintab;
-    double* P;
-    double* raw;
+    double* acc[2];  // P at acc[s][0], raw bins at acc[s] + 1
+    size_t acc_stride;  // doubles from set 0 to set 1
 };
 
 size_t ws_spec_bytes(const hufield_plan* p, int nlev) {
@@ -416,9 +414,10 @@ size_t ws_table_bytes(const hufield_plan* p, int nbins) {
     return nbins > 0 ? align256((size_t)p->half * sizeof(unsigned short)) : 0;
 }
 
+size_t ws_acc_bytes(int nbins) { return align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0))); }
+
 size_t ws_bytes(const hufield_plan* p, int nlev, int nbins) {
-    return kWsHeader + ws_spec_bytes(p, nlev) + ws_table_bytes(p, nbins) +
-           align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0)));
+    return kWsHeader + ws_spec_bytes(p, nlev) + ws_table_bytes(p, nbins) + 2 * ws_acc_bytes(nbins);
 }
 
 int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Workspace& w) {
@@ -430,8 +429,9 @@ int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Wo
     w.status = reinterpret_cast<unsigned*>(base);
     w.spec = reinterpret_cast<float2*>(base + kWsHeader);
     w.bintab = tab ? reinterpret_cast<unsigned short*>(base + kWsHeader + spec) : nullptr;
-    w.P = reinterpret_cast<double*>(base + kWsHeader + spec + tab);
-    w.raw = w.P + 1;
+    w.acc[0] = reinterpret_cast<double*>(base + kWsHeader + spec + tab);
+    w.acc_stride = ws_acc_bytes(nbins) / sizeof(double);
+    w.acc[1] = w.acc[0] + w.acc_stride;
     return HUFIELD_OK;
 }
 
@@ -586,37 +586,43 @@ int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, l
     return HUFIELD_OK;
 }
 
+// Clears both accumulator sets of a workspace (once per call).
+int clear_accumulators(const Workspace& w, cudaStream_t s) {
+    HF_CUDA(cudaMemsetAsync(w.acc[0], 0, 2 * w.acc_stride * sizeof(double), s));
+    return HUFIELD_OK;
+}
+
 // The whole path for one field; bins are added to the (already prepared)
-// sums/counts.  nbins == 0 skips every spectrum.
+// sums/counts.  nbins == 0 skips every spectrum.  The field accumulates into
+// accumulator set `set`, which must be clear; its c2r pass clears the other.
 int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx, int out_dtype,
               void* out_f, const float* levels, int nlev, int8_t* out_maps, const BinParams* bp, double* sums_f,
-              double* sums_m, const unsigned short* tab, const Workspace& w, cudaStream_t s) {
+              double* sums_m, const unsigned short* tab, const Workspace& w, int set, cudaStream_t s) {
     const FilterParams fp = make_filter(p, f);
     BinParams none{};
     none.ntheta = 1;
     const BinParams& b = bp ? *bp : none;
-    HF_CUDA(cudaMemsetAsync(w.P, 0, sizeof(double) * (size_t)(1 + b.nbins), s));
+    double* P = w.acc[set & 1];
+    double* raw = P + 1;
     int rc;
     if (p->kspace) {
         // the noise coefficients are drawn inside the axis-0 pass: no forward passes
-        rc = axis0_pass(p, kModeKspace, w.spec, 1, &fp, b, tab, w.raw, w.P, w.status, s, seed, field_idx);
+        rc = axis0_pass(p, kModeKspace, w.spec, 1, &fp, b, tab, raw, P, w.status, s, seed, field_idx);
     } else {
         rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
         if (rc) return rc;
-        rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, w.raw, w.P, w.status, s);
+        rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, raw, P, w.status, s);
     }
     if (rc) return rc;
     if (p->ndim == 3) {
         rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s);
         if (rc) return rc;
     }
-    if (bp && sums_f) {
-        HF_CUDA(profiled(p, kPassMisc, s, [&] {
-            k_finalize_field<<<1, 256, 0, s>>>(w.raw, w.P, b.nbins, (double)p->N, sums_f);
-            return cudaGetLastError();
-        }));
-    }
     C2RArgs ca{};
+    ca.sums_f = bp ? sums_f : nullptr;
+    ca.nbins = b.nbins;
+    ca.next_acc = w.acc[(set + 1) & 1];
+    ca.next_len = 1 + b.nbins;
     ca.spec = w.spec;
     ca.nrows = p->N >> (p->logM + 1);
     ca.half = p->half;
@@ -625,7 +631,7 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     ca.out_maps = reinterpret_cast<signed char*>(out_maps);
     ca.nlev = nlev;
     for (int t = 0; t < nlev; ++t) ca.levels[t] = levels[t];
-    ca.P = w.P;
+    ca.P = P;
     ca.sigma_f = f->sigma_f;
     ca.tw = p->tw;
     ca.status = w.status;
@@ -808,8 +814,10 @@ int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     rc = carve(p, ws, bytes, 0, 0, w);
     if (rc) return rc;
     HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), (cudaStream_t)stream));
+    rc = clear_accumulators(w, (cudaStream_t)stream);
+    if (rc) return rc;
     return run_field(p, f, seed, field_idx, out_dtype, out_f, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
-                     w, (cudaStream_t)stream);
+                     w, 0, (cudaStream_t)stream);
 }
 
 int hufield_threshold(hufield_plan* p, const void* f, int32_t dtype, const float* levels, int32_t nlev,
@@ -894,12 +902,14 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     const unsigned short* tab = nullptr;
     rc = bins_for_call(p, bp, w.bintab, nfields, 1 + nlev, dst, &tab, s);
     if (rc) return rc;
+    rc = clear_accumulators(w, s);
+    if (rc) return rc;
     const size_t esize = out_dtype == HUFIELD_BF16 ? 2 : 4;
     for (int e = 0; e < nfields; ++e) {
         void* fo = out_f ? reinterpret_cast<char*>(out_f) + (size_t)e * (size_t)p->N * esize : nullptr;
         int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * (size_t)p->N : nullptr;
         rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, tab, w,
-                       s);
+                       e & 1, s);
         if (rc) return rc;
     }
     return HUFIELD_OK;

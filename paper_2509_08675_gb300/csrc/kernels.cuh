@@ -45,8 +45,14 @@ struct C2RArgs {
     signed char* out_maps;  // nlev * N sign maps, may be null
     int nlev;
     float levels[kMaxLevels];
-    const double* P;        // sum over the full lattice of |G|^2
+    const double* P;        // sum over the full lattice of |G|^2, followed by the field's raw bins
     float sigma_f;
+    // CTA 0 also finishes the field's bins, sums_f[b] += raw[b] N / P (S_f = N |G|^2 / P),
+    // and clears the other accumulator set (the next field's P and raw bins)
+    double* sums_f;         // may be null (no field bins)
+    int nbins;
+    double* next_acc;       // 1 + nbins doubles to clear
+    int next_len;
     const float2* tw;
     unsigned* status;       // workspace status word (kStatusTimeout)
     long long wait_budget;  // clock cycles allowed per mbarrier wait
@@ -354,7 +360,15 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     const int t = threadIdx.x;
     // f = sigma_f * u / sqrt(sum |G|^2), u the unnormalised inverse (the mean
     // is zero because A(0) = 0): Var = sum|G|^2 / N^2 by Parseval.
-    const float scale = (float)((double)a.sigma_f / sqrt(*a.P));
+    const double Pv = *a.P;
+    const float scale = (float)((double)a.sigma_f / sqrt(Pv));
+    if (blockIdx.x == 0) {
+        if (a.sums_f) {
+            const double sN = (double)a.N / Pv;
+            for (int b = t; b < a.nbins; b += G::T) a.sums_f[b] += a.P[1 + b] * sN;
+        }
+        for (int i = t; i < a.next_len; i += G::T) a.next_acc[i] = 0.0;
+    }
     long long t0, t1;
     chunk_of(a.nrows >> LOGTR, t0, t1);
     auto issue = [&](long long tile, float2* dst, uint64_t* b) {
