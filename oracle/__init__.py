@@ -119,6 +119,8 @@ def _lib():
                                                C.c_void_p]
             lib.or_pipeline_noise.argtypes = [C.c_int, i64p, fp, C.c_uint64, C.c_uint32, C.c_int, C.c_double,
                                               f64p, C.c_int, C.c_int, C.c_int, f64p, i8p, f64p, i64p, f64p, i64p]
+            lib.or_window_variance.argtypes = [C.c_int, i64p, f64p, C.c_int, f64p, f64p]
+            lib.or_window_variance_filter.argtypes = [C.c_int, i64p, fp, C.c_double, C.c_int, f64p, f64p]
             lib.or_noise_dft_at.argtypes = [C.c_int, i64p, C.c_uint64, C.c_uint32, C.c_int, i64p, f64p]
             _LIB = lib
         return _LIB
@@ -271,6 +273,23 @@ def pipeline(shape, filt: Filter, seed: int, field_idx: int = 0, levels=(0.0,), 
         "sums_f": sf, "counts_f": cf,
         "sums_m": sm[: nlev * nb].reshape(nlev, nb), "counts_m": cm[: nlev * nb].reshape(nlev, nb),
     }
+
+
+def window_variance(y: np.ndarray, radii) -> np.ndarray:
+    """sigma_F^2(R) of a lattice field, Eq. (1), for each radius (lattice units)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    R = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
+    out = np.zeros(R.size, np.float64)
+    _lib().or_window_variance(y.ndim, _dims(y.shape), y.reshape(-1), R.size, R, out)
+    return out
+
+
+def window_variance_filter(shape, filt: Filter, radii, sigma_f: float = 1.0) -> np.ndarray:
+    """Ensemble mean of sigma_F^2(R) for fields generated with `filt`."""
+    R = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
+    out = np.zeros(R.size, np.float64)
+    _lib().or_window_variance_filter(len(shape), _dims(shape), C.byref(filt._c()), sigma_f, R.size, R, out)
+    return out
 
 
 def noise_dft_at(shape, seed: int, field_idx: int, modes) -> np.ndarray:

@@ -22,6 +22,8 @@
  *   normalise  f <- sigma_f (f - <f>) / sqrt(Var f), Eq. (15)
  *   threshold  sign map, Sec. II.B (last paragraph): f >= t -> +1 else -1
  *   spectrum   S(n) = |DFT(y)(n)|^2 / N, binned radially (and by angle in 2D)
+ *   window     sigma_F^2(R), Eq. (1): variance of the field averaged over a
+ *              ball of radius R, from the spectrum
  *
  * Readings of points the paper leaves open (each listed in the design notes):
  *   - noise is Philox4x32-10 (Salmon et al., SC'11) with key = seed and
@@ -243,7 +245,9 @@ double or_filter_value(int ndim, const int64_t *n, const int64_t *idx, const or_
     double k0 = f->form == 1 ? 0.0 : f->k0;
     double ks = or_kstar(f);
     double w2 = f->width * f->width;
-    double lnchi = f->supp * log(K / ks) - ((K - k0) * (K - k0) - (ks - k0) * (ks - k0)) / (2.0 * w2);
+    /* s ln(K/K*); with s = 0 the factor K^s is 1 and the term vanishes, also when K* = 0 */
+    double lnchi = (f->supp > 0.0 ? f->supp * log(K / ks) : 0.0) -
+                   ((K - k0) * (K - k0) - (ks - k0) * (ks - k0)) / (2.0 * w2);
     return exp(0.5 * lnchi);
 }
 
@@ -556,6 +560,80 @@ void or_pipeline(int ndim, const int64_t *n, const or_filter *f, uint64_t seed, 
                  double *sums_m, int64_t *counts_m) {
     or_pipeline_noise(ndim, n, f, seed, field_idx, 0, sigma_f, levels, nlev, nr, ntheta, out_f, out_maps, sums_f,
                       counts_f, sums_m, counts_m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Window variance, Eq. (1) of Sec. II.A: sigma_F^2(R) = (1/v1(R)) int C(r)  */
+/* alpha_2(r; R) dr, with alpha_2 the intersection volume of two balls of    */
+/* radius R at distance r over v1(R).  That is the variance of the field     */
+/* averaged over a ball of radius R; in Fourier space,                       */
+/*   sigma_F^2(R) = (1/N^2) sum_{n != 0} |Y(n)|^2 m(|k_n| R)^2,             */
+/* m the transform of the ball's indicator over its volume: 2 J1(x)/x in 2D, */
+/* 3 (sin x - x cos x)/x^3 in 3D.  Reading: the lattice field is its         */
+/* trigonometric interpolant, lengths are in lattice spacings, k_n has       */
+/* components 2 pi n_d / N_d with n_d signed in [-N_d/2, N_d/2).             */
+/* ------------------------------------------------------------------------ */
+static double ball_transform(int ndim, double x) {
+    if (x == 0.0) return 1.0;
+    if (ndim == 2) return 2.0 * j1(x) / x;
+    if (x < 1e-2) return 1.0 - x * x / 10.0 + x * x * x * x / 280.0;
+    return 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
+}
+
+static double mode_k(int ndim, const int64_t *n, const int64_t *idx) {
+    double k2 = 0.0;
+    for (int d = 0; d < ndim; ++d) {
+        double kd = 2.0 * OR_PI * (double)idx[d] / (double)n[d];
+        k2 += kd * kd;
+    }
+    return sqrt(k2);
+}
+
+/* sigma_F^2(R) of a lattice field y for nradii radii. */
+void or_window_variance(int ndim, const int64_t *n, const double *y, int nradii, const double *R, double *out) {
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    double *a = (double *)malloc(sizeof(double) * 2 * N);
+    for (int64_t i = 0; i < N; ++i) { a[2 * i] = y[i]; a[2 * i + 1] = 0.0; }
+    or_fftn(ndim, n, a, -1);
+    for (int r = 0; r < nradii; ++r) out[r] = 0.0;
+    for (int64_t lin = 1; lin < N; ++lin) {
+        int64_t idx[3] = {0, 0, 0};
+        unravel(ndim, n, lin, idx);
+        double k = mode_k(ndim, n, idx);
+        double p2 = a[2 * lin] * a[2 * lin] + a[2 * lin + 1] * a[2 * lin + 1];
+        for (int r = 0; r < nradii; ++r) {
+            double m = ball_transform(ndim, k * R[r]);
+            out[r] += p2 * m * m;
+        }
+    }
+    for (int r = 0; r < nradii; ++r) out[r] /= (double)N * (double)N;
+    free(a);
+}
+
+/* Ensemble mean of sigma_F^2(R) for the generator with filter f: the field's
+ * spectrum is proportional to A^2 (Eq. (8)) and its variance is sigma_f^2, so
+ * E sigma_F^2(R) = sigma_f^2 sum_{n != 0} A(n)^2 m^2 / sum_{n != 0} A(n)^2. */
+void or_window_variance_filter(int ndim, const int64_t *n, const or_filter *f, double sigma_f, int nradii,
+                               const double *R, double *out) {
+    int64_t N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    double total = 0.0;
+    for (int r = 0; r < nradii; ++r) out[r] = 0.0;
+    for (int64_t lin = 1; lin < N; ++lin) {
+        int64_t idx[3] = {0, 0, 0};
+        unravel(ndim, n, lin, idx);
+        double A = or_filter_value(ndim, n, idx, f);
+        double a2 = A * A;
+        if (a2 == 0.0) continue;
+        total += a2;
+        double k = mode_k(ndim, n, idx);
+        for (int r = 0; r < nradii; ++r) {
+            double m = ball_transform(ndim, k * R[r]);
+            out[r] += a2 * m * m;
+        }
+    }
+    for (int r = 0; r < nradii; ++r) out[r] = total > 0.0 ? sigma_f * sigma_f * out[r] / total : 0.0;
 }
 
 /* Forward DFT of the noise at a list of modes, one by one from the

@@ -104,3 +104,11 @@ def test_small_k_power_law(s):
     a2 = oracle.filter_value((n, 4), (2, 0), f)
     slope = math.log(a2 ** 2 / a1 ** 2) / math.log(2.0)
     assert slope == pytest.approx(s, abs=2e-3)
+
+
+def test_no_suppression_is_a_plain_gaussian_band():
+    # Eq. (13) with alpha = 0: chi = C exp(-K^2 / (2 sigma^2)), maximal (1) at K -> 0
+    f = Filter(p=2.0, axes=(1.0, 1.0), width=0.1, supp=0.0, form=1)
+    for idx in ([1, 0], [3, 4], [10, 0]):
+        K = oracle.superellipse([2 * i / 64 for i in idx], f)
+        assert abs(oracle.filter_value((64, 64), idx, f) - math.exp(-K * K / (4 * 0.01))) < 1e-14
