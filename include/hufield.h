@@ -252,6 +252,31 @@ int hufield_batch_run(hufield_batch *batch, float *out_f, int8_t *out_maps, doub
 
 int hufield_batch_destroy(hufield_batch *batch);
 
+/* Window variance, Eq. (1) of Sec. II.A: sigma_F^2(R) = (1/v1(R)) int C(r)
+ * alpha_2(r; R) dr, the variance of the field averaged over a ball of radius
+ * R.  Computed from the spectrum as (1/N^2) sum_{n != 0} |Y(n)|^2 m(|k_n| R)^2,
+ * m = 2 J1(x)/x (2D) or 3 (sin x - x cos x)/x^3 (3D), the transform of the
+ * ball's indicator over its volume, with the lattice field read as its
+ * trigonometric interpolant, k_n of components 2 pi n_d / N_d (n_d signed)
+ * and R in lattice spacings.  Every mode is included (the Nyquist plane of
+ * the last axis by a separate plain DFT).  The window terms are FP64.
+ *
+ * hufield_window_variance: of a stored real field y (dtype F32, BF16 or I8:
+ * fields and sign maps), N elements in C order, 256-byte aligned.
+ * hufield_window_variance_filter: the ensemble mean for filter f, which does
+ * not depend on the noise: sigma_f^2 sum A^2 m^2 / sum A^2 (Eq. (8): the
+ * spectrum is proportional to A^2).
+ *
+ * radii: host array of nradii in [1, 64] finite values >= 0.  out: device,
+ * nradii doubles (overwritten).  ws: hufield_window_variance needs
+ * hufield_workspace_bytes(plan, 3, 0) bytes, hufield_window_variance_filter
+ * hufield_workspace_bytes(plan, 0, 0).  Stream-ordered and asynchronous;
+ * HUFIELD_ERR_INVALID_ARG for bad arguments. */
+int hufield_window_variance(hufield_plan *plan, const void *y, int32_t dtype, int32_t nradii, const float *radii,
+                            double *out, void *ws, size_t ws_bytes, void *stream);
+int hufield_window_variance_filter(hufield_plan *plan, const hufield_filter *f, int32_t nradii, const float *radii,
+                                   double *out, void *ws, size_t ws_bytes, void *stream);
+
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,
                       void *stream);

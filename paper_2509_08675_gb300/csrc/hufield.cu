@@ -15,6 +15,7 @@
 #include "../../include/hufield.h"
 #include "kernels.cuh"
 #include "launch.h"
+#include "window.cuh"
 
 namespace hf {
 KernelInfo r2c_kernel_noise(int log2m, bool big, int src);
@@ -363,7 +364,8 @@ FilterParams make_filter(const hufield_plan* p, const hufield_filter* f) {
     const double ks = 0.5 * (k0 + sqrt(k0 * k0 + 4.0 * s * w * w));  // maximiser: s w^2 = K (K - k0)
     fp.k0 = (float)k0;
     fp.kstar = (float)ks;
-    fp.log2_kstar = (float)log2(ks);
+    // with s = 0 the term s log2(K/K*) vanishes (K^0 = 1), also when K* = 0
+    fp.log2_kstar = s > 0.0 ? (float)log2(ks) : 0.0f;
     fp.two_k0 = (float)(2.0 * k0);
     fp.half_s = (float)(0.5 * s);
     fp.c_d = (float)(1.0 / (4.0 * w * w * log(2.0)));
@@ -950,6 +952,109 @@ int hufield_workspace_status(const void* ws, void* stream) {
     HF_CUDA(cudaMemcpyAsync(&word, ws, sizeof(word), cudaMemcpyDeviceToHost, s));
     HF_CUDA(cudaStreamSynchronize(s));
     return (word & kStatusTimeout) ? HUFIELD_ERR_TIMEOUT : HUFIELD_OK;
+}
+
+static int check_radii(int32_t nradii, const float* radii) {
+    if (nradii < 1 || nradii > kMaxRadii || !radii) return HUFIELD_ERR_INVALID_ARG;
+    for (int r = 0; r < nradii; ++r)
+        if (!(radii[r] >= 0.0f) || !finite(radii[r])) return HUFIELD_ERR_INVALID_ARG;
+    return HUFIELD_OK;
+}
+
+static WindowArgs window_args(const hufield_plan* p, int32_t nradii, const float* radii) {
+    WindowArgs wa{};
+    wa.ndim = p->ndim;
+    for (int d = 0; d < 3; ++d) wa.log2n[d] = p->log2n[d];
+    wa.logM = p->logM;
+    wa.half = p->half;
+    wa.nradii = nradii;
+    for (int r = 0; r < nradii; ++r) wa.radii[r] = radii[r];
+    return wa;
+}
+
+static int grid_for(const hufield_plan* p, long long work, int per_sm) {
+    const long long g = (work + 255) / 256;
+    const long long cap = (long long)per_sm * p->nsm;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+int hufield_window_variance(hufield_plan* p, const void* y, int32_t dtype, int32_t nradii, const float* radii,
+                            double* out, void* ws, size_t bytes, void* stream) {
+    if (!p || !y || !out || !aligned(y)) return HUFIELD_ERR_INVALID_ARG;
+    if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16 && dtype != HUFIELD_I8) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_radii(nradii, radii);
+    if (rc) return rc;
+    Workspace w;
+    rc = carve(p, ws, bytes, 3, 0, w);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), s));
+    const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
+    // the stored half spectrum (k_last < n_last / 2) ...
+    rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, w.status, s);
+    if (rc) return rc;
+    BinParams none{};
+    none.ntheta = 1;
+    rc = axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, nullptr, w.status, s);
+    if (rc) return rc;
+    // ... and the Nyquist plane k_last = n_last / 2, by plain DFTs of the rows' alternating sums
+    const int lnl = p->log2n[p->ndim - 1];
+    const long long nplane = p->N >> lnl;
+    double2* planeA = reinterpret_cast<double2*>(w.spec + p->half);
+    double2* planeB = planeA + nplane;
+    double* acc = reinterpret_cast<double*>(planeB + nplane);
+    HF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)(nradii + 1), s));
+    const double2* plane = nullptr;
+    HF_CUDA(profiled(p, kPassMisc, s, [&] {
+        const int g = grid_for(p, nplane * 32, 8);
+        if (src == kSrcF32) k_nyquist_rows<kSrcF32><<<g, 256, 0, s>>>(y, nplane, lnl, planeA);
+        else if (src == kSrcBF16) k_nyquist_rows<kSrcBF16><<<g, 256, 0, s>>>(y, nplane, lnl, planeA);
+        else k_nyquist_rows<kSrcI8><<<g, 256, 0, s>>>(y, nplane, lnl, planeA);
+        if (p->ndim == 2) {
+            k_dft_axis<<<grid_for(p, nplane, 8), 256, 0, s>>>(planeA, planeB, 1, p->log2n[0], 1);
+            plane = planeB;
+        } else {
+            k_dft_axis<<<grid_for(p, nplane, 8), 256, 0, s>>>(planeA, planeB, p->n[0], p->log2n[1], 1);
+            k_dft_axis<<<grid_for(p, nplane, 8), 256, 0, s>>>(planeB, planeA, 1, p->log2n[0], p->n[1]);
+            plane = planeA;
+        }
+        return cudaGetLastError();
+    }));
+    WindowArgs wa = window_args(p, nradii, radii);
+    wa.spec = w.spec;
+    wa.plane = plane;
+    wa.acc = acc;
+    HF_CUDA(profiled(p, kPassMisc, s, [&] {
+        k_window_field<<<dim3(grid_for(p, p->half, 4), nradii), 256, 0, s>>>(wa);
+        k_window_plane<<<dim3(grid_for(p, nplane, 4), nradii), 256, 0, s>>>(wa);
+        k_window_finalize<<<1, kMaxRadii, 0, s>>>(acc, nradii, 1.0 / ((double)p->N * (double)p->N), 0, out);
+        return cudaGetLastError();
+    }));
+    return HUFIELD_OK;
+}
+
+int hufield_window_variance_filter(hufield_plan* p, const hufield_filter* f, int32_t nradii, const float* radii,
+                                   double* out, void* ws, size_t bytes, void* stream) {
+    if (!p || !out) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_filter(p, f);
+    if (rc) return rc;
+    rc = check_radii(nradii, radii);
+    if (rc) return rc;
+    Workspace w;
+    rc = carve(p, ws, bytes, 0, 0, w);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* acc = reinterpret_cast<double*>(w.spec);
+    HF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)(nradii + 1), s));
+    WindowArgs wa = window_args(p, nradii, radii);
+    wa.fp = make_filter(p, f);
+    wa.acc = acc;
+    HF_CUDA(profiled(p, kPassMisc, s, [&] {
+        k_window_filter<<<dim3(grid_for(p, p->half, 4), nradii), 256, 0, s>>>(wa);
+        k_window_finalize<<<1, kMaxRadii, 0, s>>>(acc, nradii, (double)f->sigma_f * (double)f->sigma_f, 1, out);
+        return cudaGetLastError();
+    }));
+    return HUFIELD_OK;
 }
 
 int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, double* out, void* stream) {

@@ -92,6 +92,8 @@ def _load():
     lib.hufield_generate.argtypes = [vp, fptr, u64, u32, i32, vp, vp, sz, vp]
     lib.hufield_threshold.argtypes = [vp, vp, i32, C.POINTER(C.c_float), i32, vp, vp]
     lib.hufield_spectrum.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]
+    lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
+    lib.hufield_window_variance_filter.argtypes = [vp, fptr, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
                                      vp, vp, vp, vp, vp, sz, vp]
     lib.hufield_ensemble.argtypes = [vp, fptr, u64, u32, i32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32,
@@ -242,6 +244,27 @@ def hufield_ensemble(plan: Plan, filt: Filter, seed: int, field0: int, nfields: 
                                  _ptr(out_maps), nr, ntheta, int(accumulate), _ptr(sums_f), _ptr(counts_f),
                                  _ptr(sums_m), _ptr(counts_m), _ptr(ws), ws.numel(), _stream(stream)),
            "hufield_ensemble")
+
+
+def _radii(radii):
+    r = [float(x) for x in radii]
+    return (C.c_float * max(len(r), 1))(*r), len(r)
+
+
+def hufield_window_variance(plan: Plan, y: torch.Tensor, radii, out: torch.Tensor, ws: torch.Tensor, stream=None):
+    """sigma_F^2(R) (Eq. 1) of a stored field or sign map y into out (float64, len(radii))."""
+    rv, n = _radii(radii)
+    _check(_lib.hufield_window_variance(plan.handle, _ptr(y), _DTYPES[y.dtype], n, rv, _ptr(out), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "hufield_window_variance")
+
+
+def hufield_window_variance_filter(plan: Plan, filt: Filter, radii, out: torch.Tensor, ws: torch.Tensor,
+                                   stream=None):
+    """Ensemble mean of sigma_F^2(R) for filter filt into out (float64, len(radii))."""
+    fc = filt._c()
+    rv, n = _radii(radii)
+    _check(_lib.hufield_window_variance_filter(plan.handle, C.byref(fc), n, rv, _ptr(out), _ptr(ws), ws.numel(),
+                                               _stream(stream)), "hufield_window_variance_filter")
 
 
 def hufield_bins_mean(sums: torch.Tensor, counts: torch.Tensor, out_mean: torch.Tensor, stream=None):

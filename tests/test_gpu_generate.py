@@ -49,6 +49,8 @@ WIDE_P = [
     ((128, 128), dict(p=50.0, axes=(1.0, 1.0), width=0.05, supp=20.0, form=1)),
     ((32, 64, 32), dict(p=30.0, axes=(1.0, 1.0, 0.5), k0=0.2, width=0.05, supp=2.0)),
     ((32, 32, 32), dict(p=100.0, axes=(1.0, 2.0, 0.5), k0=0.3, width=0.08, supp=2.0)),
+    # Eq. (13) with alpha = 0 in the paper form: K* = 0, no suppression term
+    ((256, 256), dict(p=2.0, axes=(1.0, 1.0), width=0.1, supp=0.0, form=1)),
 ]
 
 
