@@ -277,6 +277,18 @@ int hufield_window_variance(hufield_plan *plan, const void *y, int32_t dtype, in
 int hufield_window_variance_filter(hufield_plan *plan, const hufield_filter *f, int32_t nradii, const float *radii,
                                    double *out, void *ws, size_t ws_bytes, void *stream);
 
+/* Per-mode spectra over the stored half spectrum, float out[n0][n1][k_last]
+ * (3D) or out[n0][k_last] (2D) with k_last = 0 .. n_last/2 - 1 and the other
+ * indices in FFT order (device, N/2 floats, overwritten; the other half is
+ * the mirror, S(-n) = S(n)).
+ * hufield_spectrum_modes: S(n) = |DFT(y)(n)|^2 / N of a stored real field y
+ * (F32, BF16 or I8), ws >= hufield_workspace_bytes(plan, 1, 0).
+ * hufield_filter_modes: A(n)^2, Eqs. (8), (12), (13), the filter's target
+ * spectrum up to its normalisation (zero at n = 0 and on Nyquist planes). */
+int hufield_spectrum_modes(hufield_plan *plan, const void *y, int32_t dtype, float *out, void *ws, size_t ws_bytes,
+                           void *stream);
+int hufield_filter_modes(hufield_plan *plan, const hufield_filter *f, float *out, void *stream);
+
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,
                       void *stream);

@@ -1057,6 +1057,44 @@ int hufield_window_variance_filter(hufield_plan* p, const hufield_filter* f, int
     return HUFIELD_OK;
 }
 
+int hufield_spectrum_modes(hufield_plan* p, const void* y, int32_t dtype, float* out, void* ws, size_t bytes,
+                           void* stream) {
+    if (!p || !y || !out || !aligned(y)) return HUFIELD_ERR_INVALID_ARG;
+    if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16 && dtype != HUFIELD_I8) return HUFIELD_ERR_INVALID_ARG;
+    Workspace w;
+    int rc = carve(p, ws, bytes, 1, 0, w);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), s));
+    const int src = dtype == HUFIELD_F32 ? kSrcF32 : dtype == HUFIELD_BF16 ? kSrcBF16 : kSrcI8;
+    rc = forward_rows_and_mid(p, src, y, 0, 0, w.spec, w.status, s);
+    if (rc) return rc;
+    BinParams none{};
+    none.ntheta = 1;
+    rc = axis0_pass(p, kModePlain, w.spec, 1, nullptr, none, nullptr, nullptr, nullptr, w.status, s);
+    if (rc) return rc;
+    HF_CUDA(profiled(p, kPassMisc, s, [&] {
+        k_spectrum_modes<<<grid_for(p, p->half, 8), 256, 0, s>>>(w.spec, p->half, (float)(1.0 / (double)p->N), out);
+        return cudaGetLastError();
+    }));
+    return HUFIELD_OK;
+}
+
+int hufield_filter_modes(hufield_plan* p, const hufield_filter* f, float* out, void* stream) {
+    if (!p || !out) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_filter(p, f);
+    if (rc) return rc;
+    const float none = 0.0f;
+    WindowArgs wa = window_args(p, 1, &none);
+    wa.fp = make_filter(p, f);
+    cudaStream_t s = (cudaStream_t)stream;
+    HF_CUDA(profiled(p, kPassMisc, s, [&] {
+        k_filter_modes<<<grid_for(p, p->half, 8), 256, 0, s>>>(wa, out);
+        return cudaGetLastError();
+    }));
+    return HUFIELD_OK;
+}
+
 int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, double* out, void* stream) {
     if (!sums || !counts || !out || nbins < 1) return HUFIELD_ERR_INVALID_ARG;
     k_bins_mean<<<(nbins + 255) / 256, 256, 0, (cudaStream_t)stream>>>(

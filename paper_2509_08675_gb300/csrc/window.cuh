@@ -204,6 +204,35 @@ __global__ void k_dft_axis(const double2* in, double2* out, long long A, int log
     }
 }
 
+// Per-mode outputs over the stored half spectrum (k_last < n_last / 2),
+// natural layout [n0][n1][k_last]: the spectral density of a field,
+// S(n) = |Y(n)|^2 / N, or the filter's A(n)^2 (Eq. 8: the target spectrum up
+// to its normalisation; zero at n = 0 and on Nyquist planes).
+__global__ void k_spectrum_modes(const float2* spec, long long half, float inv_n, float* out) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < half;
+         m += (long long)gridDim.x * blockDim.x) {
+        const float2 y = spec[m];
+        out[m] = (y.x * y.x + y.y * y.y) * inv_n;
+    }
+}
+
+__global__ void k_filter_modes(const __grid_constant__ WindowArgs a, float* out) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.half;
+         m += (long long)gridDim.x * blockDim.x) {
+        int i0, i1, i2;
+        double w;
+        half_mode(a, m, i0, i1, i2, w);
+        float A = 0.0f;
+        if (i0 != -(1 << (a.log2n[0] - 1)) && !(a.ndim == 3 && i1 == -(1 << (a.log2n[1] - 1)))) {
+            const float x = (float)i0 * __int_as_float((127 + 1 - a.log2n[0]) << 23);
+            const float y = (float)i1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
+            const float z = a.ndim == 3 ? (float)i2 * __int_as_float((127 + 1 - a.log2n[2]) << 23) : 0.0f;
+            A = filter_amplitude(a.fp, x, y, z, a.ndim);
+        }
+        out[m] = A * A;
+    }
+}
+
 __global__ void k_window_finalize(const double* acc, int nradii, double scale, int by_norm, double* out) {
     const int r = threadIdx.x;
     if (r < nradii) out[r] = by_norm ? (acc[nradii] > 0.0 ? scale * acc[r] / acc[nradii] : 0.0) : scale * acc[r];

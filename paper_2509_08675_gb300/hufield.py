@@ -92,6 +92,8 @@ def _load():
     lib.hufield_generate.argtypes = [vp, fptr, u64, u32, i32, vp, vp, sz, vp]
     lib.hufield_threshold.argtypes = [vp, vp, i32, C.POINTER(C.c_float), i32, vp, vp]
     lib.hufield_spectrum.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]
+    lib.hufield_spectrum_modes.argtypes = [vp, vp, i32, vp, vp, sz, vp]
+    lib.hufield_filter_modes.argtypes = [vp, fptr, vp, vp]
     lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_window_variance_filter.argtypes = [vp, fptr, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
@@ -244,6 +246,18 @@ def hufield_ensemble(plan: Plan, filt: Filter, seed: int, field0: int, nfields: 
                                  _ptr(out_maps), nr, ntheta, int(accumulate), _ptr(sums_f), _ptr(counts_f),
                                  _ptr(sums_m), _ptr(counts_m), _ptr(ws), ws.numel(), _stream(stream)),
            "hufield_ensemble")
+
+
+def hufield_spectrum_modes(plan: Plan, y: torch.Tensor, out: torch.Tensor, ws: torch.Tensor, stream=None):
+    """S(n) = |DFT(y)|^2 / N over the stored half spectrum into out (float32, N/2)."""
+    _check(_lib.hufield_spectrum_modes(plan.handle, _ptr(y), _DTYPES[y.dtype], _ptr(out), _ptr(ws), ws.numel(),
+                                       _stream(stream)), "hufield_spectrum_modes")
+
+
+def hufield_filter_modes(plan: Plan, filt: Filter, out: torch.Tensor, stream=None):
+    """A(n)^2 over the stored half spectrum into out (float32, N/2)."""
+    fc = filt._c()
+    _check(_lib.hufield_filter_modes(plan.handle, C.byref(fc), _ptr(out), _stream(stream)), "hufield_filter_modes")
 
 
 def _radii(radii):
