@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparator (context line)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
     ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
@@ -243,6 +244,11 @@ def main():
         r2 = measure(hf, torch, wl2, args.also, args, rank, world, dist)
         also[args.also] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "pipeline", "passes", "clocks")}
         del r2
+    comp = {}
+    if world == 1 and not args.no_cufft:
+        comp[args.workload] = cufft_comparator(hf, torch, wl)
+        if also:
+            comp[args.also] = cufft_comparator(hf, torch, dict(WORKLOADS[args.also]))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(wl, wl["nfields"], args.noise)
@@ -264,6 +270,8 @@ def main():
                 "cpu_baseline": cpu}
         if also:
             line["also"] = also
+        if comp:
+            line["cufft_comparator"] = comp
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -353,6 +361,74 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
                          "frac": round(pipe_gbs / peak, 4)},
             "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()), "clocks": clk,
             "plan": plan, "filt": filt, "bufs": (out_f, maps, sf, cf, sm, cm, ws), "field0": field0}
+
+
+def cufft_comparator(hf, torch, wl, nfields=4):
+    """The same steps with library FFTs (torch.fft = cuFFT) and torch elementwise
+    kernels, timed beside ours for context: torch.randn noise, rfftn, multiply by
+    the filter (A from hufield_filter_modes), irfftn, normalise, threshold, rfftn of
+    each map, |.|^2 and binning by index_add (radial bins, float geometry).  Not a
+    product path; no parity claim."""
+    shape = tuple(wl["shape"])
+    N = math.prod(shape)
+    M = shape[-1] // 2
+    levels, nr, nt = wl["levels"], wl["nr"], wl["ntheta"]
+    filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
+    plan = hf.Plan(shape)
+    a2 = torch.empty(N // 2, dtype=torch.float32, device="cuda")
+    hf.hufield_filter_modes(plan, filt, a2)
+    A = torch.zeros(shape[:-1] + (M + 1,), dtype=torch.float32, device="cuda")
+    A[..., :M] = a2.view(shape[:-1] + (M,)).sqrt()
+    # radial (and, in 2D, angular) bin of every rfft mode; weight 2 for 0 < k_last < M
+    ks = [torch.fft.fftfreq(n, 1.0 / n, device="cuda") * (2.0 / n) for n in shape[:-1]]
+    ks.append(torch.arange(M + 1, device="cuda", dtype=torch.float32) * (2.0 / shape[-1]))
+    grids = torch.meshgrid(*ks, indexing="ij")
+    kap = torch.sqrt(sum(g * g for g in grids))
+    rb = torch.floor(kap * nr).long()
+    if nt > 1:
+        th = torch.atan2(grids[1], grids[0])
+        th = torch.where(th < 0, th + math.pi, th)
+        sb = torch.clamp(torch.floor(th / math.pi * nt).long(), max=nt - 1)
+        idx = rb * nt + sb
+    else:
+        idx = rb
+    keep = (rb < nr).reshape(-1)
+    idx = idx.reshape(-1)[keep]
+    w = torch.full(shape[:-1] + (M + 1,), 2.0, device="cuda")
+    w[..., 0] = 1.0
+    w[..., M] = 1.0
+    w = w.reshape(-1)[keep]
+    nb = nr * nt
+    sums = torch.zeros((1 + len(levels)) * nb, dtype=torch.float64, device="cuda")
+
+    def field(i):
+        z = torch.randn(shape, device="cuda")
+        G = torch.fft.rfftn(z) * A
+        P = (G.real ** 2 + G.imag ** 2).reshape(-1)
+        tot = (P.reshape(shape[:-1] + (M + 1,)) * torch.where(torch.arange(M + 1, device="cuda") % M == 0, 1.0,
+                                                               2.0)).sum()
+        f = torch.fft.irfftn(G, s=shape)
+        f = f * torch.rsqrt(tot / N / N)
+        sums[:nb].index_add_(0, idx, (P[keep] * w * (N / tot)).double())
+        for t, lev in enumerate(levels):
+            m = torch.where(f >= lev, 1.0, -1.0)
+            Y = torch.fft.rfftn(m)
+            sums[(1 + t) * nb:(2 + t) * nb].index_add_(0, idx, ((Y.real ** 2 + Y.imag ** 2).reshape(-1)[keep] * w
+                                                                / N).double())
+        return f
+
+    for i in range(2):
+        field(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(nfields):
+        field(i)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nfields
+    return {"ms_per_field": round(ms, 4), "value": N / (ms / 1e3), "unit": "voxels/s", "fields_timed": nfields,
+            "what": "torch.fft (cuFFT) + torch elementwise, same steps, torch.randn noise; context only"}
 
 
 def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws, field0, dist, world):
