@@ -98,16 +98,17 @@ __global__ void __launch_bounds__(256) k_bin_table(const __grid_constant__ Table
     fill_thresholds(a.bp, thr, threadIdx.x, blockDim.x);
     __syncthreads();
     const int L = 1 << a.log2l;
-    const int tile_log = a.logTB + a.log2l;
-    // each thread takes runs of 8 consecutive l of one column
-    const long long nruns = a.nmodes >> 3;
+    const int tile_log = a.logTB + a.log2l - (a.paired ? 1 : 0);  // entries per tile, log2
+    // each thread takes 8 consecutive entries: 8 consecutive l of one column,
+    // or (paired) the pairs n0 = +-m, m = m0 .. m0+7, of one column
+    const long long nruns = (a.nmodes >> (a.paired ? 1 : 0)) >> 3;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nruns;
          r += (long long)gridDim.x * blockDim.x) {
         const long long f0 = r << 3;
         const long long tile = f0 >> tile_log;
         const int within = (int)(f0 & ((1ll << tile_log) - 1));
-        const int b = within >> a.log2l;
-        const int l0 = within & (L - 1);
+        const int b = a.paired ? within / (L / 2) : within >> a.log2l;
+        const int l0 = a.paired ? within % (L / 2) : within & (L - 1);
         const int col = (int)((tile << a.logTB) + b);
         int n1, n2, klast;
         if (a.ndim == 3) {
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(256) k_bin_table(const __grid_constant__ Table
         unsigned short out[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
+            // paired: l0 + i is m, standing for n0 = +m and -m (m = 0: n0 = 0 alone, -L/2 is dropped)
             const int bin = bin_index(a.bp, thr, ang, signed_index(l0 + i, a.log2l), n1, n2, a.ndim);
             out[i] = bin < 0 ? (unsigned short)0xffff : (unsigned short)bin;
             if (bin != run_bin) {
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(256) k_bin_table(const __grid_constant__ Table
                 run_bin = bin;
                 run = 0;
             }
-            run += w;
+            run += (a.paired && l0 + i > 0) ? 2 * w : w;
         }
         if (run_bin >= 0) atomicAdd(cnt + run_bin, run);
         uint4 pk;
@@ -218,7 +220,8 @@ struct Launch {
 // p log2 |kappa_i / a_i| far from its zero sentinel within these.
 constexpr float kMaxExponent = 1024.0f;
 constexpr float kMinAxis = 1.0f / 1048576.0f, kMaxAxis = 1048576.0f;
-// Resident CTAs per SM of the strided (column) passes.
+// Resident CTAs per SM of the strided (column) passes; the maps' binning
+// pass, which stores nothing, takes one more.
 constexpr int kColCtasPerSm = 2;
 // Bound of one mbarrier wait: ~1 s at the GB300's 2.07 GHz SM clock.
 constexpr long long kWaitBudget = 2000000000ll;
@@ -283,7 +286,8 @@ bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
     L.smem = k.fixed_smem + extra_smem;
-    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm, kColCtasPerSm);
+    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm,
+                            mode == kModeBins ? kColCtasPerSm + 1 : kColCtasPerSm);
     return L.grid > 0;
 }
 
@@ -567,6 +571,8 @@ int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, l
                     long long** dst, cudaStream_t s) {
     TableArgs ta{};
     ta.tab = tab;
+    ta.paired = bp.ntheta == 1 &&
+                pairable_tile(elems_for(p->log2n[0]), (1 << (axis0_logtb(p) + p->log2n[0])) / elems_for(p->log2n[0]));
     ta.nmodes = p->half;
     ta.log2l = p->log2n[0];
     ta.logTB = axis0_logtb(p);

@@ -19,6 +19,8 @@
 #pragma once
 
 #include "common.cuh"
+#include <type_traits>
+
 #include "fft.cuh"
 #include "tma.cuh"
 
@@ -90,6 +92,12 @@ struct ColArgs {
 // 128 threads or more at 128 registers per thread or fewer (65536 / (128 T)
 // CTAs of T threads); the small tiles of tiny lattices are left unbounded.
 constexpr int min_blocks(int T) { return T >= 512 ? 1 : (T >= 128 ? 512 / T : 1); }
+// Three CTAs of 256 threads (80 registers) for the passes that gain more from
+// occupancy than they lose to register pressure (measured on 512^3: the noise
+// rows 0.428 -> 0.408 ms, the maps' bins 0.308 -> 0.270 ms; the 2048-long
+// noise rows and the filter pass lose).
+constexpr int min_blocks_r2c(int log2m, int T) { return (log2m <= 8 && T == 256) ? 3 : min_blocks(T); }
+constexpr int min_blocks_cols(int mode, int T) { return (mode == 2 && T == 256) ? 3 : min_blocks(T); }
 
 __device__ __forceinline__ int signed_index(int i, int log2n) {
     return i < (1 << (log2n - 1)) ? i : i - (1 << log2n);
@@ -281,7 +289,7 @@ __device__ __forceinline__ float2 r2c_post(float2 Z, float2 Zm_conj, float2 w) {
 // Rows: real input -> half spectrum.
 // ---------------------------------------------------------------------------
 template <int LOG2M, int LOGTR, int SRC>
-__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG2M, LOGTR, true>::T))
+__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks_r2c(LOG2M, Geo<LOG2M, LOGTR, true>::T))
     k_r2c(const __grid_constant__ RowArgs a) {
     using G = Geo<LOG2M, LOGTR, true>;
     constexpr int M = G::L;
@@ -548,13 +556,34 @@ __device__ __forceinline__ void kspace_tile(float2 (&v)[G::E], const ColArgs& a,
 // is the one whose write pattern has the fewest bank conflicts, simulated at
 // compile time for the first warps of a tile, every element slot of the FFT's
 // output layout (radix R last), 4-byte words, 32 banks.
+// Where the power of tile element (b, l) is staged: thread o, value i.
+// Plain order: o = (b L + l) / E, i = (b L + l) mod E (E consecutive n0 of one
+// column).  Paired order (radial bins only, where n0 and -n0 share a bin): the
+// column's n0 = +m and n0 = -m (m = 0 pairs with the dropped Nyquist n0 =
+// -L/2) are values 2 (m mod 8) and 2 (m mod 8) + 1 of thread
+// o = b L/16 + m/8, which then adds each pair before binning: half the bin
+// lookups and about half the runs.
+__host__ __device__ constexpr bool pairable_tile(int e, int t) { return e == 16 && t <= 256; }
+__host__ __device__ constexpr int stage_o(int b, int l, int log2l, int e, bool paired) {
+    if (!paired) return ((b << log2l) + l) / e;
+    const int L = 1 << log2l;
+    const int m = l < L / 2 ? l : (l == L / 2 ? 0 : L - l);
+    return b * (L / 16) + m / 8;
+}
+__host__ __device__ constexpr int stage_i(int l, int log2l, int e, bool paired) {
+    if (!paired) return l % e;
+    const int L = 1 << log2l;
+    const int m = l < L / 2 ? l : (l == L / 2 ? 0 : L - l);
+    return 2 * (m % 8) + (l < L / 2 ? 0 : 1);
+}
+
 template <class G>
 constexpr int staging_stride(int pad) {
     if (G::T < 32) return G::T + 1;
     const int base = G::T + (G::T / 32) * pad;
     return base + (((1 - base) % 32) + 32) % 32;
 }
-template <class G, int R>
+template <class G, int R, bool PAIRED>
 constexpr int staging_cost(int pad) {
     constexpr int T = G::T, E = G::E, L = G::L;
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
@@ -569,8 +598,8 @@ constexpr int staging_cost(int pad) {
                 const int g = 32 * w + lane + T * (e >> LR);
                 const int b = g & (G::TB - 1), j = g >> G::LOGTB;
                 const int l = j + (e & (R - 1)) * (L / R);
-                const int flat = b * L + l, o = flat / E;
-                const int bank = ((flat % E) * ts + o + (o >> 5) * pad) & 31;
+                const int o = stage_o(b, l, G::LOG2L, E, PAIRED);
+                const int bank = (stage_i(l, G::LOG2L, E, PAIRED) * ts + o + (o >> 5) * pad) & 31;
                 worst = ++count[bank] > worst ? count[bank] : worst;
             }
             cost += worst;
@@ -578,12 +607,12 @@ constexpr int staging_cost(int pad) {
     }
     return cost;
 }
-template <class G, int R>
+template <class G, int R, bool PAIRED>
 constexpr int staging_pad() {
-    int best = 0, best_cost = staging_cost<G, R>(0);
+    int best = 0, best_cost = staging_cost<G, R, PAIRED>(0);
     for (int pad = 1; pad < 40 && G::T >= 32; ++pad) {
         if (G::E * staging_stride<G>(pad) > 2 * G::TB * G::L) break;  // must fit the tile buffer (2 x float)
-        const int c = staging_cost<G, R>(pad);
+        const int c = staging_cost<G, R, PAIRED>(pad);
         if (c < best_cost) {
             best = pad;
             best_cost = c;
@@ -601,7 +630,7 @@ struct ColGeo {
 };
 
 template <int LOG2L, int LOGTB, int MODE, int DIR>
-__global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LOG2L, LOGTB, false>::T))
+__global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(MODE, Geo<LOG2L, LOGTB, false>::T))
     k_cols(const __grid_constant__ ColArgs a) {
     using CG = ColGeo<LOG2L, LOGTB>;
     using G = typename CG::G;
@@ -615,6 +644,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
     constexpr bool kAcc = MODE != kModePlain;
     constexpr bool kStore = MODE != kModeBins;
     constexpr bool kFilt = MODE == kModeFilter || MODE == kModeKspace;
+    // paired staging needs 16 values per thread (L >= 16); left out of the
+    // 512-thread tiles, where the second binning variant costs spills
+    constexpr bool kPairable = kAcc && pairable_tile(E, T);
     constexpr bool kLoad = MODE != kModeKspace;
     static_assert(TB >= 2, "k-space mode pairs rely on two columns per tile");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -711,8 +743,19 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
         uint32_t binw[E / 2 > 0 ? E / 2 : 1];
         if constexpr (kAcc) {
             if (nb > 0) {
-                const unsigned short* src = a.bintab + (ti - ab * tpb) * tile_elems + t * E;
-                if constexpr (E >= 8) {
+                // E entries per thread (E/2 pair bins when paired, see stage_o)
+                const int per = (kPairable && a.bp.ntheta == 1) ? E / 2 : E;
+                const unsigned short* src = a.bintab + (ti - ab * tpb) * (tile_elems / E * per) + t * per;
+                if (per == E / 2 && E >= 16) {
+#pragma unroll
+                    for (int q = 0; q < E / 16; ++q) {
+                        const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
+                        binw[4 * q] = w4.x;
+                        binw[4 * q + 1] = w4.y;
+                        binw[4 * q + 2] = w4.z;
+                        binw[4 * q + 3] = w4.w;
+                    }
+                } else if constexpr (E >= 8) {
 #pragma unroll
                     for (int q = 0; q < E / 8; ++q) {
                         const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
@@ -782,10 +825,16 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
                 // always are); their bins come precomputed from the bin
                 // table, and consecutive modes mostly share a bin, so one atomic
                 // per run of equal bins replaces one per mode.
-                constexpr int PAD = staging_pad<G, PF::last_radix()>();
-                constexpr int TS = staging_stride<G>(PAD);
-                static_assert(T - 1 + ((T - 1) >> 5) * PAD < TS, "staging slots are one-to-one");
-                static_assert(E * TS <= 2 * tile_elems, "power staging fits the tile buffer");
+                constexpr int PAD0 = staging_pad<G, PF::last_radix(), false>();
+                constexpr int TS0 = staging_stride<G>(PAD0);
+                constexpr int PAD1 = staging_pad<G, PF::last_radix(), true>();
+                constexpr int TS1 = staging_stride<G>(PAD1);
+                static_assert(T - 1 + ((T - 1) >> 5) * PAD0 < TS0, "staging slots are one-to-one");
+                static_assert(T - 1 + ((T - 1) >> 5) * PAD1 < TS1, "staging slots are one-to-one");
+                static_assert(E * TS0 <= 2 * tile_elems && E * TS1 <= 2 * tile_elems, "staging fits the tile buffer");
+                // radial bins only: n0 and -n0 share every bin (see stage_o)
+                const bool paired = kPairable && a.bp.ntheta == 1;
+                const int TS = paired ? TS1 : TS0, PAD = paired ? PAD1 : PAD0;
                 float pacc = 0.0f;
                 if (nb > 0 || kFilt) {
                     float* ps = reinterpret_cast<float*>(buf);
@@ -806,27 +855,43 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
                         }
                         const float pw = wcol * cabs2(v[e]);
                         pacc += pw;
-                        const int flat = (b << LOG2L) + l;
-                        const int owner = flat / E;
-                        ps[(flat & (E - 1)) * TS + owner + (owner >> 5) * PAD] = pw;
+                        const int owner = stage_o(b, l, LOG2L, E, paired);
+                        // the Nyquist n0 = -L/2 is dropped from the bins: it stages as 0 next to n0 = 0
+                        ps[stage_i(l, LOG2L, E, paired) * TS + owner + (owner >> 5) * PAD] =
+                            (paired && l == L / 2) ? 0.0f : pw;
                     });
                     __syncthreads();
                     if (nb > 0) {
-                        int cur_bin = -1;
-                        float acc = 0.0f;
+                        // runs of equal bins (E values, or E/2 pairs), one atomic per run
+                        auto binning = [&](auto npos, auto pair) {
+                            constexpr int K = decltype(npos)::value;
+                            constexpr bool P = decltype(pair)::value;
+                            int cur_bin = -1;
+                            float acc = 0.0f;
 #pragma unroll
-                        for (int i = 0; i < E; ++i) {
-                            const float pw = ps[i * TS + t + (t >> 5) * PAD];
-                            const int raw = (int)((binw[i >> 1] >> (16 * (i & 1))) & 0xffffu);
-                            const int bin = raw == 0xffff ? -1 : raw;
-                            if (bin != cur_bin) {
-                                if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
-                                cur_bin = bin;
-                                acc = 0.0f;
+                            for (int q = 0; q < K; ++q) {
+                                float pw = ps[(P ? 2 * q : q) * TS + t + (t >> 5) * PAD];
+                                if constexpr (P) pw += ps[(2 * q + 1) * TS + t + (t >> 5) * PAD];
+                                const int raw = (int)((binw[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+                                const int bin = raw == 0xffff ? -1 : raw;
+                                if (bin != cur_bin) {
+                                    if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
+                                    cur_bin = bin;
+                                    acc = 0.0f;
+                                }
+                                acc += pw;
                             }
-                            acc += pw;
+                            if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
+                        };
+                        if constexpr (kPairable) {
+                            if (paired) {
+                                binning(std::integral_constant<int, E / 2>{}, std::true_type{});
+                            } else {
+                                binning(std::integral_constant<int, E>{}, std::false_type{});
+                            }
+                        } else {
+                            binning(std::integral_constant<int, E>{}, std::false_type{});
                         }
-                        if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
                     }
                 }
                 if constexpr (kFilt) {
@@ -898,6 +963,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks(Geo<LO
 // ---------------------------------------------------------------------------
 struct TableArgs {
     unsigned short* tab;
+    int paired;        // paired staging order (radial bins, L >= 16): one entry per (n0, -n0) pair
     long long nmodes;  // N / 2
     int log2l;         // axis-0 length
     int logTB;         // axis-0 tile width
