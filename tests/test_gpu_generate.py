@@ -79,7 +79,8 @@ def test_generate_sigma_f_and_seeds(hf, shape):
 
 
 def test_generate_bf16_storage_error(hf):
-    # BF16 storage: expected relative L2 ~ 2^-9 / sqrt(3) ~ 1.1e-3 (round to nearest, 8-bit significand)
+    # BF16 storage: round to nearest with an 8-bit significand, the error uniform within
+    # half an ulp (2^-8 of the binade's base): relative L2 1.6e-3 for a Gaussian field
     shape = (256, 256)
     gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
     plan = hf.Plan(shape)
@@ -88,7 +89,7 @@ def test_generate_bf16_storage_error(hf):
     hf.hufield_generate(plan, gf, 0, 0, out, ws)
     torch.cuda.synchronize()
     r = rel_l2(np_(out.float()).astype(np.float64), oracle.generate(shape, of, 0, 0))
-    assert 3e-4 < r < 2e-3
+    assert 1.3e-3 < r < 2.0e-3
 
 
 def test_forward_spectrum(hf):
