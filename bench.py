@@ -40,6 +40,8 @@ WORKLOADS = {
     "2d-256": dict(shape=(256, 256), nfields=1, p=2.0, axes=(1.0, 1.0), rot=0.0, k0=0.25, width=0.05, supp=2.0,
                    levels=(0.0,), nr=128, ntheta=1),
 }
+# ragged batch: 2000 fields, sizes uniform over nine lattices, parameters drawn per field
+RAGGED = dict(count=2000, sizes=[(n, n) for n in (64, 128, 256, 512, 1024)] + [(n, n, n) for n in (32, 64, 128, 256)])
 METRIC = "voxels/s for gen+threshold+S(k)"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant pass from an ncu capture of the current kernels, keyed by
@@ -189,12 +191,90 @@ def run_reference(args, wl, name):
     print(json.dumps(line), flush=True)
 
 
+def ragged_items(hf, count, seed=0):
+    """The ragged workload: a host Philox stream (numpy) draws each field's lattice
+    uniformly from the nine sizes and its filter: p in [1, 8], semi-axes (r1, r2) in
+    2D and (1, r1, r2) in 3D with r in [0.5, 2], rotation in [0, pi), k0 in
+    [0.05, 0.4], width in [0.01, 0.1], s in {2, 4, 6}; level t in [-1, 1];
+    nr = min(128, n / 2) radial bins."""
+    import numpy as np
+
+    rng = np.random.Generator(np.random.Philox(seed))
+    items = []
+    for i in range(count):
+        shape = RAGGED["sizes"][int(rng.integers(len(RAGGED["sizes"])))]
+        r1, r2 = float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.5, 2.0))
+        axes = (r1, r2) if len(shape) == 2 else (1.0, r1, r2)
+        filt = hf.Filter(p=float(rng.uniform(1.0, 8.0)), axes=axes, rot=float(rng.uniform(0.0, math.pi)),
+                         k0=float(rng.uniform(0.05, 0.4)), width=float(rng.uniform(0.01, 0.1)),
+                         supp=float(rng.choice([2.0, 4.0, 6.0])))
+        items.append((shape, filt, seed, i, float(rng.uniform(-1.0, 1.0)), min(128, shape[0] // 2)))
+    return items
+
+
+def run_ragged(args):
+    """The ragged batch as one CUDA graph launch per step (hufield_batch_run)."""
+    import torch
+
+    from paper_2509_08675_gb300 import builder
+
+    builder.build()
+    from paper_2509_08675_gb300 import hufield as hf
+
+    torch.cuda.set_device(0)
+    items = ragged_items(hf, RAGGED["count"])
+    batch = hf.Batch(items)
+    out_f = torch.empty(batch.total_voxels, dtype=torch.float32, device="cuda")
+    maps = torch.empty(batch.total_voxels, dtype=torch.int8, device="cuda")
+    z = lambda dt: torch.zeros(batch.total_bins, dtype=dt, device="cuda")  # noqa: E731
+    sf, cf, sm, cm = z(torch.float64), z(torch.int64), z(torch.float64), z(torch.int64)
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):  # the first run captures the graph
+        hf.hufield_batch_run(batch, out_f, maps, sf, cf, sm, cm, ws, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        hf.hufield_batch_run(batch, out_f, maps, sf, cf, sm, cm, ws, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop(None)
+    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
+    voxels = int(batch.total_voxels)
+    value = args.steps * voxels / (tot_ms / 1e3)
+    n3 = sum(1 for it in items if len(it[0]) == 3)
+    n2 = len(items) - n3
+    # pass plan per field with one level: 2D 4 + 9 + 13 + 5 = 31 B/voxel, 3D 55 B/voxel
+    nbytes = sum((55 if len(it[0]) == 3 else 31) * math.prod(it[0]) for it in items)
+    peak, peak_kind = peaks()
+    gbs = nbytes / (tot_ms / args.steps / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ragged-2000", "fields_per_step": len(items), "fields_2d": n2, "fields_3d": n3,
+                       "voxels_per_step": voxels, "levels": "one per field, t in [-1, 1]",
+                       "l2": "flushed between timed steps", "parallelism": "replicas x1",
+                       "launch": "one CUDA graph per step (hufield_batch_run)"},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "traffic": None, "kernel": "whole batch graph",
+                         "peak_source": peak_kind},
+            "pipeline": {"bytes_per_voxel": round(nbytes / voxels, 2), "GBps": round(gbs, 1),
+                         "frac": round(gbs / peak, 4)},
+            "gpu_launches": args.steps * (4 * n2 + 7 * n3), "clocks": clk, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="ensemble-2d-4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ensemble-2d-4096", choices=sorted(WORKLOADS) + ["ragged-2000"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -205,6 +285,12 @@ def main():
     ap.add_argument("--noise", default="real", choices=["real", "kspace"],
                     help="white noise in real space (forward FFT) or drawn as k-space coefficients")
     args = ap.parse_args()
+    if args.workload == "ragged-2000":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the ragged batch has no oracle leg; "
+                              "use the per-workload reference arm"}))
+            return
+        return run_ragged(args)
     wl = dict(WORKLOADS[args.workload])
     if args.fields > 0:
         wl["nfields"] = args.fields
