@@ -46,7 +46,10 @@ METRIC = "voxels/s for gen+threshold+S(k)"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant pass from an ncu capture of the current kernels, keyed by
 # (workload, pass); None until captured.
-TRAFFIC = {}
+TRAFFIC = {
+    ("ensemble-2d-4096", "cols_bins"): 318.6e6,  # k_cols<12, 1, 2, -1>, 4 fields of 4096^2, per launch
+    ("3d-512", "cols_filter"): 1099.3e6,  # k_cols<9, 3, 1, -1>, 512^3
+}
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
