@@ -298,7 +298,9 @@ static void filter_inverse_normalise(int ndim, const int64_t *n, const or_filter
         var += d * d;
     }
     var /= (double)N;
-    double scale = sigma_f / sqrt(var);
+    /* Eq. (15) needs Var > 0; a filter with no power on the lattice gives g = 0,
+     * and then f = 0 */
+    double scale = var > 0.0 ? sigma_f / sqrt(var) : 0.0;
     for (int64_t i = 0; i < N; ++i) out_f[i] = (a[2 * i] / (double)N - mean) * scale;
 }
 

@@ -211,3 +211,14 @@ def test_pipeline_consistency():
     np.testing.assert_array_equal(out["sums_m"][1], s)
     np.testing.assert_array_equal(out["counts_m"][1], c)
     np.testing.assert_array_equal(out["counts_f"], c)
+
+
+def test_filter_without_power_gives_a_zero_field():
+    # a band far outside the lattice (k0 = 3 k_Nyq, w = 0.01): A underflows to 0 at every
+    # mode, Var g = 0 and Eq. (15) is read as f = 0; the maps are all +1 at t <= 0
+    filt = Filter(p=2.0, axes=(1.0, 1.0), k0=3.0, width=0.01, supp=2.0)
+    assert oracle.filter_grid((32, 32), filt).max() == 0.0
+    r = oracle.pipeline((32, 32), filt, 1, levels=(0.0, 0.5), nr=16)
+    assert np.all(r["f"] == 0.0)
+    assert np.all(r["maps"][0] == 1) and np.all(r["maps"][1] == -1)
+    assert np.all(r["sums_f"] == 0.0)
