@@ -67,7 +67,8 @@ enum hufield_status {
     HUFIELD_ERR_WS_TOO_SMALL = 3,     /* ws_bytes below hufield_workspace_bytes() */
     HUFIELD_ERR_CUDA = 4,             /* a CUDA runtime call or launch failed */
     HUFIELD_ERR_TIMEOUT = 5,          /* reserved for bounded device-side waits */
-    HUFIELD_ERR_TOO_LARGE = 6         /* lattice larger than a fixed-size static scratch */
+    HUFIELD_ERR_TOO_LARGE = 6,        /* lattice larger than a fixed-size static scratch */
+    HUFIELD_ERR_NO_POWER = 7          /* device status: the filter is 0 at every lattice mode */
 };
 
 enum hufield_dtype { HUFIELD_F32 = 0, HUFIELD_BF16 = 1, HUFIELD_I8 = 2 };
@@ -293,12 +294,17 @@ int hufield_filter_modes(hufield_plan *plan, const hufield_filter *f, float *out
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,
                       void *stream);
 
-/* Device-side status of the most recent call that used workspace `ws`: the
- * strided passes bound every wait on their bulk copies (~1 s); one that runs
- * out leaves the call's outputs undefined, returns early and sets a bit in
- * the first word of the workspace (every call clears that word when it
- * starts, in stream order).  This function waits for `stream`, reads the word
- * and returns HUFIELD_ERR_TIMEOUT if the bit is set, HUFIELD_OK otherwise. */
+/* Device-side status of the most recent call that used workspace `ws` (every
+ * call clears the first word of its workspace when it starts, in stream
+ * order, and its kernels set bits in it).  This function waits for `stream`,
+ * reads the word and returns:
+ *   HUFIELD_ERR_TIMEOUT   a bounded wait on a bulk copy (~1 s) ran out: the
+ *                         call's outputs are undefined;
+ *   HUFIELD_ERR_NO_POWER  the filter is 0 at every lattice mode (for example a
+ *                         band beyond the Nyquist wavenumber): Eq. (15) has no
+ *                         variance to divide by, the field was set to 0 (its
+ *                         maps follow from f = 0) and no field bins were added;
+ *   HUFIELD_OK            otherwise. */
 int hufield_workspace_status(const void *ws, void *stream);
 
 /* Profiling (plans created with HUFIELD_PLAN_PROFILE): waits for the events

@@ -681,6 +681,7 @@ const char* hufield_status_string(int status) {
         case HUFIELD_ERR_CUDA: return "CUDA error";
         case HUFIELD_ERR_TIMEOUT: return "device wait timed out";
         case HUFIELD_ERR_TOO_LARGE: return "lattice larger than the static scratch";
+        case HUFIELD_ERR_NO_POWER: return "the filter passes no power on this lattice (field set to 0)";
         default: return "unknown status";
     }
 }
@@ -957,7 +958,8 @@ int hufield_workspace_status(const void* ws, void* stream) {
     unsigned word = 0;
     HF_CUDA(cudaMemcpyAsync(&word, ws, sizeof(word), cudaMemcpyDeviceToHost, s));
     HF_CUDA(cudaStreamSynchronize(s));
-    return (word & kStatusTimeout) ? HUFIELD_ERR_TIMEOUT : HUFIELD_OK;
+    if (word & kStatusTimeout) return HUFIELD_ERR_TIMEOUT;
+    return (word & kStatusNoPower) ? HUFIELD_ERR_NO_POWER : HUFIELD_OK;
 }
 
 static int check_radii(int32_t nradii, const float* radii) {

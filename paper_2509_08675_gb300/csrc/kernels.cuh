@@ -369,9 +369,12 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     // f = sigma_f * u / sqrt(sum |G|^2), u the unnormalised inverse (the mean
     // is zero because A(0) = 0): Var = sum|G|^2 / N^2 by Parseval.
     const double Pv = *a.P;
-    const float scale = (float)((double)a.sigma_f / sqrt(Pv));
+    // no power at all (a band beyond the lattice): Eq. (15) is read as f = 0
+    const bool empty = !(Pv > 0.0);
+    const float scale = empty ? 0.0f : (float)((double)a.sigma_f / sqrt(Pv));
     if (blockIdx.x == 0) {
-        if (a.sums_f) {
+        if (empty && t == 0) atomicOr(a.status, kStatusNoPower);
+        if (a.sums_f && !empty) {
             const double sN = (double)a.N / Pv;
             for (int b = t; b < a.nbins; b += G::T) a.sums_f[b] += a.P[1 + b] * sN;
         }

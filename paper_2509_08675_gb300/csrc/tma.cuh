@@ -12,6 +12,7 @@ namespace hf {
 
 // Status bits written to the workspace status word.
 constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusNoPower = 2u;  // the filter passed no power: the field was set to 0
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

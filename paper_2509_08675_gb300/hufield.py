@@ -18,7 +18,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, f"libhufield_{platform.machine()}.so")
 
-OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEOUT, ERR_TOO_LARGE = range(7)
+(OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_DIMS, ERR_WS_TOO_SMALL, ERR_CUDA, ERR_TIMEOUT, ERR_TOO_LARGE,
+ ERR_NO_POWER) = range(8)
 F32, BF16, I8 = 0, 1, 2
 PLAN_PROFILE = 1
 PLAN_INJECT_TIMEOUT = 2
@@ -309,7 +310,7 @@ def hufield_spectrum_noalloc(shape, y: torch.Tensor, nr: int, ntheta: int, accum
 
 
 def hufield_workspace_status(ws: torch.Tensor, stream=None) -> int:
-    """Status of the most recent call on `ws` (waits for the stream): OK or ERR_TIMEOUT."""
+    """Status of the most recent call on `ws` (waits for the stream): OK, ERR_TIMEOUT or ERR_NO_POWER."""
     return int(_lib.hufield_workspace_status(_ptr(ws), _stream(stream)))
 
 

@@ -36,6 +36,8 @@ def test_status_strings_without_a_gpu():
     lib.hufield_status_string.restype = ctypes.c_char_p
     assert lib.hufield_status_string(0) == b"ok"
     assert lib.hufield_status_string(3) == b"workspace too small"
+    assert lib.hufield_status_string(7).startswith(b"the filter passes no power")
+    assert lib.hufield_status_string(99) == b"unknown status"
     lib.hufield_workspace_bytes.restype = ctypes.c_size_t
     assert lib.hufield_workspace_bytes(None, 0, 0) == 0
 

@@ -142,3 +142,22 @@ def test_plan_cached_bins(hf, shape, nr, nt):
     other = run_pipeline(hf, cached, gf, shape, 3, 1, levels, nr // 2, nt, nfields=1)
     want = oracle.pipeline(shape, of, 3, 1, levels=levels, nr=nr // 2, ntheta=nt)
     check_bins(other["sums_f"], want["sums_f"], other["counts_f"], want["counts_f"])
+
+
+def test_filter_without_power(hf):
+    # a band beyond the Nyquist wavenumber: A = 0 at every mode, Eq. (15) is read as f = 0;
+    # the call reports it in the workspace status and adds no field bins
+    shape, levels = (64, 32), (0.0, 0.5)
+    gf, of = filters(hf, p=2.0, axes=(1.0, 1.0), k0=3.0, width=0.01, supp=2.0)
+    plan = hf.Plan(shape)
+    got = run_pipeline(hf, plan, gf, shape, 1, 0, levels, 16, 1)
+    ws = plan.workspace(len(levels), 16)
+    f = torch.empty(shape, device="cuda")
+    hf.hufield_generate(plan, gf, 1, 0, f, ws)
+    assert hf.hufield_workspace_status(ws) == hf.ERR_NO_POWER
+    assert bool((f == 0).all())
+    want = oracle.pipeline(shape, of, 1, 0, levels=levels, nr=16)
+    assert np.all(got["f"] == 0.0) and np.all(got["sums_f"] == 0.0)
+    np.testing.assert_array_equal(got["maps"][0][: len(levels)], want["maps"])
+    for t in range(len(levels)):
+        check_bins(got["sums_m"][t], want["sums_m"][t], got["counts_m"][t], want["counts_m"][t])
