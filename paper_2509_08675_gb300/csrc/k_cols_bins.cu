@@ -27,7 +27,7 @@ KernelInfo cols_kernel_bins(int log2l, bool big, int mode, int dir) {
             if (mode == 2 && dir == -1) return big ? cols_info<9, 3, 2, -1>() : cols_info<9, 1, 2, -1>();
             return {};
         case 10:
-            if (mode == 2 && dir == -1) return big ? cols_info<10, 2, 2, -1>() : cols_info<10, 1, 2, -1>();
+            if (mode == 2 && dir == -1) return big ? cols_info<10, 3, 2, -1>() : cols_info<10, 1, 2, -1>();
             return {};
         case 11:
             if (mode == 2 && dir == -1) return big ? cols_info<11, 2, 2, -1>() : cols_info<11, 1, 2, -1>();

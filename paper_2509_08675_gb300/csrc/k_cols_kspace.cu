@@ -28,7 +28,7 @@ KernelInfo cols_kernel_kspace(int log2l, bool big, int mode, int dir) {
             if (mode == 3 && dir == -1) return big ? cols_info<9, 3, 3, -1>() : cols_info<9, 1, 3, -1>();
             return {};
         case 10:
-            if (mode == 3 && dir == -1) return big ? cols_info<10, 2, 3, -1>() : cols_info<10, 1, 3, -1>();
+            if (mode == 3 && dir == -1) return big ? cols_info<10, 3, 3, -1>() : cols_info<10, 1, 3, -1>();
             return {};
         case 11:
             if (mode == 3 && dir == -1) return big ? cols_info<11, 2, 3, -1>() : cols_info<11, 1, 3, -1>();

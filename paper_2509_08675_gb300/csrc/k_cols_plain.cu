@@ -34,8 +34,8 @@ KernelInfo cols_kernel_plain(int log2l, bool big, int mode, int dir) {
             if (mode == 0 && dir == 1) return big ? cols_info<9, 3, 0, 1>() : cols_info<9, 1, 0, 1>();
             return {};
         case 10:
-            if (mode == 0 && dir == -1) return big ? cols_info<10, 2, 0, -1>() : cols_info<10, 1, 0, -1>();
-            if (mode == 0 && dir == 1) return big ? cols_info<10, 2, 0, 1>() : cols_info<10, 1, 0, 1>();
+            if (mode == 0 && dir == -1) return big ? cols_info<10, 3, 0, -1>() : cols_info<10, 1, 0, -1>();
+            if (mode == 0 && dir == 1) return big ? cols_info<10, 3, 0, 1>() : cols_info<10, 1, 0, 1>();
             return {};
         case 11:
             if (mode == 0 && dir == -1) return big ? cols_info<11, 2, 0, -1>() : cols_info<11, 1, 0, -1>();

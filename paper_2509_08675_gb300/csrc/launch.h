@@ -20,7 +20,7 @@ struct KernelInfo {
 // log2 lines per tile of each variant
 constexpr int row_logtr(int log2m, bool big) { return big ? (log2m <= 4 ? 8 : 12 - log2m) : 0; }
 constexpr int col_logtb(int log2l, bool big) {
-    return big ? (log2l <= 4 ? 8 : (log2l >= 11 ? 13 - log2l : 12 - log2l)) : 1;
+    return big ? (log2l <= 4 ? 8 : (log2l >= 10 ? 13 - log2l : 12 - log2l)) : 1;
 }
 
 KernelInfo r2c_kernel(int log2m, bool big, int src);

@@ -65,3 +65,33 @@ def test_error_leaves_outputs_untouched(hf):
         hf.hufield_generate(plan, hf.Filter(p=-1.0), 0, 0, out, ws)
     torch.cuda.synchronize()
     assert bool((out == 7.0).all())
+
+
+def test_largest_lattice_and_empty_ensemble(hf):
+    # N = 2^31 voxels is the largest lattice a plan takes; one voxel more of any axis
+    # is refused above.  The field there still has mean 0 and variance 1 (Eq. 15).
+    shape = (2048, 1024, 1024)
+    plan = hf.Plan(shape)
+    ws = plan.workspace(0, 0)
+    f = torch.empty(shape, dtype=torch.float32, device="cuda")
+    hf.hufield_generate(plan, hf.Filter(p=2.0, axes=(1.0, 1.0, 1.0), k0=0.3, width=0.1, supp=2.0), 5, 0, f, ws)
+    torch.cuda.synchronize()
+    assert hf.hufield_workspace_status(ws) == hf.OK
+    mean = float(f.double().mean())
+    var = float(f.double().square().mean())
+    assert abs(mean) < 1e-6 and abs(var - 1.0) < 2e-5, (mean, var)
+    del f, ws
+    torch.cuda.empty_cache()
+    # an ensemble of no fields is an argument error and writes nothing
+    small = hf.Plan((32, 32))
+    wss = small.workspace(1, 8)
+    out = torch.full((1, 32, 32), 7.0, device="cuda")
+    maps = torch.full((1, 1, 32, 32), 3, dtype=torch.int8, device="cuda")
+    s = torch.full((8,), 2.0, dtype=torch.float64, device="cuda")
+    c = torch.full((8,), 4, dtype=torch.int64, device="cuda")
+    with pytest.raises(hf.HufieldError) as e:
+        hf.hufield_ensemble(small, hf.Filter(), 0, 0, 0, out, [0.0], maps, 8, 1, False, s, c, s, c, wss)
+    assert e.value.status == hf.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all()) and bool((maps == 3).all())
+    assert bool((s == 2.0).all()) and bool((c == 4).all())

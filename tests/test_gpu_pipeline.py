@@ -63,6 +63,32 @@ def test_pipeline_parity(hf, name, shape, fk, levels, nr, nt):
     compare(got, want, levels, int(np.prod(shape)))
 
 
+def wide_tile(L):
+    """Columns per tile of the strided pass of length L with enough columns for its
+    wide tile: 256 up to L = 16, 4096 / L up to 512, 8192 / L from 1024."""
+    return 256 if L <= 16 else (4096 // L if L <= 512 else 8192 // L)
+
+
+AXIS_LENGTHS = [1 << k for k in range(3, 13)]
+
+
+@pytest.mark.parametrize("noise", ["real", "kspace"])
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("L", AXIS_LENGTHS)
+def test_every_axis_length(hf, L, ndim, noise):
+    # each strided-pass length in both its tile widths: a few columns (narrow tile) and
+    # two wide tiles' worth (n_last / 2 = 2 TB), along axis 0 (2D) and the middle axis (3D)
+    w = max(8, 2 * wide_tile(L))
+    for shape in ([(L, 8), (L, w)] if ndim == 2 else [(8, L, 8), (8, L, w)]):
+        fk = dict(p=2.0, axes=(1.0,) * ndim, k0=0.3, width=0.1, supp=2.0)
+        gf, of = filters(hf, **fk)
+        plan = hf.Plan(shape, kspace=noise == "kspace")
+        nt = 2 if ndim == 2 else 1
+        got = run_pipeline(hf, plan, gf, shape, 3, 1, (0.0,), 16, nt)
+        want = oracle.pipeline(shape, of, 3, 1, levels=(0.0,), nr=16, ntheta=nt, noise=noise)
+        compare(got, want, (0.0,), int(np.prod(shape)))
+
+
 def test_pipeline_no_levels(hf):
     shape = (64, 64)
     gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
