@@ -23,7 +23,7 @@ KernelInfo c2r_info() {
 
 template <int LOG2L, int LOGTB, int MODE, int DIR>
 KernelInfo cols_info() {
-    using CG = ColGeo<LOG2L, LOGTB>;
+    using CG = ColGeo<LOG2L, LOGTB, MODE>;
     return {reinterpret_cast<const void*>(&k_cols<LOG2L, LOGTB, MODE, DIR>), CG::G::T, LOGTB, CG::fixed_bytes};
 }
 

@@ -624,18 +624,27 @@ constexpr int staging_pad() {
     return best;
 }
 
-template <int LOG2L, int LOGTB>
+// Tile buffers of a strided pass: three for the plain passes (pure
+// streaming: a third tile in flight covers more of the HBM latency) where
+// they fit in 220 KB with the stage tables, else two.
+constexpr int col_buffers(int mode, size_t tile_bytes, size_t table_bytes) {
+    return (mode == kModePlain && 3 * tile_bytes + table_bytes <= 220 * 1024) ? 3 : 2;
+}
+
+template <int LOG2L, int LOGTB, int MODE>
 struct ColGeo {
     using G = Geo<LOG2L, LOGTB, false>;
     static constexpr int tile_elems = G::TB * G::L;
-    // dynamic shared memory before the bins: two tile buffers, the stage twiddles, two mbarriers
-    static constexpr size_t fixed_bytes = (size_t)2 * tile_elems * 8 + (size_t)plan_twiddle_slots<LOG2L>() * 8 + 16;
+    static constexpr int nbuf = col_buffers(MODE, (size_t)tile_elems * 8, (size_t)plan_twiddle_slots<LOG2L>() * 8);
+    // dynamic shared memory before the bins: the tile buffers, the stage twiddles, one mbarrier per buffer
+    static constexpr size_t fixed_bytes =
+        (size_t)nbuf * tile_elems * 8 + (size_t)plan_twiddle_slots<LOG2L>() * 8 + (size_t)nbuf * 8;
 };
 
 template <int LOG2L, int LOGTB, int MODE, int DIR>
 __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(MODE, Geo<LOG2L, LOGTB, false>::T))
     k_cols(const __grid_constant__ ColArgs a) {
-    using CG = ColGeo<LOG2L, LOGTB>;
+    using CG = ColGeo<LOG2L, LOGTB, MODE>;
     using G = typename CG::G;
     constexpr int L = G::L;
     constexpr int E = G::E;
@@ -654,11 +663,13 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     static_assert(TB >= 2, "k-space mode pairs rely on two columns per tile");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int tile_elems = CG::tile_elems;
-    float2* const buf0 = reinterpret_cast<float2*>(smem_raw);  // two tile buffers: buf0 + s tile_elems
-    float2* twf = buf0 + 2 * tile_elems;  // stage tables: forward plan, then its reverse
+    constexpr int NBUF = CG::nbuf;
+    static_assert(NBUF == 2 || kLoad, "the k-space mode's store ring assumes two buffers");
+    float2* const buf0 = reinterpret_cast<float2*>(smem_raw);  // NBUF tile buffers: buf0 + s tile_elems
+    float2* twf = buf0 + NBUF * tile_elems;  // stage tables: forward plan, then its reverse
     uint64_t* bar = reinterpret_cast<uint64_t*>(twf + plan_twiddle_slots<LOG2L>());
     const int nb = a.bp.nbins;
-    double* dbin = reinterpret_cast<double*>(bar + 2);   // nb + 1 (last: Parseval)
+    double* dbin = reinterpret_cast<double*>(bar + NBUF);   // nb + 1 (last: Parseval)
     float* fbin = reinterpret_cast<float*>(dbin + nb + 1);  // nb + 1
     float* tab0 = fbin + nb + 1;                          // FILTER: p log2 |kappa_0 / a|, L
     const int t = threadIdx.x;
@@ -677,8 +688,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
 
     float2* twi = load_plan_twiddles<LOG2L>(twf, a.tw, t, T);
     if (t == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+#pragma unroll
+        for (int q = 0; q < NBUF; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
     if constexpr (kFilt) {
@@ -698,7 +709,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     __syncthreads();
     if (kLoad && t == 0) {
         if (t0 < t1 && !a.inject_skip) issue(t0, buf0, &bar[0]);
-        if (t0 + 1 < t1) issue(t0 + 1, buf0 + tile_elems, &bar[1]);
+#pragma unroll
+        for (int q = 1; q < NBUF; ++q)
+            if (t0 + q < t1) issue(t0 + q, buf0 + q * tile_elems, &bar[q]);
     }
 
     auto flush = [&](long long batch) {
@@ -719,7 +732,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     long long cur = -1;
     long long failed_at = -1;
     for (long long ti = t0; ti < t1; ++ti) {
-        const int s = (int)((ti - t0) & 1);
+        const int s = (int)((ti - t0) % NBUF);
         float2* buf = buf0 + s * tile_elems;
         if constexpr (kLoad) {
             if (!cta_wait(&bar[s], (phases >> s) & 1u, a.wait_budget)) {
@@ -911,7 +924,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                 }
             }
         }
-        // the tile's results are in buf: store them, then refill buf with tile i+2
+        // the tile's results are in buf: store them, then refill buf with tile i+NBUF
         fence_proxy_async_smem();
         __syncthreads();
         if (t == 0) {
@@ -920,9 +933,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                 for (int y = 0; y < L; y += LB) tma_store_3d(&a.map, (int)c0, y, (int)ab, buf + y * TB);
                 bulk_commit();
             }
-            if (kLoad && ti + 2 < t1) {
+            if (kLoad && ti + NBUF < t1) {
                 if constexpr (kStore) bulk_wait_read_all();
-                issue(ti + 2, buf, &bar[s]);
+                issue(ti + NBUF, buf, &bar[s]);
             }
         }
         if constexpr (kAcc) {
@@ -936,11 +949,14 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     if (failed_at >= 0) {
         if (t == 0) {
             atomicOr(a.status, kStatusTimeout);
-            // drain this CTA's own loads still in flight (bounded), then its stores
-            const int s = (int)((failed_at - t0) & 1);
-            const bool issued = !(a.inject_skip && failed_at == t0);
-            if (issued) mbar_wait_bounded(&bar[s], (phases >> s) & 1u, a.wait_budget);
-            if (failed_at + 1 < t1) mbar_wait_bounded(&bar[s ^ 1], (phases >> (s ^ 1)) & 1u, a.wait_budget);
+            // drain this CTA's own loads still in flight (bounded): tiles
+            // failed_at .. failed_at + NBUF - 1 were issued (all but a skipped
+            // first load), none of them waited for yet; then its stores
+            for (int q = 0; q < NBUF && failed_at + q < t1; ++q) {
+                if (q == 0 && a.inject_skip && failed_at == t0) continue;
+                const int s = (int)((failed_at + q - t0) % NBUF);
+                mbar_wait_bounded(&bar[s], (phases >> s) & 1u, a.wait_budget);
+            }
             if constexpr (kStore) bulk_wait_all();
         }
         __syncthreads();
