@@ -150,6 +150,7 @@ struct FilterParams {
     float two_k0;
     float half_s;       // s / 2                 H = 2^(s/2 (log2 K - log2 K*) - c d),
     float c_d;          // log2(e) / (4 w^2)     d = (K - k0)^2 - (K* - k0)^2
+    float u_zero;       // p log2 K from which the exponent is below -140: H flushes to 0 exactly
 };
 
 // Binning parameters; the angle table lives in shared memory at run time.

@@ -1,6 +1,7 @@
 // hufield.cu -- C ABI (include/hufield.h): plans, argument checks, workspace
 // layout and the launch sequence of the passes, plus the small kernels
 // (twiddle table, noise, sign maps, bin counts, bin finalisation).
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -355,6 +356,40 @@ int check_filter(const hufield_plan* p, const hufield_filter* f) {
     return HUFIELD_OK;
 }
 
+// u = p log2 K from which the amplitude exponent x(K) = s/2 (log2 K - log2 K*)
+// - c (K - K*)(K + K* - 2 k0) is below -140, with the FP32 parameters the
+// kernels use.  x is concave with its maximum at K*, so past that point it
+// only falls; 2^x then flushes to 0 in ex2.approx.ftz with 14 units of the
+// exponent to spare for the rounding of K, log2 S and the parameters.  A
+// mode whose largest term p log2 |kappa'_i / a_i| reaches u has log2 S >= u
+// and so A = 0 exactly: the kernels skip its amplitude.  FLT_MAX when no such
+// K is found.
+float zero_bound(const FilterParams& fp) {
+    const double hs = fp.half_s, l2ks = fp.log2_kstar, cd = fp.c_d, ks = fp.kstar, tk0 = fp.two_k0;
+    auto x = [&](double K) { return hs * (log2(K) - l2ks) - cd * (K - ks) * (K + ks - tk0); };
+    const double limit = -140.0;
+    double lo = ks > 1e-30 ? ks : 1e-30;
+    if (x(lo) <= limit) return FLT_MAX;  // not expected (x(K*) = 0): never skip
+    double step = 1e-3, hi = lo + step;
+    int grow = 0;
+    while (x(hi) > limit) {
+        if (++grow > 200) return FLT_MAX;
+        step *= 2.0;
+        hi = lo + step;
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (x(mid) <= limit)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    const double u = (double)fp.p * log2(hi);
+    float uf = (float)u;
+    if ((double)uf < u) uf = nextafterf(uf, FLT_MAX);
+    return uf;
+}
+
 FilterParams make_filter(const hufield_plan* p, const hufield_filter* f) {
     FilterParams fp{};
     for (int d = 0; d < 3; ++d) fp.inv_a[d] = (float)(1.0 / (double)(d < p->ndim ? f->axes[d] : 1.0f));
@@ -373,6 +408,7 @@ FilterParams make_filter(const hufield_plan* p, const hufield_filter* f) {
     fp.two_k0 = (float)(2.0 * k0);
     fp.half_s = (float)(0.5 * s);
     fp.c_d = (float)(1.0 / (4.0 * w * w * log(2.0)));
+    fp.u_zero = zero_bound(fp);
     return fp;
 }
 
@@ -456,8 +492,54 @@ bool aligned(const void* ptr) { return ((uintptr_t)ptr & 255) == 0; }
         if ((expr) != cudaSuccess) return HUFIELD_ERR_CUDA; \
     } while (0)
 
-// Strided pass along axis 1 (3D) over `nbatch` spectra of N/2 modes each.
-int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind, unsigned* status, cudaStream_t s) {
+// The tiles a strided pass runs when only the columns with k_last < kz hold
+// nonzero data (kz = M: all): per row of M / TB tiles along k_last, the first
+// ceil(kz / TB); every tile when a tile spans more than one row.  Caps the
+// grid at the tiles run.
+void set_tiles(const hufield_plan* p, ColArgs& ca, int logtb, long long kz, Launch& L) {
+    const long long M = 1ll << p->logM, TB = 1ll << logtb, per_batch = ca.B >> logtb;
+    if (kz < M && TB <= M) {
+        ca.row_tiles = (int)(M >> logtb);
+        ca.live_tiles = (int)((kz + TB - 1) >> logtb);
+        ca.tpb = per_batch / ca.row_tiles * ca.live_tiles;
+        if (ca.live_tiles == 0) ca.live_tiles = 1;  // nothing runs (tpb = 0); keeps the divisor nonzero
+    } else {
+        ca.row_tiles = ca.live_tiles = 1;
+        ca.tpb = per_batch;
+    }
+    ca.ntiles = ca.A * ca.tpb;
+    if ((long long)L.grid > ca.ntiles) L.grid = (int)(ca.ntiles > 0 ? ca.ntiles : 1);
+}
+
+// The first k_last from which every mode of the filter is exactly zero (M
+// when there is none): all its modes have a term p log2 |kappa'_i / a_i| at or
+// above u_zero (zero_bound).  3D: the term of the last axis, which the
+// rotation (about that axis) leaves alone.  2D: along the column kappa_1 =
+// const every point of the plane has max_i |kappa'_i| / a_i >= r = 2^(u_zero /
+// p) once the column misses the rotated rectangle |kappa'_i| < r a_i, whose
+// extent in kappa_1 is r (a_0 |sin| + a_1 |cos|).  A relative margin of 1e-6
+// covers the rounding of the FP32 terms.
+long long zero_kz(const hufield_plan* p, const FilterParams& fp) {
+    const long long M = 1ll << p->logM;
+    if (!(fp.u_zero < FLT_MAX)) return M;
+    const double r = exp2((double)fp.u_zero / (double)fp.p) * (1.0 + 1e-6);
+    double lim;  // |kappa_last| at and beyond which the column is zero
+    if (p->ndim == 3) {
+        lim = r / (double)fp.inv_a[2];
+    } else if (fp.rotated) {
+        lim = r * (fabs((double)fp.sr) / (double)fp.inv_a[0] + fabs((double)fp.cr) / (double)fp.inv_a[1]);
+    } else {
+        lim = r / (double)fp.inv_a[1];
+    }
+    const double k = ceil(lim * (double)(M << 1) * 0.5);  // kappa_last = 2 k / n_last, n_last = 2 M
+    if (!(k < (double)M)) return M;
+    return k > 0.0 ? (long long)k : 0;
+}
+
+// Strided pass along axis 1 (3D) over `nbatch` spectra of N/2 modes each;
+// only the columns k_last < kz are read and written.
+int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind, unsigned* status, cudaStream_t s,
+             long long kz = -1) {
     ColArgs ca{};
     ca.data = data;
     ca.B = 1ll << p->logM;
@@ -470,7 +552,7 @@ int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind,
     Launch L;
     KernelInfo k;
     if (!col_launch(p, p->log2n[1], kModePlain, dir, ca.B, ca.A, 0, k, L)) return HUFIELD_ERR_CUDA;
-    ca.ntiles = ca.A * (ca.B >> k.log2_lines);
+    set_tiles(p, ca, k.log2_lines, kz < 0 ? ca.B : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[1], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     HF_CUDA(launch(p, kind, k.fn, L, &ca, s));
     return HUFIELD_OK;
@@ -496,10 +578,11 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
     return HUFIELD_OK;
 }
 
-// Strided pass along axis 0 over `nbatch` spectra of N/2 modes each.
+// Strided pass along axis 0 over `nbatch` spectra of N/2 modes each; the
+// filter passes run only the columns k_last < kz (kz < 0: all).
 int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const FilterParams* fp,
                const BinParams& bp, const unsigned short* bintab, double* gbins, double* gP, unsigned* status,
-               cudaStream_t s, uint64_t seed = 0, uint32_t field_idx = 0) {
+               cudaStream_t s, uint64_t seed = 0, uint32_t field_idx = 0, long long kz = -1) {
     ColArgs ca{};
     ca.seed = seed;
     ca.field_idx = field_idx;
@@ -529,7 +612,7 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     Launch L;
     KernelInfo k;
     if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, extra, k, L)) return HUFIELD_ERR_CUDA;
-    ca.ntiles = ca.A * (ca.B >> k.log2_lines);
+    set_tiles(p, ca, k.log2_lines, kz < 0 ? (1ll << p->logM) : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     const int kind = (mode == kModeFilter || mode == kModeKspace) ? kPassFilter
                      : mode == kModeBins                           ? kPassBins
@@ -612,21 +695,25 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     const BinParams& b = bp ? *bp : none;
     double* P = w.acc[set & 1];
     double* raw = P + 1;
+    // past the filter's band the spectrum is exactly zero: the passes after
+    // the forward transform skip the columns k_last >= kz (c2r reads zeros there)
+    const long long kz = zero_kz(p, fp);
     int rc;
     if (p->kspace) {
         // the noise coefficients are drawn inside the axis-0 pass: no forward passes
-        rc = axis0_pass(p, kModeKspace, w.spec, 1, &fp, b, tab, raw, P, w.status, s, seed, field_idx);
+        rc = axis0_pass(p, kModeKspace, w.spec, 1, &fp, b, tab, raw, P, w.status, s, seed, field_idx, kz);
     } else {
         rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
         if (rc) return rc;
-        rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, raw, P, w.status, s);
+        rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, raw, P, w.status, s, 0, 0, kz);
     }
     if (rc) return rc;
     if (p->ndim == 3) {
-        rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s);
+        rc = mid_pass(p, +1, w.spec, 1, kPassMidInv, w.status, s, kz);
         if (rc) return rc;
     }
     C2RArgs ca{};
+    ca.kz = (int)kz;
     ca.sums_f = bp ? sums_f : nullptr;
     ca.nbins = b.nbins;
     ca.next_acc = w.acc[(set + 1) & 1];

@@ -59,6 +59,7 @@ struct C2RArgs {
     unsigned* status;       // workspace status word (kStatusTimeout)
     long long wait_budget;  // clock cycles allowed per mbarrier wait
     int inject_skip;        // test hook: 1 = the first tile's load is never issued
+    int kz;                 // entries k_last >= kz of each row are zero (<= M)
 };
 
 struct ColArgs {
@@ -67,7 +68,12 @@ struct ColArgs {
     long long B;            // contiguous columns
     long long A;            // batches
     long long bstride;
-    long long ntiles;       // A * B / TB
+    long long ntiles;       // A * tpb
+    // Tiles that are run: the columns form rows of row_tiles tiles, of which
+    // the first live_tiles of each row are run (all with row_tiles =
+    // live_tiles = 1); tpb of them per batch.
+    long long tpb;
+    int row_tiles, live_tiles;
     const float2* tw;
     // mode decoding for the pass along axis 0 (FILTER, BINS)
     int ndim;
@@ -154,7 +160,8 @@ __device__ __forceinline__ float filter_amplitude(const FilterParams& fp, float 
     const float u1 = plog2(fabsf(yr) * fp.inv_a[1], fp.p);
     const float u2 = ndim == 3 ? plog2(fabsf(z) * fp.inv_a[2], fp.p) : kLog2Zero;
     const float m = fmaxf(fmaxf(u0, u1), u2);
-    if (m < 0.5f * kLog2Zero) return 0.0f;
+    // log2 S >= m: K is zero, or far enough out that the power of two flushes to 0
+    if (m < 0.5f * kLog2Zero || m >= fp.u_zero) return 0.0f;
     return amplitude_from_log2s(fp, m + fast_lg2(fast_ex2(u0 - m) + fast_ex2(u1 - m) + fast_ex2(u2 - m)));
 }
 
@@ -382,6 +389,11 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     }
     long long t0, t1;
     chunk_of(a.nrows >> LOGTR, t0, t1);
+    // Entries k_last >= kz are zero (the filter's band ends before them) and
+    // were not written by the passes before: they are loaded with the rest of
+    // the tile (one bulk copy measured faster than a copy per row of the
+    // entries below kz) and read as zero.
+    const int kz = a.kz;
     auto issue = [&](long long tile, float2* dst, uint64_t* b) {
         mbar_arrive_expect_tx(b, tile_bytes);
         bulk_load(dst, a.spec + tile * tile_elems, tile_bytes, b);
@@ -413,11 +425,11 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
         // c2r pre-processing: Z[k] = (X[k] + X*[M-k]) + i (X[k] - X*[M-k]) W_N^{-k}
         for_each_element<G, PI::first_radix()>(t, [&](int e, int b, int k) {
             const float2* rowp = buf + (b << LOG2M);
-            float2 X = rowp[k];
+            float2 X = k < kz ? rowp[k] : make_float2(0.0f, 0.0f);
             float2 Xmc = make_float2(0.0f, 0.0f);
             if (k == 0) {
                 X.y = 0.0f;  // the DC of a real row is real; the Nyquist term is zero
-            } else {
+            } else if (M - k < kz) {
                 Xmc = cconj(rowp[M - k]);
             }
             const float2 ep = cadd(X, Xmc);
@@ -676,11 +688,25 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
 
     long long t0, t1;
     chunk_of(a.ntiles, t0, t1);
-    const long long tpb = a.B >> LOGTB;
+    // run tile ti: batch ab, tile tcol of the batch in the full tile order
+    // (tile counts stay below 2^31: 32-bit divisions, the second one only
+    // when columns are skipped)
+    auto tile_of = [&](long long ti, long long& ab, long long& tcol) {
+        const unsigned q = (unsigned)ti / (unsigned)a.tpb;
+        const unsigned r = (unsigned)ti - q * (unsigned)a.tpb;
+        ab = q;
+        if (a.live_tiles == a.row_tiles) {
+            tcol = r;
+        } else {
+            const unsigned row = r / (unsigned)a.live_tiles;
+            tcol = (long long)row * a.row_tiles + (r - row * (unsigned)a.live_tiles);
+        }
+    };
     constexpr uint32_t tile_bytes = (uint32_t)tile_elems * (uint32_t)sizeof(float2);
     auto issue = [&](long long ti, float2* dst, uint64_t* b) {
-        const long long ab = ti / tpb;
-        const int c0 = (int)((ti - ab * tpb) << LOGTB);
+        long long ab, tcol;
+        tile_of(ti, ab, tcol);
+        const int c0 = (int)(tcol << LOGTB);
         mbar_arrive_expect_tx(b, tile_bytes);
 #pragma unroll
         for (int y = 0; y < L; y += LB) tma_load_3d(dst + y * TB, &a.map, c0, y, (int)ab, b);
@@ -746,8 +772,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
             // every thread wait for this
             if (t == 0) bulk_wait_read_1();
         }
-        const long long ab = ti / tpb;
-        const long long c0 = (ti - ab * tpb) << LOGTB;
+        long long ab, tcol;
+        tile_of(ti, ab, tcol);
+        const long long c0 = tcol << LOGTB;
         if constexpr (MODE == kModeBins) {
             if (ab != cur) {
                 if (cur >= 0) flush(cur);
@@ -761,7 +788,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
             if (nb > 0) {
                 // E entries per thread (E/2 pair bins when paired, see stage_o)
                 const int per = (kPairable && a.bp.ntheta == 1) ? E / 2 : E;
-                const unsigned short* src = a.bintab + (ti - ab * tpb) * (tile_elems / E * per) + t * per;
+                const unsigned short* src = a.bintab + tcol * (tile_elems / E * per) + t * per;
                 if (per == E / 2 && E >= 16) {
 #pragma unroll
                     for (int q = 0; q < E / 16; ++q) {
@@ -858,14 +885,22 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                     for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) {
                         if constexpr (kFilt) {
                             float h = 0.0f;
-                            if (!nyq_col && l != L / 2) {
-                                if (!a.fp.rotated) {
-                                    h = amplitude_from_log2s(a.fp, log2_sum2(tab0[l], u_col));
-                                } else {
-                                    const float x =
-                                        (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                                    h = filter_amplitude(a.fp, x, y, z, a.ndim);
+                            const bool live = !nyq_col && l != L / 2;
+                            if (!a.fp.rotated) {
+                                // log2 S >= the larger term: from u_zero on A is 0 exactly.
+                                // The warp skips the amplitude when none of its
+                                // lanes needs it (every thread of the CTA runs this loop).
+                                constexpr unsigned kWarp = T >= 32 ? 0xffffffffu : (1u << T) - 1u;
+                                const float t0 = tab0[l];
+                                const bool need = live && fmaxf(t0, u_col) < a.fp.u_zero;
+                                if (__any_sync(kWarp, need)) {
+                                    const float hv = amplitude_from_log2s(a.fp, log2_sum2(t0, u_col));
+                                    h = need ? hv : 0.0f;
                                 }
+                            } else if (live) {
+                                const float x =
+                                    (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                                h = filter_amplitude(a.fp, x, y, z, a.ndim);
                             }
                             v[e] = cscale(v[e], h);
                         }

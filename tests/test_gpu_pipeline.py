@@ -89,6 +89,52 @@ def test_every_axis_length(hf, L, ndim, noise):
         compare(got, want, (0.0,), int(np.prod(shape)))
 
 
+# Narrow bands (Eqs. 12-13) end well inside the lattice: past the band the
+# filtered spectrum is exactly zero in FP32, and the passes after the forward
+# transform skip the columns k_last >= kz where every mode is zero.  Cases with
+# kz odd, kz inside a tile, rotated 2D and 3D filters, the paper's form and
+# small lattices whose tiles span several rows.
+BAND_CASES = [
+    ("2d-256", (256, 256), dict(p=2.0, axes=(1.0, 1.0), k0=0.2, width=0.02, supp=2.0), 16, 1),
+    ("2d-rot-128x512", (128, 512), dict(p=3.0, axes=(1.0, 0.5), rot=0.7, k0=0.15, width=0.02, supp=4.0), 16, 6),
+    ("2d-paper-64", (64, 64), dict(p=1.0, axes=(1.0, 0.5), width=0.05, supp=2.0, form=1), 16, 1),
+    ("2d-256x16", (256, 16), dict(p=2.0, axes=(1.0, 1.0), k0=0.2, width=0.03, supp=2.0), 16, 1),
+    ("3d-32x64x128", (32, 64, 128), dict(p=6.0, axes=(1.0, 1.0, 0.5), k0=0.2, width=0.03, supp=2.0), 16, 1),
+    ("3d-rot-64x32x64", (64, 32, 64), dict(p=2.5, axes=(1.0, 0.7, 0.6), rot=1.1, k0=0.15, width=0.03, supp=2.0),
+     16, 1),
+    ("3d-16x1024x64", (16, 1024, 64), dict(p=2.0, axes=(1.0, 1.0, 1.0), k0=0.1, width=0.02, supp=2.0), 16, 1),
+    ("3d-16^3", (16, 16, 16), dict(p=6.0, axes=(1.0, 1.0, 0.5), k0=0.2, width=0.04, supp=2.0), 8, 1),
+]
+
+
+@pytest.mark.parametrize("noise", ["real", "kspace"])
+@pytest.mark.parametrize("name,shape,fk,nr,nt", BAND_CASES, ids=[c[0] for c in BAND_CASES])
+def test_narrow_band_parity(hf, name, shape, fk, nr, nt, noise):
+    gf, of = filters(hf, **fk)
+    plan = hf.Plan(shape, kspace=noise == "kspace")
+    levels = (0.0, 0.4)
+    got = run_pipeline(hf, plan, gf, shape, 6, 3, levels, nr, nt, nfields=2)
+    sf, cf = 0.0, 0
+    sm, cm = 0.0, 0
+    for e in range(2):
+        want = oracle.pipeline(shape, of, 6, 3 + e, levels=levels, nr=nr, ntheta=nt, noise=noise)
+        check_field(got["f"][e], want["f"])
+        check_maps(got["maps"][e], want["maps"], want["f"], levels)
+        sf, cf = sf + want["sums_f"], cf + want["counts_f"]
+        sm, cm = sm + want["sums_m"], cm + want["counts_m"]
+    check_bins(got["sums_f"], sf, got["counts_f"], cf)
+    for t in range(len(levels)):
+        check_bins(got["sums_m"][t], sm[t], got["counts_m"][t], cm[t], flips=2, N=int(np.prod(shape)))
+    # generate (no bins) and BF16 output take the same passes
+    ws = plan.workspace(0, 0)
+    out = torch.empty(shape, dtype=torch.bfloat16, device="cuda")
+    hf.hufield_generate(plan, gf, 6, 3, out, ws)
+    torch.cuda.synchronize()
+    ref = oracle.pipeline(shape, of, 6, 3, levels=(), nr=nr, ntheta=nt, noise=noise)["f"]
+    err = np.linalg.norm(np_(out.float()).astype(np.float64) - ref) / np.linalg.norm(ref)
+    assert err < 2.5e-3, err
+
+
 def test_pipeline_no_levels(hf):
     shape = (64, 64)
     gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
