@@ -47,34 +47,51 @@ METRIC = "voxels/s for gen+threshold+S(k)"
 # dominant pass from an ncu capture of the current kernels, keyed by
 # (workload, pass); None until captured.
 TRAFFIC = {
-    ("ensemble-2d-4096", "cols_bins"): 318.6e6,  # k_cols<12, 1, 2, -1>, 4 fields of 4096^2, per launch
-    ("3d-512", "cols_filter"): 1099.3e6,  # k_cols<9, 3, 1, -1>, 512^3
+    ("ensemble-2d-4096", "cols_bins"): 318.5e6,  # k_cols<12, 1, 2, -1>, 3 maps of 4096^2, per launch
+    ("3d-512", "r2c"): 477.1e6,  # k_r2c<8, 4, 0>, 512^3
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
-def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False):
+def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0):
     """Bytes each pass kind must move per launch (one field), by the pass plan:
     r2c writes the half spectrum (4 B/voxel); a strided pass reads and writes it
     (8 B/voxel per spectrum; the filter pass of k-space noise only writes it);
     c2r reads it, writes the field, nlev sign maps and nlev map spectra; the
     bins pass reads the nlev map spectra; the binning passes read the bin table
     (1 B/voxel each time), which the table pass ("counts") writes once per
-    call."""
+    call.  After the filter only the columns below the band edge hold nonzero
+    data (a fraction `live` = kz / (n_last / 2) of the half spectrum): the
+    filter pass and the axis-1 inverse move that part, and c2r needs only it."""
     N = math.prod(shape)
     h = 4 * N  # half spectrum bytes
     tab = N  # bin table: one uint16 per half-spectrum mode
     return {
         "r2c": h,
         "cols_mid_fwd": 2 * h,
-        "cols_filter": (1 if kspace else 2) * h + tab,
-        "cols_mid_inv": 2 * h,
-        "c2r": h + field_bytes * N + nlev * N + nlev * h,
+        "cols_filter": ((1 if kspace else 2) * h + tab) * live,
+        "cols_mid_inv": 2 * h * live,
+        "c2r": h * live + field_bytes * N + nlev * N + nlev * h,
         "cols_mid_maps": 2 * h * nlev,
         "cols_bins": (h + tab) * nlev,
         "counts": tab,
         "misc": 0,
     }
+
+
+def field_bytes(shape, nlev, live, kspace=False, out_bytes=4):
+    """Algorithmic bytes of one field's pipeline (the passes it runs, bin table cached)."""
+    algo = algorithmic_bytes(shape, nlev, out_bytes, kspace, live)
+    keys = ["cols_filter", "c2r"] + (["cols_bins"] if nlev else [])
+    keys += [] if kspace else ["r2c"]
+    if len(shape) == 3:
+        keys += ["cols_mid_inv"] + ([] if kspace else ["cols_mid_fwd"]) + (["cols_mid_maps"] if nlev else [])
+    return sum(algo[k] for k in keys)
+
+
+def band_live(hf, plan, filt, shape):
+    """Fraction of the half spectrum below the filter's band edge (hufield_filter_band_edge)."""
+    return hf.hufield_filter_band_edge(plan, filt) / (shape[-1] // 2)
 
 
 def replica_field0(rank: int, nfields: int) -> int:
@@ -252,8 +269,10 @@ def run_ragged(args):
     value = args.steps * voxels / (tot_ms / 1e3)
     n3 = sum(1 for it in items if len(it[0]) == 3)
     n2 = len(items) - n3
-    # pass plan per field with one level: 2D 4 + 9 + 13 + 5 = 31 B/voxel, 3D 55 B/voxel
-    nbytes = sum((55 if len(it[0]) == 3 else 31) * math.prod(it[0]) for it in items)
+    # pass plan per field with one level (2D 4 + 9 + 13 + 5 = 31 B/voxel, 3D 55 B/voxel
+    # without a band edge), each field's filter and band edge
+    plans = {tuple(it[0]): hf.Plan(tuple(it[0])) for it in items}
+    nbytes = sum(field_bytes(tuple(it[0]), 1, band_live(hf, plans[tuple(it[0])], it[1], it[0])) for it in items)
     peak, peak_kind = peaks()
     gbs = nbytes / (tot_ms / args.steps / 1e3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
@@ -426,7 +445,8 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     value = world * args.steps * nf * N / (tot_ms / 1e3)
 
     # roofline of the dominant pass (live per-launch CUDA-event times of the timed steps)
-    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2, args.noise == "kspace")
+    live = band_live(hf, plan, filt, shape)
+    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2, args.noise == "kspace", live)
     peak, peak_kind = peaks()
     passes = {}
     for k, (ms, cnt) in prof.items():
@@ -444,7 +464,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
             "kernel": dom, "peak_source": peak_kind}
     return {"value": value, "ms_per_step": tot_ms / args.steps, "roofline": roof,
             "pipeline": {"bytes_per_voxel": round(per_step_bytes / (nf * N), 2), "GBps": round(pipe_gbs, 1),
-                         "frac": round(pipe_gbs / peak, 4)},
+                         "frac": round(pipe_gbs / peak, 4), "band_live": round(live, 4)},
             "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()), "clocks": clk,
             "plan": plan, "filt": filt, "bufs": (out_f, maps, sf, cf, sm, cm, ws), "field0": field0}
 

@@ -290,6 +290,15 @@ int hufield_spectrum_modes(hufield_plan *plan, const void *y, int32_t dtype, flo
                            void *stream);
 int hufield_filter_modes(hufield_plan *plan, const hufield_filter *f, float *out, void *stream);
 
+/* The filter's band edge along the last axis (Eqs. 12-13, Sec. II.B): *kz
+ * receives the first k_last from which every mode of the filter is exactly
+ * zero in FP32 (the exponent of A is below -140, far past the FP32 underflow),
+ * or n_last / 2 when there is none.  The generator's passes after the forward
+ * transform skip the columns k_last >= kz; a caller can use kz to count the
+ * bytes those passes move.  Host only, nothing is enqueued.  Errors:
+ * HUFIELD_ERR_INVALID_ARG (null pointer or a filter hufield_generate rejects). */
+int hufield_filter_band_edge(const hufield_plan *plan, const hufield_filter *f, int64_t *kz);
+
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,
                       void *stream);

@@ -1190,6 +1190,14 @@ int hufield_filter_modes(hufield_plan* p, const hufield_filter* f, float* out, v
     return HUFIELD_OK;
 }
 
+int hufield_filter_band_edge(const hufield_plan* p, const hufield_filter* f, int64_t* kz) {
+    if (!p || !kz) return HUFIELD_ERR_INVALID_ARG;
+    const int rc = check_filter(p, f);
+    if (rc) return rc;
+    *kz = (int64_t)zero_kz(p, make_filter(p, f));
+    return HUFIELD_OK;
+}
+
 int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, double* out, void* stream) {
     if (!sums || !counts || !out || nbins < 1) return HUFIELD_ERR_INVALID_ARG;
     k_bins_mean<<<(nbins + 255) / 256, 256, 0, (cudaStream_t)stream>>>(

@@ -95,6 +95,7 @@ def _load():
     lib.hufield_spectrum.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]
     lib.hufield_spectrum_modes.argtypes = [vp, vp, i32, vp, vp, sz, vp]
     lib.hufield_filter_modes.argtypes = [vp, fptr, vp, vp]
+    lib.hufield_filter_band_edge.argtypes = [vp, fptr, C.POINTER(C.c_int64)]
     lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_window_variance_filter.argtypes = [vp, fptr, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
@@ -259,6 +260,14 @@ def hufield_filter_modes(plan: Plan, filt: Filter, out: torch.Tensor, stream=Non
     """A(n)^2 over the stored half spectrum into out (float32, N/2)."""
     fc = filt._c()
     _check(_lib.hufield_filter_modes(plan.handle, C.byref(fc), _ptr(out), _stream(stream)), "hufield_filter_modes")
+
+
+def hufield_filter_band_edge(plan: Plan, filt: Filter) -> int:
+    """First k_last from which the filter is exactly zero (n_last / 2: none)."""
+    fc = filt._c()
+    kz = C.c_int64(0)
+    _check(_lib.hufield_filter_band_edge(plan.handle, C.byref(fc), C.byref(kz)), "hufield_filter_band_edge")
+    return int(kz.value)
 
 
 def _radii(radii):

@@ -107,6 +107,28 @@ BAND_CASES = [
 ]
 
 
+@pytest.mark.parametrize("name,shape,fk,nr,nt", BAND_CASES + [
+    ("C1-like-512^2", (512, 512), inputs.filter_kwargs(inputs.C1), 64, 36),
+    ("C2-like-64^3", (64, 64, 64), inputs.filter_kwargs(inputs.C2), 32, 1),
+    ("C0-256^2", (256, 256), inputs.filter_kwargs(inputs.C0), 128, 1)], ids=lambda v: v if isinstance(v, str) else None)
+def test_band_edge_is_exactly_zero(hf, name, shape, fk, nr, nt):
+    # the passes skip k_last >= kz: there the FP64 filter (Eqs. 12-13) must be
+    # far below the FP32 underflow (2^-126), for k_last and -k_last alike
+    gf, of = filters(hf, **fk)
+    plan = hf.Plan(shape)
+    kz = hf.hufield_filter_band_edge(plan, gf)
+    M = shape[-1] // 2
+    assert 0 < kz <= M
+    if name != "C0-256^2":
+        assert kz < M  # narrow bands end inside the lattice
+    H = oracle.filter_grid(shape, of)
+    klast = np.abs(np.fft.fftfreq(shape[-1], 1.0 / shape[-1]))
+    if kz < M:
+        assert np.abs(H[..., klast >= kz]).max() <= 2.0 ** -139
+    with pytest.raises(hf.HufieldError):
+        hf.hufield_filter_band_edge(plan, hf.Filter(p=-1.0, axes=(1.0,) * len(shape)))
+
+
 @pytest.mark.parametrize("noise", ["real", "kspace"])
 @pytest.mark.parametrize("name,shape,fk,nr,nt", BAND_CASES, ids=[c[0] for c in BAND_CASES])
 def test_narrow_band_parity(hf, name, shape, fk, nr, nt, noise):
