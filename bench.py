@@ -60,15 +60,16 @@ def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0):
     c2r reads it, writes the field, nlev sign maps and nlev map spectra; the
     bins pass reads the nlev map spectra; the binning passes read the bin table
     (1 B/voxel each time), which the table pass ("counts") writes once per
-    call.  After the filter only the columns below the band edge hold nonzero
-    data (a fraction `live` = kz / (n_last / 2) of the half spectrum): the
-    filter pass and the axis-1 inverse move that part, and c2r needs only it."""
+    call.  Only the columns below the filter's band edge hold nonzero data
+    after the filter (a fraction `live` = kz / (n_last / 2) of the half
+    spectrum): the axis-1 forward, the filter pass and the axis-1 inverse move
+    that part, and c2r needs only it."""
     N = math.prod(shape)
     h = 4 * N  # half spectrum bytes
     tab = N  # bin table: one uint16 per half-spectrum mode
     return {
         "r2c": h,
-        "cols_mid_fwd": 2 * h,
+        "cols_mid_fwd": 2 * h * live,
         "cols_filter": ((1 if kspace else 2) * h + tab) * live,
         "cols_mid_inv": 2 * h * live,
         "c2r": h * live + field_bytes * N + nlev * N + nlev * h,

@@ -559,9 +559,10 @@ int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind,
 }
 
 // r2c rows of the noise (src == kSrcNoise) or of a stored field into w.spec,
-// then the forward FFT along axis 1 for 3D.
+// then the forward FFT along axis 1 for 3D, of the columns k_last < kz only
+// (kz < 0: all; the filter zeroes the others).
 int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed, uint32_t field_idx,
-                         float2* spec, unsigned* status, cudaStream_t s) {
+                         float2* spec, unsigned* status, cudaStream_t s, long long kz = -1) {
     const long long nrows = p->N >> (p->logM + 1);
     RowArgs ra{};
     ra.src = y;
@@ -574,7 +575,7 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
     const KernelInfo k = pick_row(p->logM, nrows, r2c_kernel, src);
     if (!row_launch(p, k, nrows, L)) return HUFIELD_ERR_CUDA;
     HF_CUDA(launch(p, kPassR2C, k.fn, L, &ra, s));
-    if (p->ndim == 3) return mid_pass(p, -1, spec, 1, kPassMidFwd, status, s);
+    if (p->ndim == 3) return mid_pass(p, -1, spec, 1, kPassMidFwd, status, s, kz);
     return HUFIELD_OK;
 }
 
@@ -695,15 +696,17 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     const BinParams& b = bp ? *bp : none;
     double* P = w.acc[set & 1];
     double* raw = P + 1;
-    // past the filter's band the spectrum is exactly zero: the passes after
-    // the forward transform skip the columns k_last >= kz (c2r reads zeros there)
+    // past the filter's band the spectrum is exactly zero: the passes from the
+    // axis-1 forward on skip the columns k_last >= kz (c2r reads zeros there).
+    // The r2c rows still write them: a filter tile that straddles kz
+    // transforms finite numbers there, which the filter then zeroes.
     const long long kz = zero_kz(p, fp);
     int rc;
     if (p->kspace) {
         // the noise coefficients are drawn inside the axis-0 pass: no forward passes
         rc = axis0_pass(p, kModeKspace, w.spec, 1, &fp, b, tab, raw, P, w.status, s, seed, field_idx, kz);
     } else {
-        rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s);
+        rc = forward_rows_and_mid(p, kSrcNoise, nullptr, seed, field_idx, w.spec, w.status, s, kz);
         if (rc) return rc;
         rc = axis0_pass(p, kModeFilter, w.spec, 1, &fp, b, tab, raw, P, w.status, s, 0, 0, kz);
     }
