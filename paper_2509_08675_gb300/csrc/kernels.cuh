@@ -740,13 +740,23 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
             if (t0 + q < t1) issue(t0 + q, buf0 + q * tile_elems, &bar[q]);
     }
 
+    // The bins gather in FP32 (shared-memory atomics) over up to kMergeTiles
+    // tiles, then in FP64: a bin takes a few dozen run sums in FP32 at most,
+    // far inside the 1e-4 relative bound of the bins, and the FP64 adds (slow
+    // on this part) run once per kMergeTiles tiles.  The Parseval sum goes to
+    // FP64 every tile (it sets the field's normalisation).
+    constexpr int kMergeTiles = 4;
+    int since_merge = 0;
     auto flush = [&](long long batch) {
         __syncthreads();
         double* g = MODE == kModeBins ? a.gbins + batch * nb : a.gbins;
         for (int i = t; i < nb; i += T) {
-            if (dbin[i] != 0.0) atomicAdd(g + i, dbin[i]);
+            const double v = dbin[i] + (double)fbin[i];
+            if (v != 0.0) atomicAdd(g + i, v);
             dbin[i] = 0.0;
+            fbin[i] = 0.0f;
         }
+        since_merge = 0;
         if (kFilt && t == 0) {
             atomicAdd(a.gP, dbin[nb]);
             dbin[nb] = 0.0;
@@ -974,9 +984,16 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
             }
         }
         if constexpr (kAcc) {
-            for (int i = t; i <= nb; i += T) {
-                dbin[i] += (double)fbin[i];
-                fbin[i] = 0.0f;
+            if (kFilt && t == 0) {
+                dbin[nb] += (double)fbin[nb];
+                fbin[nb] = 0.0f;
+            }
+            if (++since_merge == kMergeTiles) {
+                for (int i = t; i < nb; i += T) {
+                    dbin[i] += (double)fbin[i];
+                    fbin[i] = 0.0f;
+                }
+                since_merge = 0;
             }
             __syncthreads();
         }
