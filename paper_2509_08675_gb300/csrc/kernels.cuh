@@ -995,7 +995,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                 }
                 since_merge = 0;
             }
-            __syncthreads();
+            // no barrier here: the next tile's first atomics on fbin come after
+            // the barriers of its wait and FFT, and flush starts with one
         }
     }
     if (failed_at >= 0) {
