@@ -220,9 +220,10 @@ int hufield_spectrum_noalloc(const hufield_dims *dims, const void *y, int32_t dt
  * Many fields of different lattices and filters in one launch: the whole
  * path (as hufield_pipeline with one level and radial bins) for every item.
  * Items are grouped by lattice into size classes, each with its own plan
- * (bins cached), workspace slice and stream; hufield_batch_run captures the
- * whole batch into one CUDA graph, with the classes as parallel branches, and
- * replays it on later runs with the same buffers (one graph launch per run).
+ * (bins cached) and two lanes (a stream and a workspace slice each) that take
+ * the class's items in turn; hufield_batch_run captures the whole batch into
+ * one CUDA graph, with the lanes as parallel branches, and replays it on later
+ * runs with the same buffers (one graph launch per run).
  * Outputs lie end to end in item order (see hufield_batch_layout). */
 typedef struct {
     hufield_dims dims;

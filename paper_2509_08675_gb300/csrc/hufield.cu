@@ -1322,17 +1322,22 @@ extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y,
 }
 
 // ---------------------------------------------------------------------------
-// Ragged batches (hufield_batch_*): one plan, stream and workspace slice per
-// size class; the whole batch is captured into one CUDA graph (classes as
-// parallel branches, items of a class in sequence) and replayed.
+// Ragged batches (hufield_batch_*): one plan per size class, and per class
+// up to kBatchLanes lanes (a stream and a workspace slice each) that take its
+// items in turn; the whole batch is captured into one CUDA graph (every lane
+// a parallel branch, the items of a lane in sequence) and replayed.  Two
+// lanes let one item's passes fill the tail and launch gaps of the other's.
 // ---------------------------------------------------------------------------
+constexpr int kBatchLanes = 2;
+
 struct hufield_batch {
     struct Class {
         hufield_plan* plan = nullptr;
-        cudaStream_t stream = nullptr;
-        cudaEvent_t join = nullptr;
+        int lanes = 1;
+        cudaStream_t stream[kBatchLanes] = {};
+        cudaEvent_t join[kBatchLanes] = {};
         std::vector<int> members;
-        size_t ws_off = 0, ws_bytes = 0;
+        size_t ws_off = 0, ws_bytes = 0;  // lane l's slice starts at ws_off + l * align256(ws_bytes)
     };
     std::vector<hufield_batch_item> items;
     std::vector<Class> classes;
@@ -1353,8 +1358,10 @@ void batch_free(hufield_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto& c : b->classes) {
         if (c.plan) hufield_plan_destroy(c.plan);
-        if (c.stream) cudaStreamDestroy(c.stream);
-        if (c.join) cudaEventDestroy(c.join);
+        for (int l = 0; l < kBatchLanes; ++l) {
+            if (c.stream[l]) cudaStreamDestroy(c.stream[l]);
+            if (c.join[l]) cudaEventDestroy(c.join[l]);
+        }
     }
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->origin) cudaStreamDestroy(b->origin);
@@ -1422,12 +1429,14 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
     }
     for (size_t c = 0; c < b->classes.size(); ++c) {
         auto& C = b->classes[c];
+        C.lanes = (int)C.members.size() < kBatchLanes ? (int)C.members.size() : kBatchLanes;
         C.ws_off = b->ws_total;
-        b->ws_total += align256(C.ws_bytes);
+        b->ws_total += (size_t)C.lanes * align256(C.ws_bytes);
         if (uniform[c] && hufield_plan_set_bins(C.plan, class_nr[c], 1) != HUFIELD_OK) rc = HUFIELD_ERR_CUDA;
-        if (cudaStreamCreateWithFlags(&C.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&C.join, cudaEventDisableTiming) != cudaSuccess)
-            rc = HUFIELD_ERR_CUDA;
+        for (int l = 0; l < C.lanes; ++l)
+            if (cudaStreamCreateWithFlags(&C.stream[l], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&C.join[l], cudaEventDisableTiming) != cudaSuccess)
+                rc = HUFIELD_ERR_CUDA;
     }
     if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
@@ -1470,20 +1479,24 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
         HF_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
         int rc = cudaEventRecord(b->fork, b->origin) == cudaSuccess ? HUFIELD_OK : HUFIELD_ERR_CUDA;
         for (auto& C : b->classes) {
-            if (rc) break;
-            if (cudaStreamWaitEvent(C.stream, b->fork, 0) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
-            for (int i : C.members) {
-                if (rc) break;
-                const hufield_batch_item& it = b->items[i];
-                const long long fo = b->f_off[i], bo = b->bin_off[i];
-                rc = hufield_ensemble(C.plan, &it.filt, it.seed, it.field_idx, 1, HUFIELD_F32, out_f ? out_f + fo : nullptr,
-                                      &it.level, 1, out_maps ? out_maps + fo : nullptr, it.nr, 1, 0, sums_f + bo,
-                                      counts_f + bo, sums_m + bo, counts_m + bo,
-                                      reinterpret_cast<char*>(ws) + C.ws_off, C.ws_bytes, C.stream);
+            for (int l = 0; l < C.lanes && !rc; ++l) {
+                cudaStream_t ls = C.stream[l];
+                char* lws = reinterpret_cast<char*>(ws) + C.ws_off + (size_t)l * align256(C.ws_bytes);
+                if (cudaStreamWaitEvent(ls, b->fork, 0) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
+                for (size_t m = (size_t)l; m < C.members.size() && !rc; m += (size_t)C.lanes) {
+                    const int i = C.members[m];
+                    const hufield_batch_item& it = b->items[i];
+                    const long long fo = b->f_off[i], bo = b->bin_off[i];
+                    rc = hufield_ensemble(C.plan, &it.filt, it.seed, it.field_idx, 1, HUFIELD_F32,
+                                          out_f ? out_f + fo : nullptr, &it.level, 1, out_maps ? out_maps + fo : nullptr,
+                                          it.nr, 1, 0, sums_f + bo, counts_f + bo, sums_m + bo, counts_m + bo, lws,
+                                          C.ws_bytes, ls);
+                }
+                if (!rc && (cudaEventRecord(C.join[l], ls) != cudaSuccess ||
+                            cudaStreamWaitEvent(b->origin, C.join[l], 0) != cudaSuccess))
+                    rc = HUFIELD_ERR_CUDA;
             }
-            if (!rc && (cudaEventRecord(C.join, C.stream) != cudaSuccess ||
-                        cudaStreamWaitEvent(b->origin, C.join, 0) != cudaSuccess))
-                rc = HUFIELD_ERR_CUDA;
+            if (rc) break;
         }
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);

@@ -59,3 +59,33 @@ def test_batch_rejects_bad_items(hf):
         hf.Batch([((16, 16), gf, 0, 0, 0.0, 0)])
     with pytest.raises(hf.HufieldError):
         hf.Batch([((12, 16), gf, 0, 0, 0.0, 8)])
+
+
+def test_batch_one_class_two_lanes_uncached_bins(hf):
+    # seven items of one lattice share a plan and run on two lanes in turn; their
+    # bin counts differ, so every item builds its bin table in its lane's workspace
+    rng = np.random.default_rng(3)
+    items, oitems = [], []
+    for i in range(7):
+        shape = (32, 64)
+        gf, of = filters(hf, **inputs.random_filter(2, 500 + i))
+        level = float(np.float32(rng.uniform(-1, 1)))
+        nr = 8 + 3 * i
+        items.append((shape, gf, 11, i, level, nr))
+        oitems.append((shape, of, 11, i, level, nr))
+    batch = hf.Batch(items)
+    out_f = dev_zeros(batch.total_voxels, torch.float32)
+    maps = dev_zeros(batch.total_voxels, torch.int8)
+    sf, cf = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
+    sm, cm = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+    hf.hufield_batch_run(batch, out_f, maps, sf, cf, sm, cm, ws)
+    torch.cuda.synchronize()
+    f_all = np_(out_f)
+    for i, (shape, of, seed, field, level, nr) in enumerate(oitems):
+        N = int(np.prod(shape))
+        fo, bo = batch.f_offset[i], batch.bin_offset[i]
+        want = oracle.pipeline(shape, of, seed, field, levels=(level,), nr=nr, ntheta=1)
+        check_field(f_all[fo:fo + N].reshape(shape), want["f"])
+        check_bins(np_(sf)[bo:bo + nr], want["sums_f"], np_(cf)[bo:bo + nr], want["counts_f"])
+    batch.close()
