@@ -51,6 +51,7 @@ TRAFFIC = {
     ("3d-512", "r2c"): 477.1e6,  # k_r2c<8, 4, 0>, 512^3
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+E2E_CHUNK = 8  # fields per ensemble call in the end-to-end leg
 
 
 def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0):
@@ -348,7 +349,8 @@ def main():
     if args.also and args.also != args.workload and world == 1:
         wl2 = dict(WORKLOADS[args.also])
         r2 = measure(hf, torch, wl2, args.also, args, rank, world, dist)
-        also[args.also] = {k: r2[k] for k in ("value", "ms_per_step", "roofline", "pipeline", "passes", "clocks")}
+        also[args.also] = {k: r2[k] for k in ("value", "ms_per_step", "ms_per_step_one_lane", "lanes", "roofline",
+                                              "pipeline", "passes", "clocks")}
         del r2
     comp = {}
     if world == 1 and not args.no_cufft:
@@ -366,7 +368,8 @@ def main():
                 "config": {"workload": args.workload, "shape": list(shape), "fields_per_step": wl["nfields"],
                            "levels": list(wl["levels"]), "bins": [wl["nr"], wl["ntheta"]],
                            "noise": args.noise, "l2": "flushed between timed steps",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}", "lanes": res["lanes"]},
+                "ms_per_step_one_lane": res["ms_per_step_one_lane"],
                 "roofline": res["roofline"],
                 "pipeline": res["pipeline"],
                 "passes": res["passes"],
@@ -385,7 +388,10 @@ def main():
 
 def measure(hf, torch, wl, name, args, rank, world, dist):
     """Device-timed steps of one workload: per-step CUDA events on the launching
-    stream, L2 flushed between steps, live per-pass event times of the plan."""
+    stream, L2 flushed between steps.  An ensemble runs on two lanes (a
+    two-slice workspace: consecutive fields overlap); the per-pass times come
+    from the plan's per-launch CUDA events over the same number of steps run
+    on one lane, where every launch's events bracket that kernel alone."""
     shape, nf, levels = wl["shape"], wl["nfields"], wl["levels"]
     nlev, nr, nt = len(levels), wl["nr"], wl["ntheta"]
     nb = nr * nt
@@ -394,7 +400,9 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
     plan = hf.Plan(shape, profile=True, kspace=args.noise == "kspace")
     hf.hufield_plan_set_bins(plan, nr, nt)  # plan-time bin table and counts, as a production caller would
-    ws = plan.workspace(nlev, nb)
+    ws = plan.workspace(nlev, nb, lanes=2 if nf >= 2 else 1)
+    slice_bytes = (hf.hufield_workspace_bytes(plan, nlev, nb) + 255) & ~255
+    ws_one = ws[:slice_bytes]  # the first slice alone: one lane
     out_f = torch.empty((nf,) + tuple(shape), dtype=fdt, device="cuda")
     maps = torch.empty((nf, nlev) + tuple(shape), dtype=torch.int8, device="cuda")
     sf = torch.zeros(nb, dtype=torch.float64, device="cuda")
@@ -405,8 +413,8 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     stream = torch.cuda.current_stream()
     field0 = replica_field0(rank, nf)
 
-    def step(i):
-        hf.hufield_ensemble(plan, filt, 1000 + i, field0, nf, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, ws,
+    def step(i, w=ws):
+        hf.hufield_ensemble(plan, filt, 1000 + i, field0, nf, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, w,
                             stream=stream)
 
     for i in range(args.warmup):
@@ -439,13 +447,26 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
         bus = None
     clk = clocks.stop(bus)
     tot_ms = sum(a.elapsed_time(b) for a, b in ev)
-    prof = hf.hufield_profile_read(plan)
     if hf.hufield_workspace_status(ws) != hf.OK:
         raise RuntimeError("device-side timeout during the timed steps")
     tot_ms = max_over_ranks(dist, tot_ms, "cuda")
     value = world * args.steps * nf * N / (tot_ms / 1e3)
 
-    # roofline of the dominant pass (live per-launch CUDA-event times of the timed steps)
+    # per-pass times: the same steps on one lane (no overlap between fields)
+    hf.hufield_profile_read(plan)  # drop the two-lane records
+    one_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step(args.warmup + i, ws_one)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    one_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    prof = hf.hufield_profile_read(plan)
+    if hf.hufield_workspace_status(ws_one) != hf.OK:
+        raise RuntimeError("device-side timeout during the one-lane steps")
+
+    # roofline of the dominant pass (per-launch CUDA-event times of the one-lane steps)
     live = band_live(hf, plan, filt, shape)
     algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2, args.noise == "kspace", live)
     peak, peak_kind = peaks()
@@ -463,7 +484,8 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     roof = {"bound": "hbm", "achieved": passes[dom]["GBps"], "peak": peak, "unit": "GB/s",
             "frac": passes[dom]["frac"], "traffic": TRAFFIC.get((name, dom)),
             "kernel": dom, "peak_source": peak_kind}
-    return {"value": value, "ms_per_step": tot_ms / args.steps, "roofline": roof,
+    return {"value": value, "ms_per_step": tot_ms / args.steps, "ms_per_step_one_lane": round(one_ms, 4),
+            "lanes": 2 if nf >= 2 else 1, "roofline": roof,
             "pipeline": {"bytes_per_voxel": round(per_step_bytes / (nf * N), 2), "GBps": round(pipe_gbs, 1),
                          "frac": round(pipe_gbs / peak, 4), "band_live": round(live, 4)},
             "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()), "clocks": clk,
@@ -539,9 +561,10 @@ def cufft_comparator(hf, torch, wl, nfields=4):
 
 
 def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws, field0, dist, world):
-    """The same step through the public per-field call, with every output (fields,
-    sign maps, bins) copied to pinned host memory on a second stream that
-    overlaps the next field's compute."""
+    """The same step through the public ensemble call in chunks of E2E_CHUNK
+    fields (two lanes each), with every output (fields, sign maps, bins) copied
+    to pinned host memory on a second stream that overlaps the next chunk's
+    compute."""
     shape, nf, levels = wl["shape"], wl["nfields"], wl["levels"]
     nlev, nr, nt = len(levels), wl["nr"], wl["ntheta"]
     N = math.prod(shape)
@@ -553,17 +576,18 @@ def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws
     host_bins = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (sf, cf, sm, cm)]
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
-    done = [torch.cuda.Event() for _ in range(nf)]
+    chunks = [(c, min(nf, c + E2E_CHUNK)) for c in range(0, nf, E2E_CHUNK)]
+    done = [torch.cuda.Event() for _ in chunks]
 
     def step(i):
-        for e in range(nf):
-            hf.hufield_pipeline(plan, filt, 2000 + i, field0 + e, out_f[e], levels, maps[e], nr, nt, e > 0, sf, cf,
-                                sm, cm, ws, stream=comp)
-            done[e].record(comp)
+        for k, (a, b) in enumerate(chunks):
+            hf.hufield_ensemble(plan, filt, 2000 + i, field0 + a, b - a, out_f[a:b], levels, maps[a:b], nr, nt, a > 0,
+                                sf, cf, sm, cm, ws, stream=comp)
+            done[k].record(comp)
             with torch.cuda.stream(copy):
-                copy.wait_event(done[e])
-                host_f[e].copy_(out_f[e], non_blocking=True)
-                host_m[e].copy_(maps[e], non_blocking=True)
+                copy.wait_event(done[k])
+                host_f[a:b].copy_(out_f[a:b], non_blocking=True)
+                host_m[a:b].copy_(maps[a:b], non_blocking=True)
         comp.wait_stream(copy)
         for h, d in zip(host_bins, (sf, cf, sm, cm)):
             h.copy_(d, non_blocking=True)

@@ -186,7 +186,13 @@ int hufield_pipeline(hufield_plan *plan, const hufield_filter *filt, uint64_t se
 /* Ensemble: hufield_pipeline for field_idx = field0 .. field0 + nfields - 1
  * with the same seed and filter, bins accumulated over the ensemble.  Field e
  * is written at out_f + e * N elements and its maps at out_maps + e * nlev * N
- * (either may be NULL).  accumulate applies to the first field. */
+ * (either may be NULL).  accumulate applies to the first field.  A workspace
+ * of two slices, ws_bytes >= 2 * W with W = hufield_workspace_bytes(plan,
+ * nlev, nr * ntheta) rounded up to a multiple of 256, runs the odd fields on
+ * the plan's second stream and slice, overlapping consecutive fields; the
+ * call stays ordered on `stream` (it forks and joins there), both lanes
+ * report to the first slice's status word, and the bins are added in a
+ * different order (the sums agree to rounding). */
 int hufield_ensemble(hufield_plan *plan, const hufield_filter *filt, uint64_t seed, uint32_t field0,
                      int32_t nfields, int32_t out_dtype, void *out_f, const float *levels, int32_t nlev,
                      int8_t *out_maps, int32_t nr, int32_t ntheta, int32_t accumulate, double *sums_f,

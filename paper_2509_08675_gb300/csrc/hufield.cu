@@ -162,7 +162,8 @@ struct AddCountsArgs {
 };
 __global__ void k_add_counts(const __grid_constant__ AddCountsArgs a) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nbins; b += gridDim.x * blockDim.x)
-        for (int d = 0; d < a.ndst; ++d) a.dst[d][b] += a.mult * a.counts[b];
+        for (int d = 0; d < a.ndst; ++d)  // atomic: calls on other streams may add to the same counts
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.dst[d] + b), (unsigned long long)(a.mult * a.counts[b]));
 }
 
 __global__ void k_bins_mean(const double* sums, const long long* counts, int nbins, double* out) {
@@ -208,6 +209,9 @@ struct hufield_plan {
     long long wait_budget = 0;                            // SM cycles per bounded mbarrier wait
     bool inject_timeout = false;                          // test hook (HUFIELD_PLAN_INJECT_TIMEOUT)
     bool kspace = false;                                  // HUFIELD_PLAN_KSPACE_NOISE
+    // second lane of ensembles (odd fields) and its fork/join events
+    cudaStream_t lane = nullptr;
+    cudaEvent_t lane_fork = nullptr, lane_join = nullptr;
 };
 
 namespace {
@@ -815,7 +819,12 @@ int hufield_plan_create(hufield_plan** out, const hufield_dims* dims, uint32_t f
         return HUFIELD_ERR_CUDA;
     }
     k_twiddles<<<kTwN / 256, 256>>>(p->tw);
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->lane, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->lane_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->lane_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (p->lane) cudaStreamDestroy(p->lane);
+        if (p->lane_fork) cudaEventDestroy(p->lane_fork);
         cudaFree(p->tw);
         delete p;
         return HUFIELD_ERR_CUDA;
@@ -831,6 +840,9 @@ int hufield_plan_destroy(hufield_plan* p) {
         cudaEventDestroy(r.stop);
     }
     for (auto e : p->pool) cudaEventDestroy(e);
+    if (p->lane) cudaStreamDestroy(p->lane);
+    if (p->lane_fork) cudaEventDestroy(p->lane_fork);
+    if (p->lane_join) cudaEventDestroy(p->lane_join);
     cudaFree(p->cache_tab);
     cudaFree(p->cache_counts);
     cudaFree(p->tw);
@@ -982,9 +994,20 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     BinParams bp;
     rc = make_bins(p, nr, ntheta, bp);
     if (rc) return rc;
-    Workspace w;
-    rc = carve(p, ws, bytes, nlev, bp.nbins, w);
+    // Two lanes when the workspace holds two slices: odd fields run on the
+    // plan's second stream with the second slice, so that one field's passes
+    // fill the tail waves and launch gaps of the other's.  Both lanes report
+    // to the first slice's status word and add their bins atomically.
+    const size_t slice = align256(ws_bytes(p, nlev, bp.nbins));
+    const int lanes = (nfields >= 2 && bytes >= 2 * slice) ? 2 : 1;
+    Workspace w, w1;
+    rc = carve(p, ws, lanes == 2 ? slice : bytes, nlev, bp.nbins, w);
     if (rc) return rc;
+    if (lanes == 2) {
+        rc = carve(p, reinterpret_cast<char*>(ws) + slice, slice, nlev, bp.nbins, w1);
+        if (rc) return rc;
+        w1.status = w.status;
+    }
     HF_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned), (cudaStream_t)stream));
     cudaStream_t s = (cudaStream_t)stream;
     if (!accumulate) {
@@ -1003,13 +1026,24 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     if (rc) return rc;
     rc = clear_accumulators(w, s);
     if (rc) return rc;
+    if (lanes == 2) {
+        rc = clear_accumulators(w1, s);
+        if (rc) return rc;
+        HF_CUDA(cudaEventRecord(p->lane_fork, s));
+        HF_CUDA(cudaStreamWaitEvent(p->lane, p->lane_fork, 0));
+    }
     const size_t esize = out_dtype == HUFIELD_BF16 ? 2 : 4;
     for (int e = 0; e < nfields; ++e) {
         void* fo = out_f ? reinterpret_cast<char*>(out_f) + (size_t)e * (size_t)p->N * esize : nullptr;
         int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * (size_t)p->N : nullptr;
-        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, tab, w,
-                       e & 1, s);
+        const bool odd = lanes == 2 && (e & 1);
+        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, tab,
+                       odd ? w1 : w, lanes == 2 ? (e >> 1) & 1 : e & 1, odd ? p->lane : s);
         if (rc) return rc;
+    }
+    if (lanes == 2) {
+        HF_CUDA(cudaEventRecord(p->lane_join, p->lane));
+        HF_CUDA(cudaStreamWaitEvent(s, p->lane_join, 0));
     }
     return HUFIELD_OK;
 }

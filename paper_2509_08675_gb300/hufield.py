@@ -179,8 +179,14 @@ class Plan:
         except Exception:
             pass
 
-    def workspace(self, nlev: int = 0, nbins: int = 0, device=None) -> torch.Tensor:
+    def workspace(self, nlev: int = 0, nbins: int = 0, device=None, lanes: int = 1) -> torch.Tensor:
+        """Workspace for calls with nlev maps and nbins bins; lanes = 2 holds two
+        slices, with which hufield_ensemble overlaps consecutive fields."""
         n = hufield_workspace_bytes(self, nlev, nbins)
+        if lanes == 2:
+            n = 2 * ((n + 255) & ~255)
+        elif lanes != 1:
+            raise ValueError("lanes must be 1 or 2")
         return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
 

@@ -10,11 +10,11 @@ from tests.gpu_common import check_bins, check_field, check_maps, dev_zeros, fil
 pytestmark = pytest.mark.gpu
 
 
-def run_pipeline(hf, plan, gf, shape, seed, field, levels, nr, ntheta, out_dtype=torch.float32, nfields=1):
+def run_pipeline(hf, plan, gf, shape, seed, field, levels, nr, ntheta, out_dtype=torch.float32, nfields=1, lanes=1):
     N = int(np.prod(shape))
     nb = nr * ntheta
     nlev = len(levels)
-    ws = plan.workspace(nlev, nb)
+    ws = plan.workspace(nlev, nb, lanes=lanes)
     out_f = torch.empty((nfields,) + tuple(shape), dtype=out_dtype, device="cuda")
     maps = torch.empty((nfields, max(nlev, 1)) + tuple(shape), dtype=torch.int8, device="cuda")
     sf, cf = dev_zeros(nb, torch.float64), dev_zeros(nb, torch.int64)
@@ -167,26 +167,30 @@ def test_pipeline_no_levels(hf):
     check_bins(got["sums_f"], want["sums_f"], got["counts_f"], want["counts_f"])
 
 
-def test_ensemble_accumulates(hf):
+@pytest.mark.parametrize("lanes,nf", [(1, 3), (2, 3), (2, 6)])
+def test_ensemble_accumulates(hf, lanes, nf):
+    # lanes = 2: a two-slice workspace runs the odd fields on the plan's second stream
     shape, levels, nr, nt = (64, 128), (0.0, 0.5, -0.5), 16, 6
     gf, of = filters(hf, **inputs.filter_kwargs(inputs.C1))
     plan = hf.Plan(shape)
-    got = run_pipeline(hf, plan, gf, shape, 0, 5, levels, nr, nt, nfields=3)
+    got = run_pipeline(hf, plan, gf, shape, 0, 5, levels, nr, nt, nfields=nf, lanes=lanes)
     sf = np.zeros(nr * nt)
     cf = np.zeros(nr * nt, np.int64)
     sm = np.zeros((len(levels), nr * nt))
     cm = np.zeros((len(levels), nr * nt), np.int64)
-    for e in range(3):
+    flips = np.zeros(len(levels), np.int64)
+    for e in range(nf):
         w = oracle.pipeline(shape, of, 0, 5 + e, levels=levels, nr=nr, ntheta=nt)
         check_field(got["f"][e], w["f"])
-        check_maps(got["maps"][e], w["maps"], w["f"], levels)
+        flips += np.asarray(check_maps(got["maps"][e], w["maps"], w["f"], levels))
         sf += w["sums_f"]
         cf += w["counts_f"]
         sm += w["sums_m"]
         cm += w["counts_m"]
     check_bins(got["sums_f"], sf, got["counts_f"], cf)
     for t in range(len(levels)):
-        check_bins(got["sums_m"][t], sm[t], got["counts_m"][t], cm[t], flips=2, N=int(np.prod(shape)))
+        check_bins(got["sums_m"][t], sm[t], got["counts_m"][t], cm[t], flips=max(2, int(flips[t])),
+                   N=int(np.prod(shape)))
 
 
 def test_pipeline_bf16_maps_from_fp32(hf):
