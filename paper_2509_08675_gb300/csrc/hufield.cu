@@ -166,6 +166,11 @@ __global__ void k_add_counts(const __grid_constant__ AddCountsArgs a) {
             atomicAdd(reinterpret_cast<unsigned long long*>(a.dst[d] + b), (unsigned long long)(a.mult * a.counts[b]));
 }
 
+__global__ void k_add_doubles(double* dst, const double* src, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] += src[i];
+}
+
 __global__ void k_bins_mean(const double* sums, const long long* counts, int nbins, double* out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nbins) out[b] = counts[b] ? sums[b] / (double)counts[b] : 0.0;
@@ -451,6 +456,7 @@ struct Workspace {
     unsigned short* bintab;
     double* acc[2];  // P at acc[s][0], raw bins at acc[s] + 1
     size_t acc_stride;  // doubles from set 0 to set 1
+    double* lane_sums;  // field bins of an ensemble's second lane (added to the caller's at the end)
 };
 
 size_t ws_spec_bytes(const hufield_plan* p, int nlev) {
@@ -463,7 +469,7 @@ size_t ws_table_bytes(const hufield_plan* p, int nbins) {
 size_t ws_acc_bytes(int nbins) { return align256(sizeof(double) * (size_t)(1 + (nbins > 0 ? nbins : 0))); }
 
 size_t ws_bytes(const hufield_plan* p, int nlev, int nbins) {
-    return kWsHeader + ws_spec_bytes(p, nlev) + ws_table_bytes(p, nbins) + 2 * ws_acc_bytes(nbins);
+    return kWsHeader + ws_spec_bytes(p, nlev) + ws_table_bytes(p, nbins) + 3 * ws_acc_bytes(nbins);
 }
 
 int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Workspace& w) {
@@ -478,6 +484,7 @@ int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Wo
     w.acc[0] = reinterpret_cast<double*>(base + kWsHeader + spec + tab);
     w.acc_stride = ws_acc_bytes(nbins) / sizeof(double);
     w.acc[1] = w.acc[0] + w.acc_stride;
+    w.lane_sums = w.acc[1] + w.acc_stride;
     return HUFIELD_OK;
 }
 
@@ -997,7 +1004,8 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     // Two lanes when the workspace holds two slices: odd fields run on the
     // plan's second stream with the second slice, so that one field's passes
     // fill the tail waves and launch gaps of the other's.  Both lanes report
-    // to the first slice's status word and add their bins atomically.
+    // to the first slice's status word and add their maps' bins atomically;
+    // the second lane's field bins gather in its slice.
     const size_t slice = align256(ws_bytes(p, nlev, bp.nbins));
     const int lanes = (nfields >= 2 && bytes >= 2 * slice) ? 2 : 1;
     Workspace w, w1;
@@ -1029,6 +1037,9 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     if (lanes == 2) {
         rc = clear_accumulators(w1, s);
         if (rc) return rc;
+        // the second lane's field bins gather apart (the c2r pass adds them
+        // without atomics) and join the caller's at the end
+        HF_CUDA(cudaMemsetAsync(w1.lane_sums, 0, sizeof(double) * bp.nbins, s));
         HF_CUDA(cudaEventRecord(p->lane_fork, s));
         HF_CUDA(cudaStreamWaitEvent(p->lane, p->lane_fork, 0));
     }
@@ -1037,13 +1048,18 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
         void* fo = out_f ? reinterpret_cast<char*>(out_f) + (size_t)e * (size_t)p->N * esize : nullptr;
         int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * (size_t)p->N : nullptr;
         const bool odd = lanes == 2 && (e & 1);
-        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp, sums_f, sums_m, tab,
-                       odd ? w1 : w, lanes == 2 ? (e >> 1) & 1 : e & 1, odd ? p->lane : s);
+        rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp,
+                       odd ? w1.lane_sums : sums_f, sums_m, tab, odd ? w1 : w, lanes == 2 ? (e >> 1) & 1 : e & 1,
+                       odd ? p->lane : s);
         if (rc) return rc;
     }
     if (lanes == 2) {
         HF_CUDA(cudaEventRecord(p->lane_join, p->lane));
         HF_CUDA(cudaStreamWaitEvent(s, p->lane_join, 0));
+        HF_CUDA(profiled(p, kPassMisc, s, [&] {
+            k_add_doubles<<<(bp.nbins + 255) / 256, 256, 0, s>>>(sums_f, w1.lane_sums, bp.nbins);
+            return cudaGetLastError();
+        }));
     }
     return HUFIELD_OK;
 }

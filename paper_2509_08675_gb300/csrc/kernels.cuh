@@ -383,8 +383,7 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
         if (empty && t == 0) atomicOr(a.status, kStatusNoPower);
         if (a.sums_f && !empty) {
             const double sN = (double)a.N / Pv;
-            // atomic: the two lanes of an ensemble may finish fields at once
-            for (int b = t; b < a.nbins; b += G::T) atomicAdd(a.sums_f + b, a.P[1 + b] * sN);
+            for (int b = t; b < a.nbins; b += G::T) a.sums_f[b] += a.P[1 + b] * sN;
         }
         for (int i = t; i < a.next_len; i += G::T) a.next_acc[i] = 0.0;
     }
