@@ -488,7 +488,10 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
             "lanes": 2 if nf >= 2 else 1, "roofline": roof,
             "pipeline": {"bytes_per_voxel": round(per_step_bytes / (nf * N), 2), "GBps": round(pipe_gbs, 1),
                          "frac": round(pipe_gbs / peak, 4), "band_live": round(live, 4)},
-            "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()), "clocks": clk,
+            # the one-lane steps launch what the timed steps do, less the one kernel per
+            # two-lane ensemble call that joins the second lane's field bins
+            "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()) + (args.steps if nf >= 2 else 0),
+            "clocks": clk,
             "plan": plan, "filt": filt, "bufs": (out_f, maps, sf, cf, sm, cm, ws), "field0": field0}
 
 
