@@ -490,7 +490,8 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
                          "frac": round(pipe_gbs / peak, 4), "band_live": round(live, 4)},
             # the one-lane steps launch what the timed steps do, less the one kernel per
             # two-lane ensemble call that joins the second lane's field bins
-            "passes": passes, "gpu_launches": sum(p["launches"] for p in passes.values()) + (args.steps if nf >= 2 else 0),
+            "passes": passes,
+            "gpu_launches": sum(p["launches"] for p in passes.values()) + (args.steps if nf >= 2 else 0),
             "clocks": clk,
             "plan": plan, "filt": filt, "bufs": (out_f, maps, sf, cf, sm, cm, ws), "field0": field0}
 
