@@ -523,13 +523,15 @@ void set_tiles(const hufield_plan* p, ColArgs& ca, int logtb, long long kz, Laun
 }
 
 // The first k_last from which every mode of the filter is exactly zero (M
-// when there is none): all its modes have a term p log2 |kappa'_i / a_i| at or
-// above u_zero (zero_bound).  3D: the term of the last axis, which the
-// rotation (about that axis) leaves alone.  2D: along the column kappa_1 =
-// const every point of the plane has max_i |kappa'_i| / a_i >= r = 2^(u_zero /
-// p) once the column misses the rotated rectangle |kappa'_i| < r a_i, whose
-// extent in kappa_1 is r (a_0 |sin| + a_1 |cos|).  A relative margin of 1e-6
-// covers the rounding of the FP32 terms.
+// when there is none): all its modes have K >= r = 2^(u_zero / p), i.e. log2 S
+// >= u_zero (zero_bound).  3D: the last axis, which the rotation (about that
+// axis) leaves alone, has K >= |kappa_2| / a_2.  2D: the column kappa_1 = const
+// misses the superellipse K < r once |kappa_1| exceeds its extent along
+// kappa_1 = sin kappa'_0 + cos kappa'_1, which is r times the dual norm of
+// (a_0 |sin|, a_1 |cos|): the q-norm with 1/p + 1/q = 1 for p > 1 (Hoelder),
+// the larger entry for p <= 1 (a non-convex ball reaches no further than its
+// axis tips).  A relative margin of 1e-6 covers the rounding of the FP32
+// terms.
 long long zero_kz(const hufield_plan* p, const FilterParams& fp) {
     const long long M = 1ll << p->logM;
     if (!(fp.u_zero < FLT_MAX)) return M;
@@ -538,7 +540,16 @@ long long zero_kz(const hufield_plan* p, const FilterParams& fp) {
     if (p->ndim == 3) {
         lim = r / (double)fp.inv_a[2];
     } else if (fp.rotated) {
-        lim = r * (fabs((double)fp.sr) / (double)fp.inv_a[0] + fabs((double)fp.cr) / (double)fp.inv_a[1]);
+        const double e0 = fabs((double)fp.sr) / (double)fp.inv_a[0], e1 = fabs((double)fp.cr) / (double)fp.inv_a[1];
+        const double pp = (double)fp.p;
+        double ext;
+        if (pp <= 1.0) {
+            ext = e0 > e1 ? e0 : e1;
+        } else {
+            const double q = pp / (pp - 1.0), m = e0 > e1 ? e0 : e1;  // scaled: no under- or overflow
+            ext = m > 0.0 ? m * pow(pow(e0 / m, q) + pow(e1 / m, q), 1.0 / q) : 0.0;
+        }
+        lim = r * ext;
     } else {
         lim = r / (double)fp.inv_a[1];
     }
