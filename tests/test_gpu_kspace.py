@@ -65,14 +65,15 @@ def test_kspace_differs_from_real_space_noise(hf):
     assert abs(float((a * b).mean())) < 0.1
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
 @pytest.mark.parametrize("shape,nf", [((512, 512), 3), ((64, 64, 64), 2)])
-def test_kspace_ensemble(hf, shape, nf):
+def test_kspace_ensemble(hf, shape, nf, lanes):
     fk = inputs.filter_kwargs(inputs.C1 if len(shape) == 2 else inputs.C2)
     gf, of = filters(hf, **fk)
     levels = (0.0, 0.5) if len(shape) == 2 else (0.0,)
     nr, nt = (64, 36) if len(shape) == 2 else (32, 1)
     plan = hf.Plan(shape, kspace=True)
-    got = run_pipeline(hf, plan, gf, shape, 7, 4, levels, nr, nt, nfields=nf)
+    got = run_pipeline(hf, plan, gf, shape, 7, 4, levels, nr, nt, nfields=nf, lanes=lanes)
     sums_f = np.zeros(nr * nt)
     for e in range(nf):
         want = oracle.pipeline(shape, of, 7, 4 + e, levels=levels, nr=nr, ntheta=nt, noise="kspace")

@@ -193,6 +193,31 @@ def test_ensemble_accumulates(hf, lanes, nf):
                    N=int(np.prod(shape)))
 
 
+def test_two_lane_ensembles_accumulate_across_calls(hf):
+    # a second call with accumulate = 1 adds its fields' bins to the first call's,
+    # the second lane's field bins included
+    shape, levels, nr, nt = (32, 64), (0.0,), 8, 4
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C1))
+    plan = hf.Plan(shape)
+    nb = nr * nt
+    ws = plan.workspace(1, nb, lanes=2)
+    out_f = torch.empty((3,) + shape, dtype=torch.float32, device="cuda")
+    maps = torch.empty((3, 1) + shape, dtype=torch.int8, device="cuda")
+    sf, cf = dev_zeros(nb, torch.float64), dev_zeros(nb, torch.int64)
+    sm, cm = dev_zeros(nb, torch.float64), dev_zeros(nb, torch.int64)
+    hf.hufield_ensemble(plan, gf, 4, 0, 3, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, ws)
+    hf.hufield_ensemble(plan, gf, 4, 3, 3, out_f, levels, maps, nr, nt, True, sf, cf, sm, cm, ws)
+    torch.cuda.synchronize()
+    assert hf.hufield_workspace_status(ws) == hf.OK
+    want_s, want_c = 0.0, 0
+    for e in range(6):
+        w = oracle.pipeline(shape, of, 4, e, levels=levels, nr=nr, ntheta=nt)
+        want_s, want_c = want_s + w["sums_f"], want_c + w["counts_f"]
+    check_bins(np_(sf), want_s, np_(cf), want_c)
+    for e in range(3):  # the second call's fields are the stored ones
+        check_field(np_(out_f[e]), oracle.pipeline(shape, of, 4, 3 + e, levels=levels, nr=nr, ntheta=nt)["f"])
+
+
 def test_pipeline_bf16_maps_from_fp32(hf):
     shape, levels = (128, 128), (0.0, 0.5)
     gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
