@@ -99,10 +99,11 @@ struct ColArgs {
 // CTAs of T threads); the small tiles of tiny lattices are left unbounded.
 constexpr int min_blocks(int T) { return T >= 512 ? 1 : (T >= 128 ? 512 / T : 1); }
 // Three CTAs of 256 threads (80 registers) for the passes that gain more from
-// occupancy than they lose to register pressure (measured on 512^3: the noise
-// rows 0.428 -> 0.408 ms, the maps' bins 0.308 -> 0.270 ms; the 2048-long
-// noise rows and the filter pass lose).
-constexpr int min_blocks_r2c(int log2m, int T) { return (log2m <= 8 && T == 256) ? 3 : min_blocks(T); }
+// occupancy than they lose to register pressure (measured: the 256-point
+// noise rows of 512^3 0.428 -> 0.408 ms, the 512-point ones of 1024^3 3.53 ->
+// 3.44 ms despite a few spills, the 512^3 maps' bins 0.308 -> 0.270 ms; the
+// 2048-point noise rows, the 256-point c2r rows and the filter pass lose).
+constexpr int min_blocks_r2c(int log2m, int T) { return (log2m <= 9 && T == 256) ? 3 : min_blocks(T); }
 constexpr int min_blocks_cols(int mode, int T) { return (mode == 2 && T == 256) ? 3 : min_blocks(T); }
 
 __device__ __forceinline__ int signed_index(int i, int log2n) {
