@@ -1062,17 +1062,20 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
         rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp,
                        odd ? w1.lane_sums : sums_f, sums_m, tab, odd ? w1 : w, lanes == 2 ? (e >> 1) & 1 : e & 1,
                        odd ? p->lane : s);
-        if (rc) return rc;
+        if (rc) break;
     }
     if (lanes == 2) {
+        // join even after a failed enqueue, so that nothing of this call runs
+        // after the caller's stream has moved on
         HF_CUDA(cudaEventRecord(p->lane_join, p->lane));
         HF_CUDA(cudaStreamWaitEvent(s, p->lane_join, 0));
+        if (rc) return rc;
         HF_CUDA(profiled(p, kPassMisc, s, [&] {
             k_add_doubles<<<(bp.nbins + 255) / 256, 256, 0, s>>>(sums_f, w1.lane_sums, bp.nbins);
             return cudaGetLastError();
         }));
     }
-    return HUFIELD_OK;
+    return rc;
 }
 
 int hufield_pipeline(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t field_idx, int32_t out_dtype,
