@@ -245,7 +245,7 @@ def run_ragged(args):
 
     torch.cuda.set_device(0)
     items = ragged_items(hf, RAGGED["count"])
-    batch = hf.Batch(items)
+    batch = hf.Batch(items, autotune=True)  # launch choices tuned per size class
     out_f = torch.empty(batch.total_voxels, dtype=torch.float32, device="cuda")
     maps = torch.empty(batch.total_voxels, dtype=torch.int8, device="cuda")
     z = lambda dt: torch.zeros(batch.total_bins, dtype=dt, device="cuda")  # noqa: E731
@@ -283,7 +283,7 @@ def run_ragged(args):
             "config": {"workload": "ragged-2000", "fields_per_step": len(items), "fields_2d": n2, "fields_3d": n3,
                        "voxels_per_step": voxels, "levels": "one per field, t in [-1, 1]",
                        "l2": "flushed between timed steps", "parallelism": "replicas x1",
-                       "launch": "one CUDA graph per step (hufield_batch_run)"},
+                       "launch": "one CUDA graph per step (hufield_batch_run)", "autotuned": True},
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(gbs / peak, 4), "traffic": None, "kernel": "whole batch graph",
                          "peak_source": peak_kind},

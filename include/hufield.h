@@ -135,6 +135,27 @@ int hufield_plan_destroy(hufield_plan *plan);
  * call it outside stream capture. */
 int hufield_plan_set_bins(hufield_plan *plan, int32_t nr, int32_t ntheta);
 
+/* Autotuning of the plan's launch choices for the strided passes: resident
+ * CTAs per SM of each pass mode (plain, filter, bins, k-space) and the L2
+ * promotion of their tensor maps.  Times hufield_pipeline with filter f, nlev
+ * levels and nr x ntheta bins on scratch it allocates and frees (best of
+ * three calls per candidate, coordinate descent, a change kept only when 2%
+ * faster), and keeps the fastest choice in the plan; results are the same
+ * for every choice up to the order of the bin sums.  With the environment
+ * variable HUFIELD_AUTOTUNE_CACHE naming a file, a choice recorded there for
+ * the same device, lattice and call shape is reused without timing, and a new
+ * one is appended.  Synchronises its own stream; call it outside stream
+ * capture.  Errors: HUFIELD_ERR_INVALID_ARG (arguments as for
+ * hufield_pipeline), HUFIELD_ERR_CUDA, HUFIELD_ERR_TIMEOUT (a bounded device
+ * wait ran out); on error the plan keeps its defaults.  Not in the paper: a
+ * deployment convenience. */
+int hufield_plan_autotune(hufield_plan *plan, const hufield_filter *f, int32_t nlev, int32_t nr, int32_t ntheta);
+
+/* The plan's launch choices: out[0..3] CTAs per SM of the plain, filter,
+ * bins and k-space strided passes, out[4] the L2 promotion in bytes (0: 64 or
+ * 128 by the tile's row width). */
+int hufield_plan_tuning(const hufield_plan *plan, int32_t out[5]);
+
 /* Bytes of device workspace a call needs: nlev sign maps (0 for
  * hufield_generate, 1 for hufield_spectrum) and nbins = nr * ntheta bins
  * (0 when no spectrum is taken).  Returns 0 for invalid arguments. */
@@ -242,8 +263,13 @@ typedef struct {
 
 typedef struct hufield_batch hufield_batch;
 
+/* Batch flag: autotune every size class's plan (hufield_plan_autotune with
+ * the class's first item: its filter, one level and its radial bins). */
+#define HUFIELD_BATCH_AUTOTUNE 1u
+
 /* Plan a batch of n >= 1 items on the current device (copies the items;
- * flags must be 0).  Allocates the size-class plans and streams. */
+ * flags 0 or HUFIELD_BATCH_AUTOTUNE).  Allocates the size-class plans and
+ * streams. */
 int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, int32_t n, uint32_t flags);
 
 /* Output layout (host arrays of n entries, either may be NULL): item i's

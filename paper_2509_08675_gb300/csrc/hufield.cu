@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <mutex>
+#include <stdio.h>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -193,6 +195,13 @@ struct ProfRecord {
     cudaEvent_t start, stop;
 };
 
+// Resident CTAs per SM of the strided (column) passes by default; the maps'
+// binning pass, which stores nothing, takes one more.  With more, the tiles in
+// flight (and the lines the L2 fetches around them) outgrow the L2 and the
+// strided passes re-read HBM (measured on 512^3: 0.208 ms per axis-1 pass at
+// two CTAs, 0.248 ms at three).
+constexpr int kColCapDefault = 2;
+
 struct hufield_plan {
     bool profile = false;
     std::vector<ProfRecord> records;
@@ -214,6 +223,12 @@ struct hufield_plan {
     long long wait_budget = 0;                            // SM cycles per bounded mbarrier wait
     bool inject_timeout = false;                          // test hook (HUFIELD_PLAN_INJECT_TIMEOUT)
     bool kspace = false;                                  // HUFIELD_PLAN_KSPACE_NOISE
+    // launch choices of the strided passes, which hufield_plan_autotune may
+    // change: resident CTAs per SM per mode (plain, filter, bins, k-space) and
+    // the L2 promotion of their tensor maps (0: by box row width, else 64,
+    // 128 or 256 bytes)
+    int col_cap[4] = {kColCapDefault, kColCapDefault, kColCapDefault + 1, kColCapDefault};
+    int l2_promo = 0;
     // second lane of ensembles (odd fields) and its fork/join events
     cudaStream_t lane = nullptr;
     cudaEvent_t lane_fork = nullptr, lane_join = nullptr;
@@ -230,9 +245,6 @@ struct Launch {
 // p log2 |kappa_i / a_i| far from its zero sentinel within these.
 constexpr float kMaxExponent = 1024.0f;
 constexpr float kMinAxis = 1.0f / 1048576.0f, kMaxAxis = 1048576.0f;
-// Resident CTAs per SM of the strided (column) passes; the maps' binning
-// pass, which stores nothing, takes one more.
-constexpr int kColCtasPerSm = 2;
 // Bound of one mbarrier wait: ~1 s at the GB300's 2.07 GHz SM clock.
 constexpr long long kWaitBudget = 2000000000ll;
 // Bound used by the timeout test hook (~2 ms).
@@ -285,10 +297,8 @@ KernelInfo pick_row(int log2m, long long nrows, KernelInfo (*table)(int, bool, i
 }
 
 // Column kernels: tiles of TB columns x L rows, double-buffered in shared
-// memory; TB >= 2 keeps a TMA box row at 16 bytes or more.  At most two CTAs
-// per SM: with more, the tiles in flight (and the lines the L2 fetches
-// around them) outgrow the L2 and the strided passes re-read HBM (measured
-// on 512^3: 0.208 ms per pass at two CTAs, 0.248 ms at three).
+// memory; TB >= 2 keeps a TMA box row at 16 bytes or more.  At most
+// p->col_cap[mode] CTAs per SM (kColCapDefault unless autotuned).
 bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, size_t extra_smem,
                 KernelInfo& k, Launch& L) {
     const bool big = B >= (1ll << col_logtb(log2l, true));
@@ -296,8 +306,7 @@ bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
     L.smem = k.fixed_smem + extra_smem;
-    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm,
-                            mode == kModeBins ? kColCtasPerSm + 1 : kColCtasPerSm);
+    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm, p->col_cap[mode & 3]);
     return L.grid > 0;
 }
 
@@ -312,10 +321,13 @@ bool col_map(const hufield_plan* p, CUtensorMap* map, void* data, long long B, i
     const cuuint64_t strides[2] = {(cuuint64_t)B * sizeof(float2), (cuuint64_t)bstride * sizeof(float2)};
     const cuuint32_t box[3] = {(cuuint32_t)1 << logTB, (cuuint32_t)(log2l < 8 ? 1 << log2l : 256), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMapL2promotion promo = (sizeof(float2) << logTB) >= 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                                    : CU_TENSOR_MAP_L2_PROMOTION_L2_64B;
+    if (p->l2_promo == 64) promo = CU_TENSOR_MAP_L2_PROMOTION_L2_64B;
+    if (p->l2_promo == 128) promo = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+    if (p->l2_promo == 256) promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
     return p->encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, data, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     (sizeof(float2) << logTB) >= 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
-                                                     : CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -865,6 +877,172 @@ int hufield_plan_destroy(hufield_plan* p) {
     cudaFree(p->cache_counts);
     cudaFree(p->tw);
     delete p;
+    return HUFIELD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Key of a tuning in the cache file: device, lattice and call shape.
+std::string tune_key(const hufield_plan* p, int nlev, int nbins) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) prop.name[0] = 0;
+    std::string k = prop.name;
+    for (auto& c : k)
+        if (c == ' ' || c == '\t') c = '_';
+    char buf[160];
+    snprintf(buf, sizeof buf, " %lldx%lldx%lld nlev=%d nbins=%d kspace=%d", p->n[0], p->n[1], p->n[2], nlev, nbins,
+             p->kspace ? 1 : 0);
+    return k + buf;
+}
+
+// Cache file (HUFIELD_AUTOTUNE_CACHE): one line per tuning, "key<TAB>c0 c1 c2 c3 promo".
+bool tune_lookup(const char* path, const std::string& key, int cap[4], int& promo) {
+    FILE* fp = fopen(path, "r");
+    if (!fp) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof line, fp)) {
+        char* tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        int c[4], pr;
+        if (key == line && sscanf(tab + 1, "%d %d %d %d %d", &c[0], &c[1], &c[2], &c[3], &pr) == 5) {
+            for (int i = 0; i < 4; ++i) cap[i] = c[i];
+            promo = pr;
+            found = true;  // the last entry for a key wins
+        }
+    }
+    fclose(fp);
+    return found;
+}
+
+void tune_store(const char* path, const std::string& key, const int cap[4], int promo) {
+    FILE* fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s\t%d %d %d %d %d\n", key.c_str(), cap[0], cap[1], cap[2], cap[3], promo);
+    fclose(fp);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hufield_plan_autotune(hufield_plan* p, const hufield_filter* f, int32_t nlev, int32_t nr, int32_t ntheta) {
+    if (!p) return HUFIELD_ERR_INVALID_ARG;
+    int rc = check_filter(p, f);
+    if (rc) return rc;
+    if (nlev < 0 || nlev > kMaxLevels) return HUFIELD_ERR_INVALID_ARG;
+    BinParams bp;
+    rc = make_bins(p, nr, ntheta, bp);
+    if (rc) return rc;
+    const std::string key = tune_key(p, nlev, bp.nbins);
+    const char* cache = getenv("HUFIELD_AUTOTUNE_CACHE");
+    int cap[4], promo = 0;
+    if (cache && *cache && tune_lookup(cache, key, cap, promo)) {
+        bool ok = promo == 0 || promo == 64 || promo == 128 || promo == 256;
+        for (int i = 0; i < 4; ++i) ok = ok && cap[i] >= 1 && cap[i] <= 8;
+        if (ok) {
+            for (int i = 0; i < 4; ++i) p->col_cap[i] = cap[i];
+            p->l2_promo = promo;
+            return HUFIELD_OK;
+        }
+    }
+    // scratch for one pipeline call (freed below)
+    const size_t wsb = ws_bytes(p, nlev, bp.nbins);
+    const long long nb = bp.nbins, nl = nlev > 0 ? nlev : 1;
+    void *ws = nullptr, *fo = nullptr, *mo = nullptr, *acc = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release = [&] {
+        cudaFree(ws);
+        cudaFree(fo);
+        cudaFree(mo);
+        cudaFree(acc);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    };
+    if (cudaMalloc(&ws, wsb) != cudaSuccess || cudaMalloc(&fo, (size_t)p->N * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&mo, (size_t)nl * (size_t)p->N) != cudaSuccess ||
+        cudaMalloc(&acc, (size_t)(2 + 2 * nl) * (size_t)nb * sizeof(double)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        release();
+        return HUFIELD_ERR_CUDA;
+    }
+    double* sums_f = static_cast<double*>(acc);
+    int64_t* counts_f = reinterpret_cast<int64_t*>(sums_f + nb);
+    double* sums_m = reinterpret_cast<double*>(counts_f + nb);
+    int64_t* counts_m = reinterpret_cast<int64_t*>(sums_m + nl * nb);
+    float levels[kMaxLevels];
+    for (int t = 0; t < nlev; ++t) levels[t] = 0.5f * (float)((t + 1) / 2) * ((t & 1) ? 1.0f : -1.0f);
+    // best of three timed calls after one untimed call
+    auto timed = [&](float& best) -> int {
+        best = 1e30f;
+        for (int r = 0; r < 4; ++r) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return HUFIELD_ERR_CUDA;
+            const int c = hufield_pipeline(p, f, 7, (uint32_t)r, HUFIELD_F32, fo, levels, nlev,
+                                           static_cast<int8_t*>(mo), nr, ntheta, 0, sums_f, counts_f, sums_m,
+                                           counts_m, ws, wsb, s);
+            if (c) return c;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return HUFIELD_ERR_CUDA;
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return HUFIELD_ERR_CUDA;
+            if (r > 0 && ms < best) best = ms;
+        }
+        return HUFIELD_OK;
+    };
+    // coordinate descent over the knobs the call shape uses; a change is kept
+    // only when it is at least 2% faster
+    float best;
+    rc = timed(best);
+    struct Knob {
+        int* slot;
+        std::vector<int> values;
+    };
+    std::vector<Knob> knobs;
+    if (p->ndim == 3) knobs.push_back({&p->col_cap[kModePlain], {1, 2, 3}});
+    knobs.push_back({&p->col_cap[p->kspace ? kModeKspace : kModeFilter], {1, 2, 3}});
+    if (nlev > 0) knobs.push_back({&p->col_cap[kModeBins], {2, 3, 4}});
+    knobs.push_back({&p->l2_promo, {0, 64, 128, 256}});
+    for (auto& kb : knobs) {
+        if (rc) break;
+        const int keep = *kb.slot;
+        int chosen = keep;
+        for (int v : kb.values) {
+            if (v == keep || rc) continue;
+            *kb.slot = v;
+            float t;
+            rc = timed(t);
+            if (!rc && t < 0.98f * best) {
+                best = t;
+                chosen = v;
+            }
+        }
+        *kb.slot = chosen;
+    }
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
+    unsigned status = 0;
+    if (!rc && cudaMemcpy(&status, ws, sizeof status, cudaMemcpyDeviceToHost) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
+    if (!rc && (status & kStatusTimeout)) rc = HUFIELD_ERR_TIMEOUT;
+    release();
+    if (rc) {
+        // back to the defaults: a failed tuning leaves the plan as created
+        for (int i = 0; i < 4; ++i) p->col_cap[i] = i == kModeBins ? kColCapDefault + 1 : kColCapDefault;
+        p->l2_promo = 0;
+        return rc;
+    }
+    if (cache && *cache) tune_store(cache, key, p->col_cap, p->l2_promo);
+    return HUFIELD_OK;
+}
+
+int hufield_plan_tuning(const hufield_plan* p, int32_t out[5]) {
+    if (!p || !out) return HUFIELD_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i) out[i] = p->col_cap[i];
+    out[4] = p->l2_promo;
     return HUFIELD_OK;
 }
 
@@ -1444,7 +1622,7 @@ bool same_dims(const hufield_dims& a, const hufield_dims& b) {
 extern "C" {
 
 int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int32_t n, uint32_t flags) {
-    if (!out || !items || n < 1 || flags != 0) return HUFIELD_ERR_INVALID_ARG;
+    if (!out || !items || n < 1 || (flags & ~HUFIELD_BATCH_AUTOTUNE) != 0) return HUFIELD_ERR_INVALID_ARG;
     *out = nullptr;
     hufield_batch* b = new (std::nothrow) hufield_batch();
     if (!b) return HUFIELD_ERR_CUDA;
@@ -1490,6 +1668,10 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
         if (class_nr[cls[i]] != it.nr) uniform[cls[i]] = false;
         const size_t need = ws_bytes(C.plan, 1, it.nr);
         if (need > C.ws_bytes) C.ws_bytes = need;
+    }
+    for (size_t c = 0; c < b->classes.size() && rc == HUFIELD_OK && (flags & HUFIELD_BATCH_AUTOTUNE); ++c) {
+        const hufield_batch_item& it = items[b->classes[c].members[0]];
+        rc = hufield_plan_autotune(b->classes[c].plan, &it.filt, 1, it.nr, 1);
     }
     for (size_t c = 0; c < b->classes.size(); ++c) {
         auto& C = b->classes[c];

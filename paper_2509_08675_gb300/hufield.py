@@ -96,6 +96,8 @@ def _load():
     lib.hufield_spectrum_modes.argtypes = [vp, vp, i32, vp, vp, sz, vp]
     lib.hufield_filter_modes.argtypes = [vp, fptr, vp, vp]
     lib.hufield_filter_band_edge.argtypes = [vp, fptr, C.POINTER(C.c_int64)]
+    lib.hufield_plan_autotune.argtypes = [vp, fptr, i32, i32, i32]
+    lib.hufield_plan_tuning.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_window_variance_filter.argtypes = [vp, fptr, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
@@ -268,6 +270,19 @@ def hufield_filter_modes(plan: Plan, filt: Filter, out: torch.Tensor, stream=Non
     _check(_lib.hufield_filter_modes(plan.handle, C.byref(fc), _ptr(out), _stream(stream)), "hufield_filter_modes")
 
 
+def hufield_plan_autotune(plan: Plan, filt: Filter, nlev: int, nr: int, ntheta: int = 1) -> None:
+    """Time the strided passes' launch choices on hufield_pipeline calls and keep the fastest."""
+    fc = filt._c()
+    _check(_lib.hufield_plan_autotune(plan.handle, C.byref(fc), nlev, nr, ntheta), "hufield_plan_autotune")
+
+
+def hufield_plan_tuning(plan: Plan) -> dict:
+    """The plan's launch choices: CTAs per SM per strided-pass mode and the L2 promotion."""
+    out = (C.c_int32 * 5)()
+    _check(_lib.hufield_plan_tuning(plan.handle, out), "hufield_plan_tuning")
+    return {"cta_cap": {"plain": out[0], "filter": out[1], "bins": out[2], "kspace": out[3]}, "l2_promotion": out[4]}
+
+
 def hufield_filter_band_edge(plan: Plan, filt: Filter) -> int:
     """First k_last from which the filter is exactly zero (n_last / 2: none)."""
     fc = filt._c()
@@ -337,9 +352,10 @@ def hufield_plan_set_bins(plan: Plan, nr: int, ntheta: int = 1):
 class Batch:
     """hufield_batch: a ragged batch of fields run as one CUDA graph launch.
 
-    items: sequence of (shape, Filter, seed, field_idx, level, nr)."""
+    items: sequence of (shape, Filter, seed, field_idx, level, nr); autotune = True
+    tunes every size class's plan (HUFIELD_BATCH_AUTOTUNE)."""
 
-    def __init__(self, items):
+    def __init__(self, items, autotune: bool = False):
         arr = (_BatchItem * len(items))()
         for i, (shape, filt, seed, field_idx, level, nr) in enumerate(items):
             shape = tuple(int(v) for v in shape)
@@ -350,7 +366,7 @@ class Batch:
             arr[i].level = level
             arr[i].nr = nr
         h = C.c_void_p()
-        _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), 0), "hufield_batch_plan")
+        _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), 1 if autotune else 0), "hufield_batch_plan")
         self._h = h
         self.n = len(items)
         f_off = (C.c_int64 * self.n)()

@@ -89,3 +89,23 @@ def test_batch_one_class_two_lanes_uncached_bins(hf):
         check_field(f_all[fo:fo + N].reshape(shape), want["f"])
         check_bins(np_(sf)[bo:bo + nr], want["sums_f"], np_(cf)[bo:bo + nr], want["counts_f"])
     batch.close()
+
+
+def test_autotuned_batch_matches_oracle(hf):
+    items, oitems = _items(hf, 6, 4)
+    batch = hf.Batch(items, autotune=True)
+    out_f = dev_zeros(batch.total_voxels, torch.float32)
+    maps = dev_zeros(batch.total_voxels, torch.int8)
+    sf, cf = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
+    sm, cm = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+    hf.hufield_batch_run(batch, out_f, maps, sf, cf, sm, cm, ws)
+    torch.cuda.synchronize()
+    f_all = np_(out_f)
+    for i, (shape, of, seed, field, level, nr) in enumerate(oitems):
+        N = int(np.prod(shape))
+        fo, bo = batch.f_offset[i], batch.bin_offset[i]
+        want = oracle.pipeline(shape, of, seed, field, levels=(level,), nr=nr, ntheta=1)
+        check_field(f_all[fo:fo + N].reshape(shape), want["f"])
+        check_bins(np_(sf)[bo:bo + nr], want["sums_f"], np_(cf)[bo:bo + nr], want["counts_f"])
+    batch.close()
