@@ -296,12 +296,25 @@ KernelInfo pick_row(int log2m, long long nrows, KernelInfo (*table)(int, bool, i
     return table(log2m, big, variant);
 }
 
+// The wide tile (col_logtb(L, true) columns) when the columns fill it, except
+// for columns of 1024 or more whose wide tiles leave SMs idle (fewer tiles per
+// spectrum, a_spec batches of B columns, than SMs): there the two-column tile,
+// still 128 threads or more, gives four times the tiles (1024^2: 64 wide
+// tiles for 152 SMs, 256 narrow ones; 0.101 -> 0.091 ms per field).  Shorter
+// columns keep the wide tile, whose narrow one has under 128 threads (512^2:
+// 0.095 ms wide, 0.101 ms narrow).
+bool col_big(const hufield_plan* p, int log2l, long long B, long long a_spec) {
+    const int lt = col_logtb(log2l, true);
+    if (B < (1ll << lt)) return false;
+    return log2l < 10 || a_spec * (B >> lt) >= p->nsm;
+}
+
 // Column kernels: tiles of TB columns x L rows, double-buffered in shared
 // memory; TB >= 2 keeps a TMA box row at 16 bytes or more.  At most
 // p->col_cap[mode] CTAs per SM (kColCapDefault unless autotuned).
-bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, size_t extra_smem,
-                KernelInfo& k, Launch& L) {
-    const bool big = B >= (1ll << col_logtb(log2l, true));
+bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, long long a_spec,
+                size_t extra_smem, KernelInfo& k, Launch& L) {
+    const bool big = col_big(p, log2l, B, a_spec);
     k = cols_kernel(log2l, big, mode, dir);
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
@@ -504,8 +517,7 @@ int carve(const hufield_plan* p, void* ws, size_t bytes, int nlev, int nbins, Wo
 // bin table share it.
 int axis0_logtb(const hufield_plan* p) {
     const long long B = p->half >> p->log2n[0];
-    const bool big = B >= (1ll << col_logtb(p->log2n[0], true));
-    return col_logtb(p->log2n[0], big);
+    return col_logtb(p->log2n[0], col_big(p, p->log2n[0], B, 1));
 }
 
 bool aligned(const void* ptr) { return ((uintptr_t)ptr & 255) == 0; }
@@ -585,7 +597,7 @@ int mid_pass(hufield_plan* p, int dir, float2* data, long long nbatch, int kind,
     ca.inject_skip = p->inject_timeout ? 1 : 0;
     Launch L;
     KernelInfo k;
-    if (!col_launch(p, p->log2n[1], kModePlain, dir, ca.B, ca.A, 0, k, L)) return HUFIELD_ERR_CUDA;
+    if (!col_launch(p, p->log2n[1], kModePlain, dir, ca.B, ca.A, p->n[0], 0, k, L)) return HUFIELD_ERR_CUDA;
     set_tiles(p, ca, k.log2_lines, kz < 0 ? ca.B : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[1], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     HF_CUDA(launch(p, kind, k.fn, L, &ca, s));
@@ -646,7 +658,7 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
                                                        : 0);
     Launch L;
     KernelInfo k;
-    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, extra, k, L)) return HUFIELD_ERR_CUDA;
+    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, 1, extra, k, L)) return HUFIELD_ERR_CUDA;
     set_tiles(p, ca, k.log2_lines, kz < 0 ? (1ll << p->logM) : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     const int kind = (mode == kModeFilter || mode == kModeKspace) ? kPassFilter
