@@ -784,21 +784,6 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     Launch L;
     const KernelInfo k = pick_row(p->logM, ca.nrows, c2r_kernel, out_dtype == HUFIELD_BF16 ? 1 : 0);
     if (!row_launch(p, k, ca.nrows, L)) return HUFIELD_ERR_CUDA;
-    // past the band edge c2r loads only the rows' first kzw entries (one box of
-    // at most 256 per row); HBM reads of the spectrum fall to kzw / M
-    const long long M = 1ll << p->logM, kzw = (kz + 1) & ~1ll;
-    ca.kzw = 0;
-    if (kz < M && kzw >= 2 && kzw <= 256) {
-        const cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)ca.nrows, 1};
-        const cuuint64_t strides[2] = {(cuuint64_t)M * sizeof(float2), (cuuint64_t)ca.nrows * M * sizeof(float2)};
-        const cuuint32_t box[3] = {(cuuint32_t)kzw, (cuuint32_t)1 << k.log2_lines, 1};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        if (p->encode(&ca.rmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, w.spec, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return HUFIELD_ERR_CUDA;
-        ca.kzw = (int)kzw;
-    }
     HF_CUDA(launch(p, kPassC2R, k.fn, L, &ca, s));
     if (bp && nlev > 0 && sums_m) {
         if (p->ndim == 3) {

@@ -39,7 +39,6 @@ struct RowArgs {
 };
 
 struct C2RArgs {
-    CUtensorMap rmap;       // kzw > 0: (M, nrows, 1) elements of spec, box (kzw, rows per tile, 1)
     float2* spec;           // [nrows][M] filtered spectrum in; map spectra out (level t at spec + t * half)
     long long nrows;
     long long half;         // N / 2
@@ -61,7 +60,6 @@ struct C2RArgs {
     long long wait_budget;  // clock cycles allowed per mbarrier wait
     int inject_skip;        // test hook: 1 = the first tile's load is never issued
     int kz;                 // entries k_last >= kz of each row are zero (<= M)
-    int kzw;                // > 0: load the first kzw (even, >= kz, <= 256) entries of each row through rmap
 };
 
 struct ColArgs {
@@ -393,20 +391,13 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     long long t0, t1;
     chunk_of(a.nrows >> LOGTR, t0, t1);
     // Entries k_last >= kz are zero (the filter's band ends before them) and
-    // were not written by the passes before; they are read as zero.  With
-    // kzw > 0 one tensor copy brings the first kzw entries of the tile's rows
-    // (rows kzw apart in shared memory); else one bulk copy brings whole rows
-    // (a bulk copy per row of the entries below kz measured slower).
+    // were not written by the passes before: they are loaded with the rest of
+    // the tile (one bulk copy measured faster than a copy per row of the
+    // entries below kz) and read as zero.
     const int kz = a.kz;
-    const int rs = a.kzw > 0 ? a.kzw : M;  // row stride of the loaded tile
     auto issue = [&](long long tile, float2* dst, uint64_t* b) {
-        if (a.kzw > 0) {
-            mbar_arrive_expect_tx(b, (uint32_t)(G::TB * a.kzw) * (uint32_t)sizeof(float2));
-            tma_load_3d(dst, &a.rmap, 0, (int)(tile << LOGTR), 0, b);
-        } else {
-            mbar_arrive_expect_tx(b, tile_bytes);
-            bulk_load(dst, a.spec + tile * tile_elems, tile_bytes, b);
-        }
+        mbar_arrive_expect_tx(b, tile_bytes);
+        bulk_load(dst, a.spec + tile * tile_elems, tile_bytes, b);
     };
     load_half_twiddles<LOG2M>(tw, a.tw, t, G::T);
     float2* twi = load_plan_twiddles<LOG2M>(twf, a.tw, t, G::T);
@@ -434,7 +425,7 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
         float2 v[E];
         // c2r pre-processing: Z[k] = (X[k] + X*[M-k]) + i (X[k] - X*[M-k]) W_N^{-k}
         for_each_element<G, PI::first_radix()>(t, [&](int e, int b, int k) {
-            const float2* rowp = buf + b * rs;
+            const float2* rowp = buf + (b << LOG2M);
             float2 X = k < kz ? rowp[k] : make_float2(0.0f, 0.0f);
             float2 Xmc = make_float2(0.0f, 0.0f);
             if (k == 0) {
