@@ -31,3 +31,23 @@ def test_band_edge_scales_only_the_pruned_passes():
         assert a[k] == b[k]
     for k in ("cols_mid_fwd", "cols_filter", "cols_mid_inv"):
         assert a[k] == pytest.approx(0.25 * b[k])
+
+
+def test_ragged_draws_are_seeded_and_in_range():
+    # the ragged workload's items: the same for the same seed, sizes from the nine
+    # lattices, parameters inside the stated ranges (host logic only)
+    from paper_2509_08675_gb300 import hufield as hf
+
+    a = bench.ragged_items(hf, 300, seed=0)
+    b = bench.ragged_items(hf, 300, seed=0)
+    c = bench.ragged_items(hf, 300, seed=1)
+    key = lambda items: [(s, f.p, f.axes, f.rot, f.k0, f.width, f.supp, lvl, nr)  # noqa: E731
+                         for s, f, _, _, lvl, nr in items]
+    assert key(a) == key(b) and key(a) != key(c)
+    sizes = {s for s, *_ in a}
+    assert sizes <= set(bench.RAGGED["sizes"]) and len(sizes) == len(bench.RAGGED["sizes"])
+    for shape, f, seed, i, level, nr in a:
+        assert 1.0 <= f.p <= 8.0 and 0.0 <= f.rot < 3.1416 and 0.05 <= f.k0 <= 0.4 and 0.01 <= f.width <= 0.1
+        assert f.supp in (2.0, 4.0, 6.0) and -1.0 <= level <= 1.0 and nr == min(128, shape[0] // 2)
+        axes = f.axes[:len(shape)]
+        assert all(0.5 <= r <= 2.0 for r in axes[-2:]) and (len(shape) == 2 or axes[0] == 1.0)
