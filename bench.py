@@ -59,26 +59,36 @@ def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0):
     r2c writes the half spectrum (4 B/voxel); a strided pass reads and writes it
     (8 B/voxel per spectrum; the filter pass of k-space noise only writes it);
     c2r reads it, writes the field, nlev sign maps and nlev map spectra; the
-    bins pass reads the nlev map spectra; the binning passes read the bin table
-    (1 B/voxel each time), which the table pass ("counts") writes once per
-    call.  Only the columns below the filter's band edge hold nonzero data
-    after the filter (a fraction `live` = kz / (n_last / 2) of the half
-    spectrum): the axis-1 forward, the filter pass and the axis-1 inverse move
-    that part, and c2r needs only it."""
+    bins pass reads the nlev map spectra.  Only the columns below the filter's
+    band edge hold nonzero data after the filter (a fraction `live` = kz /
+    (n_last / 2) of the half spectrum): the axis-1 forward, the filter pass and
+    the axis-1 inverse move that part, and c2r needs only it.  The bins of each
+    mode are a function of its integer indices, so the bin table the binning
+    passes read is an implementation choice, counted apart (overhead_bytes)."""
     N = math.prod(shape)
     h = 4 * N  # half spectrum bytes
-    tab = N  # bin table: one uint16 per half-spectrum mode
     return {
         "r2c": h,
         "cols_mid_fwd": 2 * h * live,
-        "cols_filter": ((1 if kspace else 2) * h + tab) * live,
+        "cols_filter": (1 if kspace else 2) * h * live,
         "cols_mid_inv": 2 * h * live,
         "c2r": h * live + field_bytes * N + nlev * N + nlev * h,
         "cols_mid_maps": 2 * h * nlev,
-        "cols_bins": (h + tab) * nlev,
-        "counts": tab,
+        "cols_bins": h * nlev,
+        "counts": 0,
         "misc": 0,
     }
+
+
+def overhead_bytes(shape, nlev, live=1.0):
+    """Bytes beyond the pass plan that the passes move per launch: the bin table
+    (one uint16 per half-spectrum mode, N/2 modes; half of that with the
+    paired radial order, counted here at its larger size) read by the filter
+    pass over its live columns and by the bins pass once per map, and written
+    by the table pass once per plan."""
+    N = math.prod(shape)
+    tab = N
+    return {"cols_filter": tab * live, "cols_bins": tab * nlev, "counts": tab}
 
 
 def field_bytes(shape, nlev, live, kspace=False, out_bytes=4):
@@ -481,8 +491,15 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     dom = max((k for k in passes if algo.get(k, 0)), key=lambda k: passes[k]["ms_total"])
     per_step_bytes = sum(algo[k] * passes[k]["launches"] / args.steps for k in passes if algo.get(k))
     pipe_gbs = per_step_bytes / (tot_ms / args.steps / 1e3) / 1e9
+    over = overhead_bytes(shape, nlev, live)
+    dom_per = passes[dom]["ms_per_launch"]
+    traffic = TRAFFIC.get((name, dom))
     roof = {"bound": "hbm", "achieved": passes[dom]["GBps"], "peak": peak, "unit": "GB/s",
-            "frac": passes[dom]["frac"], "traffic": TRAFFIC.get((name, dom)),
+            "frac": passes[dom]["frac"], "traffic": traffic,
+            "algorithmic_bytes": algo[dom],
+            "traffic_over_algorithmic": round(traffic / algo[dom], 3) if traffic else None,
+            "overhead_bytes": over.get(dom, 0),
+            "frac_with_overhead": round((algo[dom] + over.get(dom, 0)) / (dom_per / 1e3) / 1e9 / peak, 4),
             "kernel": dom, "peak_source": peak_kind}
     return {"value": value, "ms_per_step": tot_ms / args.steps, "ms_per_step_one_lane": round(one_ms, 4),
             "lanes": 2 if nf >= 2 else 1, "roofline": roof,
