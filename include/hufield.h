@@ -243,6 +243,15 @@ int hufield_ensemble(hufield_plan *plan, const hufield_filter *filt, uint64_t se
 int hufield_spectrum_noalloc(const hufield_dims *dims, const void *y, int32_t dtype, int32_t nr, int32_t ntheta,
                              int32_t accumulate, double *sums, int64_t *counts, void *stream);
 
+/* Device-side status of the most recent hufield_spectrum_noalloc call on the
+ * current device: the allocation-free call has no workspace, so its kernels
+ * report a bounded wait that ran out in a word of the library's static
+ * scratch instead.  Waits for `stream`, reads that word (no allocation) and
+ * returns HUFIELD_ERR_TIMEOUT (that call's bins are undefined) or HUFIELD_OK
+ * (also before any call on the device); HUFIELD_ERR_CUDA if the copy fails.
+ * The word belongs to whichever call ran last, like the rest of the scratch. */
+int hufield_spectrum_noalloc_status(void *stream);
+
 /* ---- Ragged batches ------------------------------------------------------
  * Many fields of different lattices and filters in one launch: the whole
  * path (as hufield_pipeline with one level and radial bins) for every item.

@@ -1575,6 +1575,25 @@ extern "C" int hufield_spectrum_noalloc(const hufield_dims* dims, const void* y,
     return axis0_pass(&p, kModeBins, st.spec, 1, nullptr, bp, st.bintab, sums, nullptr, st.status, s);
 }
 
+// The static scratch's status word: set by the kernels of the most recent
+// hufield_spectrum_noalloc call on the current device (each call clears it in
+// stream order before its kernels run).  Waits for `stream`.
+extern "C" int hufield_spectrum_noalloc_status(void* stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HUFIELD_ERR_CUDA;
+    unsigned* word_dev = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static[dev].ready) return HUFIELD_OK;  // no call on this device yet
+        word_dev = g_static[dev].status;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned word = 0;
+    HF_CUDA(cudaMemcpyAsync(&word, word_dev, sizeof(word), cudaMemcpyDeviceToHost, s));
+    HF_CUDA(cudaStreamSynchronize(s));
+    return (word & kStatusTimeout) ? HUFIELD_ERR_TIMEOUT : HUFIELD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Ragged batches (hufield_batch_*): one plan per size class, and per class
 // up to kBatchLanes lanes (a stream and a workspace slice each) that take its

@@ -106,6 +106,7 @@ def _load():
                                      i32, vp, vp, vp, vp, vp, sz, vp]
     lib.hufield_bins_mean.argtypes = [vp, vp, i32, vp, vp]
     lib.hufield_spectrum_noalloc.argtypes = [C.POINTER(_Dims), vp, i32, i32, i32, i32, vp, vp, vp]
+    lib.hufield_spectrum_noalloc_status.argtypes = [vp]
     lib.hufield_status_string.argtypes = [C.c_int]
     lib.hufield_status_string.restype = C.c_char_p
     lib.hufield_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
@@ -334,9 +335,24 @@ def hufield_spectrum_noalloc(shape, y: torch.Tensor, nr: int, ntheta: int, accum
     shape = tuple(int(v) for v in shape)
     if len(shape) not in (2, 3):
         raise HufieldError(ERR_UNSUPPORTED_DIMS, "hufield_spectrum_noalloc")
+    # the C call sees only pointers: buffers smaller than the lattice and the bins
+    # would be read or written out of bounds on the device
+    nbins = int(nr) * int(ntheta)
+    if y.numel() != math.prod(shape) or y.dtype not in _DTYPES:
+        raise HufieldError(ERR_INVALID_ARG, "hufield_spectrum_noalloc: y must hold prod(shape) F32/BF16/I8 values")
+    if nbins < 1 or sums.dtype != torch.float64 or counts.dtype != torch.int64 or sums.numel() < nbins \
+            or counts.numel() < nbins:
+        raise HufieldError(ERR_INVALID_ARG, "hufield_spectrum_noalloc: sums (float64) and counts (int64) need "
+                                            "nr * ntheta entries")
     dims = _Dims(len(shape), 0, (C.c_int64 * 3)(*(shape + (1,) * (3 - len(shape)))))
     _check(_lib.hufield_spectrum_noalloc(C.byref(dims), _ptr(y), _DTYPES[y.dtype], nr, ntheta, int(accumulate),
                                          _ptr(sums), _ptr(counts), _stream(stream)), "hufield_spectrum_noalloc")
+
+
+def hufield_spectrum_noalloc_status(stream=None) -> int:
+    """Status of the most recent hufield_spectrum_noalloc call on the current device
+    (waits for the stream): OK or ERR_TIMEOUT."""
+    return int(_lib.hufield_spectrum_noalloc_status(_stream(stream)))
 
 
 def hufield_workspace_status(ws: torch.Tensor, stream=None) -> int:

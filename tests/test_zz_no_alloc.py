@@ -36,7 +36,26 @@ def test_noalloc_matches_workspace_call_twice(hf, shape, nr, nt):
         s, c = dev_zeros(nr * nt, torch.float64), dev_zeros(nr * nt, torch.int64)
         hf.hufield_spectrum_noalloc(shape, y, nr, nt, False, s, c)
         torch.cuda.synchronize()
+        assert hf.hufield_spectrum_noalloc_status() == hf.OK
         check_bins(np_(s), ws_, np_(c), wc)
+
+
+def test_noalloc_allocates_nothing(hf):
+    # after the first call on the device (the set-up, and the first use of the
+    # kernels), further calls leave both torch's pool and the device's free
+    # memory exactly as they were
+    shape, nr = (128, 128), 32
+    y = torch.from_numpy(inputs.random_field(shape, 34, np.float32)).cuda()
+    s, c = dev_zeros(nr, torch.float64), dev_zeros(nr, torch.int64)
+    hf.hufield_spectrum_noalloc(shape, y, nr, 1, False, s, c)
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    for _ in range(3):
+        hf.hufield_spectrum_noalloc(shape, y, nr, 1, True, s, c)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    assert after == before
+    assert hf.hufield_spectrum_noalloc_status() == hf.OK
 
 
 def test_noalloc_accumulates_and_rejects_too_large(hf):
@@ -52,3 +71,8 @@ def test_noalloc_accumulates_and_rejects_too_large(hf):
     with pytest.raises(hf.HufieldError) as e:
         hf.hufield_spectrum_noalloc((2048, 1024), big, 16, 1, False, s, c)
     assert e.value.status == hf.ERR_TOO_LARGE
+    # buffers that do not match the lattice or the bins are refused before any launch
+    for args in (((64, 128), y, 16, 1), (shape, y, 32, 1), (shape, y, 4, 8)):
+        with pytest.raises(hf.HufieldError) as e:
+            hf.hufield_spectrum_noalloc(*args, False, s, c)
+        assert e.value.status == hf.ERR_INVALID_ARG
