@@ -25,7 +25,7 @@
  *   window     sigma_F^2(R), Eq. (1): variance of the field averaged over a
  *              ball of radius R, from the spectrum
  *
- * Readings of points the paper leaves open (each listed in the design notes):
+ * Readings of points the paper leaves open (Sec. II.B is silent on each):
  *   - noise is Philox4x32-10 (Salmon et al., SC'11) with key = seed and
  *     counter = (j lo, j hi, field_idx, 0), j = voxel >> 2, followed by
  *     Box-Muller on (x0,x1) and (x2,x3), u = (x + 1/2) 2^-32;

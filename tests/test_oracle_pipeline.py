@@ -189,6 +189,65 @@ def test_arcsine_law_for_zero_threshold():
     assert abs(acc[sel].sum() / want[sel].sum() - 1.0) < 0.08
 
 
+def _phi2_equal(t, rho):
+    """P(X < t, Y < t) for standard normals with correlation rho: Phi(t)^2 plus the
+    integral over r from 0 to rho of the bivariate density at (t, t), which with
+    r = sin(u) is exp(-t^2 / (1 + sin u)) / (2 pi) du (Gauss-Legendre in u)."""
+    from scipy.stats import norm
+
+    x, w = np.polynomial.legendre.leggauss(48)
+    top = np.arcsin(np.clip(np.asarray(rho, np.float64), -1.0, 1.0))
+    u = 0.5 * top[..., None] * (x + 1.0)
+    integral = 0.5 * top * np.sum(w * np.exp(-t * t / (1.0 + np.sin(u))), axis=-1) / (2.0 * np.pi)
+    return norm.cdf(t) ** 2 + integral
+
+
+def test_bivariate_normal_quadrature_against_scipy():
+    # the quadrature used by the t != 0 pin below, against scipy's own bivariate normal CDF
+    from scipy.stats import multivariate_normal
+
+    for t in (-0.5, 0.0, 0.5, 1.2):
+        for rho in (-0.9, -0.3, 0.0, 0.4, 0.95):
+            want = multivariate_normal(mean=[0, 0], cov=[[1, rho], [rho, 1]]).cdf([t, t])
+            assert abs(_phi2_equal(t, rho) - want) < 1e-6, (t, rho)
+
+
+@pytest.mark.parametrize("level", [0.5, -0.5])
+def test_map_spectrum_for_nonzero_threshold(level):
+    # m = sgn(f - t) of a unit-variance Gaussian field with correlation rho(r):
+    # E[m(x) m(x+r)] = 1 - 4 Phi(t) + 4 Phi_2(t, t; rho(r)), so away from DC the
+    # ensemble spectrum of the map is the DFT of that covariance (t = 0 is the
+    # arcsine law above); rho = IDFT(A^2) / sum A^2 (Wiener-Khinchin, Sec. II.B)
+    from scipy.stats import norm
+
+    shape = (32, 32)
+    H2 = oracle.filter_grid(shape, F2) ** 2
+    rho = np.fft.ifftn(H2).real
+    rho /= rho.flat[0]
+    mean = 1.0 - 2.0 * norm.cdf(level)
+    cov = 1.0 - 4.0 * norm.cdf(level) + 4.0 * _phi2_equal(level, rho) - mean * mean
+    want = np.fft.fftn(cov).real
+    acc = np.zeros(shape)
+    M = 128
+    for e in range(M):
+        f = oracle.generate(shape, F2, seed=23, field_idx=e)
+        acc += oracle.spectrum_modes(oracle.threshold(f, level).astype(np.float64))
+    acc /= M
+    # the sum of the covariance spectrum over all modes is N C(0) = N (1 - mean^2)
+    assert abs(want.sum() / (want.size * (1.0 - mean * mean)) - 1.0) < 1e-9
+    sel = want > 0.05 * want.max()
+    sel[0, 0] = False  # DC carries the squared mean, checked below
+    # (128 fields put the sample error near 1%; a level off by 0.2 sigma moves these by 10-15%)
+    assert abs(acc[sel].sum() / want[sel].sum() - 1.0) < 0.03
+    # and the broadband part a threshold adds (modes far from the band) within its sample band
+    far = (want < 0.05 * want.max()) & (want > 0)
+    far[0, 0] = False
+    assert abs(acc[far].sum() / want[far].sum() - 1.0) < 0.04
+    # DC holds the squared mean: E S(0) = N E[mbar^2] = N mean^2 + (the covariance's DC term)
+    N = acc.size
+    assert abs(acc[0, 0] / (N * mean * mean + want[0, 0]) - 1.0) < 0.06
+
+
 def test_noise_dft_at_matches_fft():
     shape = (8, 16, 4)
     z = oracle.noise(shape, seed=5, field_idx=1)
