@@ -1,0 +1,141 @@
+"""Element-wise parity at the benchmark's full sizes, in the launch configuration
+the benchmark times (plan-cached bins; an ensemble on two lanes), against the
+FP64 oracle's whole pipeline (Sec. II.B, Eqs. 8-15, the sign map and the binned
+S(k)) on the same seeds:
+
+- 4096^2, p = 4, semi-axes 1:0.5 rotated 30 degrees, levels 0 and +-0.5,
+  64 x 36 bins: fields 0 and 1 of an ensemble on two lanes, every voxel of
+  both fields and all six maps, and the field and map bins summed over both;
+- 512^3, p = 6, semi-axes 1:1:0.5, level 0, 256 bins: the whole field, map and
+  bins, and the BF16 storage variant's error against the same oracle field;
+- 1024^3 (same filter) when the host has the memory for the oracle's FP64
+  grids (about 60 GB); otherwise skipped with the reason.
+
+Tolerances are those of every parity test: field relative L2 <= 2e-6 and
+max |err| <= 1e-4 rms; maps bit-exact except where |f - t| < 1e-4 rms; bins
+within 1e-4 relative (plus the exact allowance of the sites allowed to
+differ)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests import inputs
+from tests.gpu_common import check_bins, check_field, check_maps, dev_zeros, filters, np_, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SEED = 21
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def _run_ensemble(hf, shape, gf, levels, nr, nt, nf, lanes, out_dtype=torch.float32):
+    """The benchmark's call: plan-cached bins, one ensemble call of nf fields."""
+    plan = hf.Plan(shape)
+    hf.hufield_plan_set_bins(plan, nr, nt)
+    nb, nlev = nr * nt, len(levels)
+    ws = plan.workspace(nlev, nb, lanes=lanes)
+    out_f = torch.empty((nf,) + shape, dtype=out_dtype, device="cuda")
+    maps = torch.empty((nf, nlev) + shape, dtype=torch.int8, device="cuda")
+    sf, cf = dev_zeros(nb, torch.float64), dev_zeros(nb, torch.int64)
+    sm, cm = dev_zeros(nlev * nb, torch.float64), dev_zeros(nlev * nb, torch.int64)
+    hf.hufield_ensemble(plan, gf, SEED, 0, nf, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, ws)
+    torch.cuda.synchronize()
+    assert hf.hufield_workspace_status(ws) == hf.OK
+    got = {"f": out_f, "maps": maps, "sums_f": np_(sf), "counts_f": np_(cf),
+           "sums_m": np_(sm).reshape(nlev, nb), "counts_m": np_(cm).reshape(nlev, nb)}
+    del ws
+    return got
+
+
+def _field_np(t):
+    return t.double().cpu().numpy()
+
+
+def test_4096_ensemble_two_lanes_against_oracle(hf):
+    shape, levels, nr, nt, nf = (4096, 4096), (0.0, 0.5, -0.5), 64, 36, 2
+    N = math.prod(shape)
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C1))
+    got = _run_ensemble(hf, shape, gf, levels, nr, nt, nf, lanes=2)
+    sums_f = np.zeros(nr * nt)
+    sums_m = np.zeros((len(levels), nr * nt))
+    counts_f = counts_m = None
+    flips = np.zeros(len(levels), dtype=np.int64)
+    for e in range(nf):  # field e ran on lane e & 1
+        want = oracle.pipeline(shape, of, SEED, e, levels=levels, nr=nr, ntheta=nt)
+        check_field(_field_np(got["f"][e]), want["f"])
+        flips += np.array(check_maps(np_(got["maps"][e]), want["maps"], want["f"], levels))
+        sums_f += want["sums_f"]
+        sums_m += want["sums_m"]
+        counts_f = want["counts_f"] * nf
+        counts_m = want["counts_m"] * nf
+        del want
+    check_bins(got["sums_f"], sums_f, got["counts_f"], counts_f)
+    for t in range(len(levels)):
+        check_bins(got["sums_m"][t], sums_m[t], got["counts_m"][t], counts_m[t], flips=int(flips[t]), N=N)
+
+
+def _volume_against_oracle(hf, n, bf16):
+    shape, levels, nr, nt = (n, n, n), (0.0,), 256, 1
+    N = math.prod(shape)
+    gf, of = filters(hf, **inputs.filter_kwargs(inputs.C2))
+    got = _run_ensemble(hf, shape, gf, levels, nr, nt, 1, lanes=1)
+    f32 = _field_np(got["f"][0])
+    maps = np_(got["maps"][0])
+    sums = (got["sums_f"], got["counts_f"], got["sums_m"], got["counts_m"])
+    del got
+    b16 = None
+    if bf16:
+        gb = _run_ensemble(hf, shape, gf, levels, nr, nt, 1, lanes=1, out_dtype=torch.bfloat16)
+        b16 = (_field_np(gb["f"][0]), np_(gb["maps"][0]))
+        del gb
+    torch.cuda.empty_cache()
+    want = oracle.pipeline(shape, of, SEED, 0, levels=levels, nr=nr, ntheta=nt)
+    r, m = check_field(f32, want["f"])
+    flips = check_maps(maps, want["maps"], want["f"], levels)
+    check_bins(sums[0], want["sums_f"], sums[1], want["counts_f"])
+    check_bins(sums[2][0], want["sums_m"][0], sums[3][0], want["counts_m"][0], flips=flips[0], N=N)
+    print(f"\n{n}^3 FP32 field against the oracle: relative L2 {r:.3e}, max |err| {m:.3e} rms, "
+          f"map sites differing {flips[0]}")
+    if b16 is not None:
+        fb, mb = b16
+        rms = math.sqrt(float(np.mean(want["f"] ** 2)))
+        rb = rel_l2(fb, want["f"])
+        mx = float(np.abs(fb - want["f"]).max()) / rms
+        # BF16 keeps 8 significant bits: rounding to nearest leaves each value within
+        # 2^-9 of itself relative, so a Gaussian field's relative L2 is about
+        # 2^-9 / sqrt(3) ~ 1.1e-3 to 1.6e-3 (the binade's spacing varies across it)
+        assert 1.0e-3 < rb < 2.0e-3, rb
+        rel_site = np.abs(fb - want["f"]) / np.maximum(np.abs(want["f"]), 1e-30)
+        assert float(rel_site.max()) <= 2.0 ** -8 + 1e-6
+        # the maps are thresholded from the FP32 field before the BF16 rounding
+        fl = check_maps(mb, want["maps"], want["f"], levels)
+        print(f"{n}^3 BF16 field against the oracle: relative L2 {rb:.3e}, max |err| {mx:.3e} rms, "
+              f"largest relative error per site {float(rel_site.max()):.3e}, map sites differing {fl[0]}")
+
+
+def test_512_volume_and_bf16_against_oracle(hf):
+    _volume_against_oracle(hf, 512, bf16=True)
+
+
+def test_1024_volume_against_oracle(hf):
+    need = 72.0
+    have = _mem_available_gb()
+    if have < need:
+        pytest.skip(f"the FP64 oracle at 1024^3 needs about {need:.0f} GB of host memory; {have:.0f} GB available")
+    if os.environ.get("HUFIELD_SKIP_1024_ORACLE"):
+        pytest.skip("HUFIELD_SKIP_1024_ORACLE is set")
+    _volume_against_oracle(hf, 1024, bf16=False)

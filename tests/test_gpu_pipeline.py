@@ -157,6 +157,30 @@ def test_narrow_band_parity(hf, name, shape, fk, nr, nt, noise):
     assert err < 2.5e-3, err
 
 
+# Corners of the ragged workload's parameter ranges (p in [1, 8], semi-axes in
+# [0.5, 2], k0 in [0.05, 0.4], width down to 0.01, s up to 6, levels in [-1, 1]):
+# the narrowest bands stretch the filter's rounding the most (a relative error
+# of K grows by about 2 |K - k0| K / (w^2 ln 4) in log2 A).
+CORNER_CASES = [
+    ("2d-1024-p8-far", (1024, 1024), dict(p=8.0, axes=(2.0, 0.5), rot=2.0, k0=0.4, width=0.01, supp=6.0), 0.7, 128),
+    ("2d-1024-p1-near", (1024, 1024), dict(p=1.0, axes=(0.5, 2.0), rot=0.3, k0=0.05, width=0.01, supp=2.0), -1.0,
+     128),
+    ("3d-256-p8-far", (256, 256, 256), dict(p=8.0, axes=(1.0, 2.0, 0.5), rot=1.0, k0=0.4, width=0.01, supp=6.0), 0.0,
+     128),
+    ("3d-256-p1-near", (256, 256, 256), dict(p=1.0, axes=(1.0, 0.5, 2.0), rot=3.0, k0=0.05, width=0.01, supp=4.0),
+     -0.5, 128),
+]
+
+
+@pytest.mark.parametrize("name,shape,fk,level,nr", CORNER_CASES, ids=[c[0] for c in CORNER_CASES])
+def test_parameter_range_corners(hf, name, shape, fk, level, nr):
+    gf, of = filters(hf, **fk)
+    plan = hf.Plan(shape)
+    got = run_pipeline(hf, plan, gf, shape, 8, 1, (level,), nr, 1)
+    want = oracle.pipeline(shape, of, 8, 1, levels=(level,), nr=nr, ntheta=1)
+    compare(got, want, (level,), int(np.prod(shape)))
+
+
 def test_pipeline_no_levels(hf):
     shape = (64, 64)
     gf, of = filters(hf, **inputs.filter_kwargs(inputs.C0))
