@@ -34,3 +34,39 @@ def random_filter(ndim, seed):
     return dict(p=float(r.uniform(1.0, 8.0)), axes=axes, rot=float(r.uniform(0.0, math.pi)),
                 k0=float(r.uniform(0.05, 0.4)), width=float(r.uniform(0.01, 0.1)),
                 supp=float(r.choice([2.0, 4.0, 6.0])))
+
+
+def mlp_params(seed, widths=(8, 256, 256, 256, 128), in_pad=32):
+    """Seeded parameters of the surrogate network (flat, layer by layer W then b):
+    W uniform within +-1.5/sqrt(fan_in) (padding columns 0), b uniform within +-0.2."""
+    r = np.random.default_rng(seed)
+    out = []
+    for l in range(len(widths) - 1):
+        n_out, fan = widths[l + 1], widths[l]
+        n_in = max(in_pad, fan) if l == 0 else fan
+        W = np.zeros((n_out, n_in))
+        W[:, :fan] = r.uniform(-1.5, 1.5, (n_out, fan)) / math.sqrt(fan)
+        out += [W.reshape(-1), r.uniform(-0.2, 0.2, n_out)]
+    return np.concatenate(out).astype(np.float32)
+
+
+def mlp_rows(rows, seed, width=8):
+    """Seeded network inputs on [-1, 1]."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, (rows, width)).astype(np.float32)
+
+
+def surrogate_thetas(rows, seed):
+    """Seeded raw parameters over the surrogate's ranges: p in [1, 8], semi-axis ratios in
+    [0.5, 2], rotation in [0, pi), k0 in [0.05, 0.4], width in [0.01, 0.1], s in {2, 4, 6},
+    level in [-1, 1] (the ragged workload's draws)."""
+    r = np.random.default_rng(seed)
+    t = np.empty((rows, 8))
+    t[:, 0] = r.uniform(1.0, 8.0, rows)
+    t[:, 1] = r.uniform(0.5, 2.0, rows)
+    t[:, 2] = r.uniform(0.5, 2.0, rows)
+    t[:, 3] = r.uniform(0.0, math.pi, rows)
+    t[:, 4] = r.uniform(0.05, 0.4, rows)
+    t[:, 5] = r.uniform(0.01, 0.1, rows)
+    t[:, 6] = r.choice([2.0, 4.0, 6.0], rows)
+    t[:, 7] = r.uniform(-1.0, 1.0, rows)
+    return t.astype(np.float32)
