@@ -9,15 +9,20 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared():
-    src = open(os.path.join(ROOT, "include", "hufield.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hufield_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(hufield_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared()
     for must in ("hufield_generate", "hufield_threshold", "hufield_spectrum", "hufield_pipeline",
-                 "hufield_plan_create", "hufield_workspace_bytes"):
+                 "hufield_plan_create", "hufield_workspace_bytes", "hufield_mlp_forward", "hufield_mlp_backward",
+                 "hufield_mlp_adam"):
         assert must in names
 
 
