@@ -223,10 +223,36 @@ def run_reference(args, wl, name):
     print(json.dumps(line), flush=True)
 
 
-def ragged_items(hf, count, seed=0):
-    """The ragged workload: a host Philox stream (numpy) draws each field's lattice
-    uniformly from the nine sizes and its filter: p in [1, 8], semi-axes (r1, r2) in
-    2D and (1, r1, r2) in 3D with r in [0.5, 2], rotation in [0, pi), k0 in
+def run_ragged_reference(args):
+    """The oracle on the ragged workload: each step a bounded sample of the batch's
+    items (consecutive items, about 20 s of host time)."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle
+
+    items = ragged_items(oracle, RAGGED["count"])
+    vox, sec, cnt, nxt = 0, 0.0, 0, 0
+    for i in range(args.warmup + args.steps):
+        v, s_, c, x = ragged_oracle_sample(items, nxt, 20.0)
+        nxt += c
+        if i >= args.warmup:
+            vox, sec, cnt = vox + x, sec + s_, cnt + c
+    value = vox / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ragged-2000", "step_sample": f"about 20 s of consecutive items ({cnt} timed)"},
+            "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": _oracle_threads(), "kind": "oracle",
+                             "sample": f"{cnt} consecutive items of the 2000-item batch"},
+            "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ragged_items(mod, count, seed=0):
+    """The ragged workload, filters as mod.Filter (the binding's or the oracle's):
+    a host Philox stream (numpy) draws each field's lattice uniformly from the
+    nine sizes and its filter: p in [1, 8], semi-axes (r1, r2) in 2D and
+    (1, r1, r2) in 3D with r in [0.5, 2], rotation in [0, pi), k0 in
     [0.05, 0.4], width in [0.01, 0.1], s in {2, 4, 6}; level t in [-1, 1];
     nr = min(128, n / 2) radial bins."""
     import numpy as np
@@ -237,7 +263,7 @@ def ragged_items(hf, count, seed=0):
         shape = RAGGED["sizes"][int(rng.integers(len(RAGGED["sizes"])))]
         r1, r2 = float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.5, 2.0))
         axes = (r1, r2) if len(shape) == 2 else (1.0, r1, r2)
-        filt = hf.Filter(p=float(rng.uniform(1.0, 8.0)), axes=axes, rot=float(rng.uniform(0.0, math.pi)),
+        filt = mod.Filter(p=float(rng.uniform(1.0, 8.0)), axes=axes, rot=float(rng.uniform(0.0, math.pi)),
                          k0=float(rng.uniform(0.05, 0.4)), width=float(rng.uniform(0.01, 0.1)),
                          supp=float(rng.choice([2.0, 4.0, 6.0])))
         items.append((shape, filt, seed, i, float(rng.uniform(-1.0, 1.0)), min(128, shape[0] // 2)))
@@ -300,6 +326,157 @@ def run_ragged(args):
             "pipeline": {"bytes_per_voxel": round(nbytes / voxels, 2), "GBps": round(gbs, 1),
                          "frac": round(gbs / peak, 4)},
             "gpu_launches": args.steps * (4 * n2 + 7 * n3), "clocks": clk, "e2e": None, "cpu_baseline": None}
+    if not args.no_e2e:
+        line["e2e"] = ragged_e2e(hf, torch, batch, out_f, maps, (sf, cf, sm, cm), ws, stream, args)
+    if not args.no_cpu_baseline:
+        v, sec, cnt, vox = ragged_oracle_sample(items, 0, 15.0)
+        line["cpu_baseline"] = {"value": v, "unit": "voxels/s", "cores": _oracle_threads(), "kind": "oracle",
+                                "sample": f"the batch's first {cnt} items ({vox} voxels, {sec:.1f} s), full FP64 "
+                                          f"pipeline with each item's filter, level and bins"}
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_threads():
+    import oracle
+
+    return oracle.num_threads()
+
+
+def ragged_oracle_sample(items, start, seconds):
+    """The FP64 oracle on consecutive items of the ragged batch from `start` until
+    `seconds` of host time have passed (at least one item): voxels/s, time, items,
+    voxels."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    vox, cnt, i = 0, 0, start
+    while cnt == 0 or time.perf_counter() - t0 < seconds:
+        shape, f, seed, idx, level, nr = items[i % len(items)]
+        of = oracle.Filter(p=f.p, axes=f.axes, rot=f.rot, k0=f.k0, width=f.width, supp=f.supp)
+        oracle.pipeline(shape, of, seed, idx, levels=(level,), nr=nr, ntheta=1)
+        vox += math.prod(shape)
+        cnt += 1
+        i += 1
+    sec = time.perf_counter() - t0
+    return vox / sec, sec, cnt, vox
+
+
+def ragged_e2e(hf, torch, batch, out_f, maps, bins, ws, stream, args):
+    """The batch through its public call with every output (fields, maps, bins)
+    copied to pinned host memory inside the timed region, median of the steps."""
+    try:
+        host_f = torch.empty(out_f.shape, dtype=out_f.dtype, pin_memory=True)
+        host_m = torch.empty(maps.shape, dtype=maps.dtype, pin_memory=True)
+        host_b = [torch.empty(b.shape, dtype=b.dtype, pin_memory=True) for b in bins]
+    except RuntimeError:
+        return None
+    times = []
+    for i in range(max(3, min(args.steps, 5)) + 1):
+        t0 = time.perf_counter()
+        hf.hufield_batch_run(batch, out_f, maps, *bins, ws, stream=stream)
+        host_f.copy_(out_f, non_blocking=True)
+        host_m.copy_(maps, non_blocking=True)
+        for h, d in zip(host_b, bins):
+            h.copy_(d, non_blocking=True)
+        stream.synchronize()
+        if i > 0:  # the first one warms the pinned pages
+            times.append(time.perf_counter() - t0)
+    dt = sorted(times)[len(times) // 2]
+    d2h = out_f.numel() * out_f.element_size() + maps.numel() + sum(b.numel() * b.element_size() for b in bins)
+    return {"value": batch.total_voxels / dt, "unit": "voxels/s", "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": int(d2h), "steps": len(times), "step_ms_median": round(1e3 * dt, 3),
+            "note": "inputs are seeds and filter parameters set at plan time; every output copied to pinned host"}
+
+
+SURROGATE = dict(fields=200000, train_frac=0.9, steps=20000, batch=1024, designs=500, starts=4, iters=300,
+                 plain_sample=10, plain_budget=300, plain_seeds=16)
+
+
+def run_surrogate(args):
+    """The surrogate workload (2D 256^2, 128 radial bins of the map's S(k)): data
+    from the plain generator, training, 500 inverse designs each confirmed by the
+    plain generator (64-field mean within 5% relative L2 of the target), and the
+    plain generator's own search (Nelder-Mead, 16 fields per evaluation) on a
+    sample of the same targets.  One JSON line: the ratio of GPU-seconds per
+    confirmed design, with and without the amortised data and training."""
+    import numpy as np
+    import torch
+
+    from paper_2509_08675_gb300 import builder
+
+    builder.build()
+    from paper_2509_08675_gb300 import surrogate as sg
+
+    torch.cuda.set_device(0)
+    cfg = dict(SURROGATE)
+    if args.fields > 0:
+        cfg["fields"] = args.fields
+    n = cfg["fields"]
+    ntr = int(cfg["train_frac"] * n)
+    clocks = ClockSampler()
+    clocks.start()
+    th = sg.draw_thetas(n, 100)
+    data = sg.generate_dataset(th, seed=7)
+    model = sg.Surrogate(seed=3)
+    model.fit_stats(data, ntr)
+    log = model.train(data, ntr, cfg["steps"], batch=cfg["batch"], log_every=cfg["steps"] // 10)
+    # held-out accuracy: predictions against the 64-field means of 200 held-out parameter sets
+    hold = th[ntr:ntr + 200]
+    Sh = sg.plain_spectra(hold, seed=99, nseeds=64).cpu().numpy()
+    ph = model.predict(data.x[ntr:ntr + 200]).cpu().numpy()
+    eh = sg.rel_err(ph, Sh)
+    # targets: 64-field means at held-out random parameters (cost counted for neither method)
+    tt = sg.draw_thetas(cfg["designs"], 555)
+    T = sg.plain_spectra(tt, seed=11, nseeds=64)
+    Tn = T.cpu().numpy()
+    best, L, design_s, allth, order = model.design(T, starts=cfg["starts"], iters=cfg["iters"])
+    with sg.Timer() as tv:
+        V = sg.plain_spectra(best, seed=12, nseeds=64).cpu().numpy()
+    err = sg.rel_err(V, Tn)
+    # a design that fails falls back to the next start by the surrogate's loss (verified the same way)
+    retry = np.where(err > sg.CONFIRM)[0]
+    with sg.Timer() as tr:
+        if len(retry):
+            alt = allth[retry, order[retry, 1]]
+            Va = sg.plain_spectra(alt, seed=12, nseeds=64).cpu().numpy()
+            ea = sg.rel_err(Va, Tn[retry])
+            better = ea < err[retry]
+            err[retry[better]] = ea[better]
+    verify_s = (tv.ms + tr.ms) / 1e3
+    confirmed = int((err <= sg.CONFIRM).sum())
+    # the plain generator's own search on a sample of the targets
+    ps = []
+    for i in range(cfg["plain_sample"]):
+        with sg.Timer() as tp:
+            thp, ep, nev = sg.nelder_mead_search(Tn[i], seed=13, nseeds=cfg["plain_seeds"],
+                                                 budget=cfg["plain_budget"], rng_seed=i)
+        Vp = sg.plain_spectra(thp[None, :].astype(np.float32), seed=12, nseeds=64).cpu().numpy()
+        ps.append((nev, tp.ms / 1e3, float(sg.rel_err(Vp, Tn[i:i + 1])[0])))
+    clk = clocks.stop(None)
+    plain_s = float(np.mean([p[1] for p in ps]))
+    plain_ok = sum(1 for p in ps if p[2] <= sg.CONFIRM)
+    plain_per_confirmed = sum(p[1] for p in ps) / max(plain_ok, 1)
+    sur_marginal = (design_s + verify_s) / max(confirmed, 1)
+    sur_total = (data.gpu_s + log.gpu_s + design_s + verify_s) / max(confirmed, 1)
+    line = {"metric": "GPU-seconds per confirmed design: plain-generator search / surrogate (5% rel. L2 of S(k))",
+            "value": plain_per_confirmed / sur_total, "unit": "x fewer GPU-seconds (amortised)", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 weights, f32 accumulation; f32 generator", "data": "synthetic",
+            "config": {"workload": "surrogate-256", "shape": [256, 256], "bins": 128, **cfg},
+            "surrogate": {
+                "designs": cfg["designs"], "confirmed": confirmed, "confirmed_frac": confirmed / cfg["designs"],
+                "err_median": float(np.median(err)), "err_p90": float(np.percentile(err, 90)),
+                "heldout_pred_err_median": float(np.median(eh)), "heldout_pred_err_p90": float(np.percentile(eh, 90)),
+                "gpu_s": {"data": round(data.gpu_s, 3), "train": round(log.gpu_s, 3), "design": round(design_s, 3),
+                          "verify": round(verify_s, 3)},
+                "train_losses": [round(x, 5) for x in log.losses],
+                "gpu_s_per_confirmed_design": {"amortised": sur_total, "marginal": sur_marginal}},
+            "plain_search": {"targets": len(ps), "confirmed": plain_ok, "evaluations_mean": float(np.mean([p[0] for p in ps])),
+                             "gpu_s_mean": plain_s, "gpu_s_per_confirmed_design": plain_per_confirmed,
+                             "errors": [round(p[2], 4) for p in ps]},
+            "ratio_marginal": plain_per_confirmed / sur_marginal,
+            "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -308,7 +485,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="ensemble-2d-4096", choices=sorted(WORKLOADS) + ["ragged-2000"])
+    ap.add_argument("--workload", default="ensemble-2d-4096",
+                    choices=sorted(WORKLOADS) + ["ragged-2000", "surrogate-256"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -319,11 +497,15 @@ def main():
     ap.add_argument("--noise", default="real", choices=["real", "kspace"],
                     help="white noise in real space (forward FFT) or drawn as k-space coefficients")
     args = ap.parse_args()
+    if args.workload == "surrogate-256":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the surrogate workload compares two GPU "
+                              "methods; its plain-search leg is the baseline"}))
+            return
+        return run_surrogate(args)
     if args.workload == "ragged-2000":
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the ragged batch has no oracle leg; "
-                              "use the per-workload reference arm"}))
-            return
+            return run_ragged_reference(args)
         return run_ragged(args)
     wl = dict(WORKLOADS[args.workload])
     if args.fields > 0:

@@ -135,9 +135,10 @@ int hufield_plan_destroy(hufield_plan *plan);
  * call it outside stream capture. */
 int hufield_plan_set_bins(hufield_plan *plan, int32_t nr, int32_t ntheta);
 
-/* Autotuning of the plan's launch choices for the strided passes: resident
- * CTAs per SM of each pass mode (plain, filter, bins, k-space) and the L2
- * promotion of their tensor maps.  Times hufield_pipeline with filter f, nlev
+/* Autotuning of the plan's launch choices for the strided passes: their tile
+ * width (hufield_plan_set_tile), resident CTAs per SM of each pass mode
+ * (plain, filter, bins, k-space) and the L2 promotion of their tensor maps.
+ * Times hufield_pipeline with filter f, nlev
  * levels and nr x ntheta bins on scratch it allocates and frees (best of
  * three calls per candidate, coordinate descent, a change kept only when 2%
  * faster), and keeps the fastest choice in the plan; results are the same
@@ -155,6 +156,17 @@ int hufield_plan_autotune(hufield_plan *plan, const hufield_filter *f, int32_t n
  * bins and k-space strided passes, out[4] the L2 promotion in bytes (0: 64 or
  * 128 by the tile's row width). */
 int hufield_plan_tuning(const hufield_plan *plan, int32_t out[5]);
+
+/* Tile width of the strided passes along axes of 256 or more: 0 by size (the
+ * wide tile of 8192 / L or 4096 / L columns, except the two-column tile for
+ * columns of 1024 or more whose wide tiles would leave SMs idle), 1 the wide
+ * tile wherever the columns fill it, 2 the two-column tile.  Every choice
+ * computes the same results up to the order of the bin sums.  A cached bin
+ * table (hufield_plan_set_bins), which is laid out in the axis-0 tiles, is
+ * rebuilt when the width of those tiles changes (synchronising the device, as
+ * hufield_plan_set_bins does).  hufield_plan_tile reads the choice. */
+int hufield_plan_set_tile(hufield_plan *plan, int32_t tile);
+int hufield_plan_tile(const hufield_plan *plan, int32_t *tile);
 
 /* Bytes of device workspace a call needs: nlev sign maps (0 for
  * hufield_generate, 1 for hufield_spectrum) and nbins = nr * ntheta bins
@@ -276,9 +288,14 @@ typedef struct hufield_batch hufield_batch;
  * the class's first item: its filter, one level and its radial bins). */
 #define HUFIELD_BATCH_AUTOTUNE 1u
 
+/* Lanes per size class: HUFIELD_BATCH_LANES(l), 1 <= l <= 8, in the flags
+ * (default 2).  Each lane is a stream and a workspace slice; more lanes let
+ * many small fields, whose passes each fill only a few SMs, run side by side. */
+#define HUFIELD_BATCH_LANES(l) (((uint32_t)(l) & 15u) << 8)
+
 /* Plan a batch of n >= 1 items on the current device (copies the items;
- * flags 0 or HUFIELD_BATCH_AUTOTUNE).  Allocates the size-class plans and
- * streams. */
+ * flags: HUFIELD_BATCH_AUTOTUNE and/or HUFIELD_BATCH_LANES(l)).  Allocates the
+ * size-class plans and streams. */
 int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, int32_t n, uint32_t flags);
 
 /* Output layout (host arrays of n entries, either may be NULL): item i's

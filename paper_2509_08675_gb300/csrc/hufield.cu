@@ -229,6 +229,10 @@ struct hufield_plan {
     // 128 or 256 bytes)
     int col_cap[4] = {kColCapDefault, kColCapDefault, kColCapDefault + 1, kColCapDefault};
     int l2_promo = 0;
+    // tile width of the strided passes of 256 or more rows: 0 by size (col_big),
+    // 1 the wide tile wherever the columns fill it, 2 the two-column tile
+    int col_tile = 0;
+    int cache_logtb = -1;  // axis-0 tile width the cached bin table was built for
     // second lane of ensembles (odd fields) and its fork/join events
     cudaStream_t lane = nullptr;
     cudaEvent_t lane_fork = nullptr, lane_join = nullptr;
@@ -306,6 +310,8 @@ KernelInfo pick_row(int log2m, long long nrows, KernelInfo (*table)(int, bool, i
 bool col_big(const hufield_plan* p, int log2l, long long B, long long a_spec) {
     const int lt = col_logtb(log2l, true);
     if (B < (1ll << lt)) return false;
+    if (log2l >= 8 && p->col_tile == 1) return true;
+    if (log2l >= 8 && p->col_tile == 2) return false;
     return log2l < 10 || a_spec * (B >> lt) >= p->nsm;
 }
 
@@ -677,7 +683,7 @@ int build_bin_table(hufield_plan* p, const BinParams& bp, unsigned short* tab, l
 // counts to each of ndst arrays; returns the table to read in `tab`.
 int bins_for_call(hufield_plan* p, const BinParams& bp, unsigned short* ws_tab, long long mult, int ndst,
                   long long** dst, const unsigned short** tab, cudaStream_t s) {
-    if (p->cache_tab && p->cache_nr == bp.nr && p->cache_nt == bp.ntheta) {
+    if (p->cache_tab && p->cache_nr == bp.nr && p->cache_nt == bp.ntheta && p->cache_logtb == axis0_logtb(p)) {
         AddCountsArgs ac{};
         ac.counts = p->cache_counts;
         ac.nbins = bp.nbins;
@@ -910,7 +916,7 @@ std::string tune_key(const hufield_plan* p, int nlev, int nbins) {
 }
 
 // Cache file (HUFIELD_AUTOTUNE_CACHE): one line per tuning, "key<TAB>c0 c1 c2 c3 promo".
-bool tune_lookup(const char* path, const std::string& key, int cap[4], int& promo) {
+bool tune_lookup(const char* path, const std::string& key, int cap[4], int& promo, int& tile) {
     FILE* fp = fopen(path, "r");
     if (!fp) return false;
     char line[512];
@@ -919,10 +925,12 @@ bool tune_lookup(const char* path, const std::string& key, int cap[4], int& prom
         char* tab = strchr(line, '\t');
         if (!tab) continue;
         *tab = 0;
-        int c[4], pr;
-        if (key == line && sscanf(tab + 1, "%d %d %d %d %d", &c[0], &c[1], &c[2], &c[3], &pr) == 5) {
+        int c[4], pr, tl = 0;
+        const int got = key == line ? sscanf(tab + 1, "%d %d %d %d %d %d", &c[0], &c[1], &c[2], &c[3], &pr, &tl) : 0;
+        if (got == 5 || got == 6) {  // lines written before the tile width was tuned have five fields
             for (int i = 0; i < 4; ++i) cap[i] = c[i];
             promo = pr;
+            tile = got == 6 ? tl : 0;
             found = true;  // the last entry for a key wins
         }
     }
@@ -930,11 +938,19 @@ bool tune_lookup(const char* path, const std::string& key, int cap[4], int& prom
     return found;
 }
 
-void tune_store(const char* path, const std::string& key, const int cap[4], int promo) {
+void tune_store(const char* path, const std::string& key, const int cap[4], int promo, int tile) {
     FILE* fp = fopen(path, "a");
     if (!fp) return;
-    fprintf(fp, "%s\t%d %d %d %d %d\n", key.c_str(), cap[0], cap[1], cap[2], cap[3], promo);
+    fprintf(fp, "%s\t%d %d %d %d %d %d\n", key.c_str(), cap[0], cap[1], cap[2], cap[3], promo, tile);
     fclose(fp);
+}
+
+// Sets the strided passes' tile width; a cached bin table laid out for
+// another axis-0 tile width is rebuilt.
+int set_tile(hufield_plan* p, int tile) {
+    p->col_tile = tile;
+    if (p->cache_tab && p->cache_logtb != axis0_logtb(p)) return hufield_plan_set_bins(p, p->cache_nr, p->cache_nt);
+    return HUFIELD_OK;
 }
 
 }  // namespace
@@ -951,14 +967,14 @@ int hufield_plan_autotune(hufield_plan* p, const hufield_filter* f, int32_t nlev
     if (rc) return rc;
     const std::string key = tune_key(p, nlev, bp.nbins);
     const char* cache = getenv("HUFIELD_AUTOTUNE_CACHE");
-    int cap[4], promo = 0;
-    if (cache && *cache && tune_lookup(cache, key, cap, promo)) {
-        bool ok = promo == 0 || promo == 64 || promo == 128 || promo == 256;
+    int cap[4], promo = 0, tile = 0;
+    if (cache && *cache && tune_lookup(cache, key, cap, promo, tile)) {
+        bool ok = (promo == 0 || promo == 64 || promo == 128 || promo == 256) && tile >= 0 && tile <= 2;
         for (int i = 0; i < 4; ++i) ok = ok && cap[i] >= 1 && cap[i] <= 8;
         if (ok) {
             for (int i = 0; i < 4; ++i) p->col_cap[i] = cap[i];
             p->l2_promo = promo;
-            return HUFIELD_OK;
+            return set_tile(p, tile);
         }
     }
     // scratch for one pipeline call (freed below)
@@ -1016,10 +1032,14 @@ int hufield_plan_autotune(hufield_plan* p, const hufield_filter* f, int32_t nlev
         std::vector<int> values;
     };
     std::vector<Knob> knobs;
+    // the tile width first: the CTA caps below are tuned for the width kept
+    knobs.push_back({&p->col_tile, {0, 1, 2}});
     if (p->ndim == 3) knobs.push_back({&p->col_cap[kModePlain], {1, 2, 3}});
     knobs.push_back({&p->col_cap[p->kspace ? kModeKspace : kModeFilter], {1, 2, 3}});
     if (nlev > 0) knobs.push_back({&p->col_cap[kModeBins], {2, 3, 4}});
     knobs.push_back({&p->l2_promo, {0, 64, 128, 256}});
+    // the timed calls build their bin table in the workspace while the tile
+    // width differs from the cached table's (bins_for_call)
     for (auto& kb : knobs) {
         if (rc) break;
         const int keep = *kb.slot;
@@ -1045,9 +1065,21 @@ int hufield_plan_autotune(hufield_plan* p, const hufield_filter* f, int32_t nlev
         // back to the defaults: a failed tuning leaves the plan as created
         for (int i = 0; i < 4; ++i) p->col_cap[i] = i == kModeBins ? kColCapDefault + 1 : kColCapDefault;
         p->l2_promo = 0;
+        set_tile(p, 0);
         return rc;
     }
-    if (cache && *cache) tune_store(cache, key, p->col_cap, p->l2_promo);
+    if (cache && *cache) tune_store(cache, key, p->col_cap, p->l2_promo, p->col_tile);
+    return set_tile(p, p->col_tile);
+}
+
+int hufield_plan_set_tile(hufield_plan* p, int32_t tile) {
+    if (!p || tile < 0 || tile > 2) return HUFIELD_ERR_INVALID_ARG;
+    return set_tile(p, tile);
+}
+
+int hufield_plan_tile(const hufield_plan* p, int32_t* tile) {
+    if (!p || !tile) return HUFIELD_ERR_INVALID_ARG;
+    *tile = p->col_tile;
     return HUFIELD_OK;
 }
 
@@ -1084,6 +1116,7 @@ int hufield_plan_set_bins(hufield_plan* p, int32_t nr, int32_t ntheta) {
     if (rc == HUFIELD_OK) {
         p->cache_nr = nr;
         p->cache_nt = ntheta;
+        p->cache_logtb = axis0_logtb(p);
     }
     return rc;
 }
@@ -1596,19 +1629,22 @@ extern "C" int hufield_spectrum_noalloc_status(void* stream) {
 
 // ---------------------------------------------------------------------------
 // Ragged batches (hufield_batch_*): one plan per size class, and per class
-// up to kBatchLanes lanes (a stream and a workspace slice each) that take its
+// up to `lanes` lanes (a stream and a workspace slice each) that take its
 // items in turn; the whole batch is captured into one CUDA graph (every lane
 // a parallel branch, the items of a lane in sequence) and replayed.  Two
-// lanes let one item's passes fill the tail and launch gaps of the other's.
+// lanes (the default) let one item's passes fill the tail and launch gaps of
+// the other's; many small lattices, whose passes each fill a few SMs, gain
+// from more.
 // ---------------------------------------------------------------------------
 constexpr int kBatchLanes = 2;
+constexpr int kMaxBatchLanes = 8;
 
 struct hufield_batch {
     struct Class {
         hufield_plan* plan = nullptr;
         int lanes = 1;
-        cudaStream_t stream[kBatchLanes] = {};
-        cudaEvent_t join[kBatchLanes] = {};
+        cudaStream_t stream[kMaxBatchLanes] = {};
+        cudaEvent_t join[kMaxBatchLanes] = {};
         std::vector<int> members;
         size_t ws_off = 0, ws_bytes = 0;  // lane l's slice starts at ws_off + l * align256(ws_bytes)
     };
@@ -1631,7 +1667,7 @@ void batch_free(hufield_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto& c : b->classes) {
         if (c.plan) hufield_plan_destroy(c.plan);
-        for (int l = 0; l < kBatchLanes; ++l) {
+        for (int l = 0; l < kMaxBatchLanes; ++l) {
             if (c.stream[l]) cudaStreamDestroy(c.stream[l]);
             if (c.join[l]) cudaEventDestroy(c.join[l]);
         }
@@ -1653,7 +1689,11 @@ bool same_dims(const hufield_dims& a, const hufield_dims& b) {
 extern "C" {
 
 int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int32_t n, uint32_t flags) {
-    if (!out || !items || n < 1 || (flags & ~HUFIELD_BATCH_AUTOTUNE) != 0) return HUFIELD_ERR_INVALID_ARG;
+    const int want_lanes = (int)((flags >> 8) & 15u);
+    if (!out || !items || n < 1 || (flags & ~(HUFIELD_BATCH_AUTOTUNE | (15u << 8))) != 0 ||
+        want_lanes > kMaxBatchLanes)
+        return HUFIELD_ERR_INVALID_ARG;
+    const int max_lanes = want_lanes > 0 ? want_lanes : kBatchLanes;
     *out = nullptr;
     hufield_batch* b = new (std::nothrow) hufield_batch();
     if (!b) return HUFIELD_ERR_CUDA;
@@ -1706,7 +1746,7 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
     }
     for (size_t c = 0; c < b->classes.size(); ++c) {
         auto& C = b->classes[c];
-        C.lanes = (int)C.members.size() < kBatchLanes ? (int)C.members.size() : kBatchLanes;
+        C.lanes = (int)C.members.size() < max_lanes ? (int)C.members.size() : max_lanes;
         C.ws_off = b->ws_total;
         b->ws_total += (size_t)C.lanes * align256(C.ws_bytes);
         if (uniform[c] && hufield_plan_set_bins(C.plan, class_nr[c], 1) != HUFIELD_OK) rc = HUFIELD_ERR_CUDA;

@@ -98,6 +98,8 @@ def _load():
     lib.hufield_filter_band_edge.argtypes = [vp, fptr, C.POINTER(C.c_int64)]
     lib.hufield_plan_autotune.argtypes = [vp, fptr, i32, i32, i32]
     lib.hufield_plan_tuning.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.hufield_plan_set_tile.argtypes = [vp, i32]
+    lib.hufield_plan_tile.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_window_variance_filter.argtypes = [vp, fptr, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
@@ -277,6 +279,17 @@ def hufield_plan_autotune(plan: Plan, filt: Filter, nlev: int, nr: int, ntheta: 
     _check(_lib.hufield_plan_autotune(plan.handle, C.byref(fc), nlev, nr, ntheta), "hufield_plan_autotune")
 
 
+def hufield_plan_set_tile(plan: Plan, tile: int) -> None:
+    """Tile width of the strided passes: 0 by size, 1 wide, 2 two-column (see include/hufield.h)."""
+    _check(_lib.hufield_plan_set_tile(plan.handle, int(tile)), "hufield_plan_set_tile")
+
+
+def hufield_plan_tile(plan: Plan) -> int:
+    v = C.c_int32()
+    _check(_lib.hufield_plan_tile(plan.handle, C.byref(v)), "hufield_plan_tile")
+    return int(v.value)
+
+
 def hufield_plan_tuning(plan: Plan) -> dict:
     """The plan's launch choices: CTAs per SM per strided-pass mode and the L2 promotion."""
     out = (C.c_int32 * 5)()
@@ -369,9 +382,10 @@ class Batch:
     """hufield_batch: a ragged batch of fields run as one CUDA graph launch.
 
     items: sequence of (shape, Filter, seed, field_idx, level, nr); autotune = True
-    tunes every size class's plan (HUFIELD_BATCH_AUTOTUNE)."""
+    tunes every size class's plan (HUFIELD_BATCH_AUTOTUNE); lanes (1..8, 0 = the
+    default of two) sets the lanes per size class (HUFIELD_BATCH_LANES)."""
 
-    def __init__(self, items, autotune: bool = False):
+    def __init__(self, items, autotune: bool = False, lanes: int = 0):
         arr = (_BatchItem * len(items))()
         for i, (shape, filt, seed, field_idx, level, nr) in enumerate(items):
             shape = tuple(int(v) for v in shape)
@@ -382,7 +396,8 @@ class Batch:
             arr[i].level = level
             arr[i].nr = nr
         h = C.c_void_p()
-        _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), 1 if autotune else 0), "hufield_batch_plan")
+        flags = (1 if autotune else 0) | ((int(lanes) & 15) << 8)
+        _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), flags), "hufield_batch_plan")
         self._h = h
         self.n = len(items)
         f_off = (C.c_int64 * self.n)()

@@ -25,6 +25,7 @@ def test_autotuned_plan_keeps_parity(hf, shape, cfg, levels, nr, nt):
     got_t = hf.hufield_plan_tuning(plan)
     assert got_t["cta_cap"]["plain"] in (1, 2, 3) and got_t["cta_cap"]["filter"] in (1, 2, 3)
     assert got_t["cta_cap"]["bins"] in (2, 3, 4) and got_t["l2_promotion"] in (0, 64, 128, 256)
+    assert hf.hufield_plan_tile(plan) in (0, 1, 2)
     got = run_pipeline(hf, plan, gf, shape, 2, 0, levels, nr, nt)
     compare(got, oracle.pipeline(shape, of, 2, 0, levels=levels, nr=nr, ntheta=nt), levels, int(np.prod(shape)))
 
@@ -40,11 +41,13 @@ def test_autotune_cache_round_trip(hf, tmp_path, monkeypatch):
     assert len(lines) == 1 and "32x32x32 nlev=1 nbins=16" in lines[0]
     # a hand-edited entry for the same key wins (the last one for a key is used)
     key = lines[0].split("\t")[0]
-    cache.write_text(cache.read_text() + f"{key}\t1 1 4 1 256\n")
+    assert len(lines[0].split("\t")[1].split()) == 6  # caps, promotion, tile width
+    cache.write_text(cache.read_text() + f"{key}\t1 1 4 1 256\n")  # five fields: an older line, tile 0
     b = hf.Plan(shape)
     hf.hufield_plan_autotune(b, gf, 1, 16, 1)
     assert hf.hufield_plan_tuning(b) == {"cta_cap": {"plain": 1, "filter": 1, "bins": 4, "kspace": 1},
                                          "l2_promotion": 256}
+    assert hf.hufield_plan_tile(b) == 0
     assert len(cache.read_text().splitlines()) == 2  # reused, not timed and appended again
 
 
@@ -56,3 +59,30 @@ def test_autotune_rejects_bad_arguments(hf):
             hf.hufield_plan_autotune(plan, gf, nlev, nr, nt)
         assert e.value.status == hf.ERR_INVALID_ARG
     assert hf.hufield_plan_tuning(plan)["l2_promotion"] == 0
+
+
+@pytest.mark.parametrize("shape,cfg,levels,nr,nt", [((1024, 1024), inputs.C1, (0.0, 0.5), 64, 36),
+                                                    ((256, 256, 256), inputs.C2, (0.0,), 128, 1)],
+                         ids=["2d-1024", "3d-256"])
+def test_tile_widths_give_the_same_results(hf, shape, cfg, levels, nr, nt):
+    # every strided column is transformed on its own, so the tile width changes
+    # only the order of the bin sums: fields and maps are bit-identical, bins agree
+    # to rounding and all match the oracle; the cached bin table follows the width
+    gf, of = filters(hf, **inputs.filter_kwargs(cfg))
+    want = oracle.pipeline(shape, of, 4, 0, levels=levels, nr=nr, ntheta=nt)
+    plan = hf.Plan(shape)
+    hf.hufield_plan_set_bins(plan, nr, nt)
+    ref = None
+    for tile in (0, 1, 2, 0):
+        hf.hufield_plan_set_tile(plan, tile)
+        assert hf.hufield_plan_tile(plan) == tile
+        got = run_pipeline(hf, plan, gf, shape, 4, 0, levels, nr, nt)
+        compare(got, want, levels, int(np.prod(shape)))
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got["f"], ref["f"]) and np.array_equal(got["maps"], ref["maps"])
+            np.testing.assert_allclose(got["sums_m"], ref["sums_m"], rtol=1e-5, atol=1e-9 * ref["sums_m"].max())
+            np.testing.assert_array_equal(got["counts_m"], ref["counts_m"])
+    with pytest.raises(hf.HufieldError):
+        hf.hufield_plan_set_tile(plan, 3)

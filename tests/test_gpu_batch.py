@@ -28,9 +28,11 @@ def _items(hf, count, seed):
     return items, oitems
 
 
-def test_batch_matches_oracle_and_replays(hf):
+@pytest.mark.parametrize("lanes", [0, 1, 8])
+def test_batch_matches_oracle_and_replays(hf, lanes):
+    # lanes 0: the default (two per size class); 8: up to eight side by side
     items, oitems = _items(hf, 14, 1)
-    batch = hf.Batch(items)
+    batch = hf.Batch(items, lanes=lanes)
     out_f = dev_zeros(batch.total_voxels, torch.float32)
     maps = dev_zeros(batch.total_voxels, torch.int8)
     sf, cf = dev_zeros(batch.total_bins, torch.float64), dev_zeros(batch.total_bins, torch.int64)
@@ -51,6 +53,13 @@ def test_batch_matches_oracle_and_replays(hf):
             check_bins(np_(sm)[bo:bo + nr], want["sums_m"][0], np_(cm)[bo:bo + nr], want["counts_m"][0],
                        flips=flips[0], N=N)
     batch.close()
+
+
+def test_batch_rejects_bad_lane_counts(hf):
+    items, _ = _items(hf, 3, 2)
+    with pytest.raises(hf.HufieldError) as e:
+        hf.Batch(items, lanes=9)
+    assert e.value.status == hf.ERR_INVALID_ARG
 
 
 def test_batch_rejects_bad_items(hf):

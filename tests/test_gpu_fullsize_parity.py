@@ -115,16 +115,19 @@ def _volume_against_oracle(hf, n, bf16):
         rms = math.sqrt(float(np.mean(want["f"] ** 2)))
         rb = rel_l2(fb, want["f"])
         mx = float(np.abs(fb - want["f"]).max()) / rms
-        # BF16 keeps 8 significant bits: rounding to nearest leaves each value within
-        # 2^-9 of itself relative, so a Gaussian field's relative L2 is about
-        # 2^-9 / sqrt(3) ~ 1.1e-3 to 1.6e-3 (the binade's spacing varies across it)
+        # BF16 keeps 8 significant bits: rounding to nearest moves a value by at most half
+        # a unit in the last place, 2^-8 of it relative; the error is uniform within that
+        # half unit, so a Gaussian field's relative L2 is about 2^-8 / sqrt(3) times the
+        # mean of 2^e / |f| over the binades, 1.3e-3 to 1.7e-3
         assert 1.0e-3 < rb < 2.0e-3, rb
-        rel_site = np.abs(fb - want["f"]) / np.maximum(np.abs(want["f"]), 1e-30)
-        assert float(rel_site.max()) <= 2.0 ** -8 + 1e-6
+        # per site: the BF16 rounding of a value that is itself within the FP32 gate
+        # (1e-4 rms) of the oracle's
+        err = np.abs(fb - want["f"])
+        assert np.all(err <= 2.0 ** -8 * (np.abs(want["f"]) + 1e-4 * rms) + 1e-4 * rms)
         # the maps are thresholded from the FP32 field before the BF16 rounding
         fl = check_maps(mb, want["maps"], want["f"], levels)
         print(f"{n}^3 BF16 field against the oracle: relative L2 {rb:.3e}, max |err| {mx:.3e} rms, "
-              f"largest relative error per site {float(rel_site.max()):.3e}, map sites differing {fl[0]}")
+              f"map sites differing {fl[0]}")
 
 
 def test_512_volume_and_bf16_against_oracle(hf):

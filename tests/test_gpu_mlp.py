@@ -3,8 +3,8 @@
 With `emulate_bf16` the oracle rounds to BF16 where the kernels store BF16
 (weights, layer inputs, back-propagated dz), so the two differ only by the
 FP32 accumulation order and by the rare value that falls on the other side of
-a BF16 rounding boundary: results agree to ~1e-5 relative, and the gates here
-are 1e-4 (forward) and 1e-3 (gradients).  Against the oracle without BF16
+a BF16 rounding boundary: results agree to ~1e-4 relative, and the gates here
+are 3e-4 (forward) and 1e-3 (gradients).  Against the oracle without BF16
 (the network's exact FP64 value) the error of the BF16 storage is stated and
 bounded at 3e-2."""
 import math
@@ -63,8 +63,11 @@ def test_forward_matches_oracle(M, rows):
     torch.cuda.synchronize()
     got = np_(y).astype(np.float64)
     want, _ = omlp.forward(flat, x, emulate_bf16=True)
+    # the FP32 dot products (K = 256) carry ~1e-6 relative error, so about one activation
+    # in a few thousand rounds to the other BF16 neighbour than the FP64 value does and
+    # moves by 2^-8 of itself: ~1e-4 relative L2 at the output (7.6e-5 measured)
     r = rel_l2(got, want)
-    assert r < 1e-4
+    assert r < 3e-4
     # an activation that rounds to the other BF16 neighbour (its FP32 value within
     # FP32 rounding of a BF16 tie) moves by 2^-8 of itself, and an output by about
     # |W| 2^-8 |a|: a few 1e-3 of the output rms at the worst element
