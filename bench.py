@@ -325,7 +325,7 @@ def run_ragged(args):
                          "peak_source": peak_kind},
             "pipeline": {"bytes_per_voxel": round(nbytes / voxels, 2), "GBps": round(gbs, 1),
                          "frac": round(gbs / peak, 4)},
-            "gpu_launches": args.steps * (4 * n2 + 7 * n3), "clocks": clk, "e2e": None, "cpu_baseline": None}
+            "gpu_launches": args.steps * batch.launches(), "clocks": clk, "e2e": None, "cpu_baseline": None}
     if not args.no_e2e:
         line["e2e"] = ragged_e2e(hf, torch, batch, out_f, maps, (sf, cf, sm, cm), ws, stream, args)
     if not args.no_cpu_baseline:
@@ -399,7 +399,10 @@ def run_surrogate(args):
     plain generator (64-field mean within 5% relative L2 of the target), and the
     plain generator's own search (Nelder-Mead, 16 fields per evaluation) on a
     sample of the same targets.  One JSON line: the ratio of GPU-seconds per
-    confirmed design, with and without the amortised data and training."""
+    confirmed design, with the surrogate's data and training amortised over the
+    designs (value) and without (ratio_marginal).  GPU-seconds are the device
+    time of each phase's GPU work (CUDA events around it); host work between
+    (planning batches, the search's own logic) is not counted on either side."""
     import numpy as np
     import torch
 
@@ -431,28 +434,31 @@ def run_surrogate(args):
     T = sg.plain_spectra(tt, seed=11, nseeds=64)
     Tn = T.cpu().numpy()
     best, L, design_s, allth, order = model.design(T, starts=cfg["starts"], iters=cfg["iters"])
-    with sg.Timer() as tv:
-        V = sg.plain_spectra(best, seed=12, nseeds=64).cpu().numpy()
+    tv = sg.Timer()  # device time of the verification runs (their batches' planning is host work)
+    V = sg.plain_spectra(best, seed=12, nseeds=64, timer=tv).cpu().numpy()
     err = sg.rel_err(V, Tn)
     # a design that fails falls back to the next start by the surrogate's loss (verified the same way)
     retry = np.where(err > sg.CONFIRM)[0]
-    with sg.Timer() as tr:
-        if len(retry):
-            alt = allth[retry, order[retry, 1]]
-            Va = sg.plain_spectra(alt, seed=12, nseeds=64).cpu().numpy()
-            ea = sg.rel_err(Va, Tn[retry])
-            better = ea < err[retry]
-            err[retry[better]] = ea[better]
-    verify_s = (tv.ms + tr.ms) / 1e3
+    if len(retry):
+        alt = allth[retry, order[retry, 1]]
+        Va = sg.plain_spectra(alt, seed=12, nseeds=64, timer=tv).cpu().numpy()
+        ea = sg.rel_err(Va, Tn[retry])
+        better = ea < err[retry]
+        err[retry[better]] = ea[better]
+    verify_s = tv.ms / 1e3
     confirmed = int((err <= sg.CONFIRM).sum())
-    # the plain generator's own search on a sample of the targets
+    # the plain generator's own search on a sample of the targets, its answer
+    # confirmed the same way as a design (64 fields)
     ps = []
+    ev = sg.Evaluator(13, cfg["plain_seeds"])
     for i in range(cfg["plain_sample"]):
-        with sg.Timer() as tp:
-            thp, ep, nev = sg.nelder_mead_search(Tn[i], seed=13, nseeds=cfg["plain_seeds"],
-                                                 budget=cfg["plain_budget"], rng_seed=i)
-        Vp = sg.plain_spectra(thp[None, :].astype(np.float32), seed=12, nseeds=64).cpu().numpy()
-        ps.append((nev, tp.ms / 1e3, float(sg.rel_err(Vp, Tn[i:i + 1])[0])))
+        before = ev.timer.ms
+        tc = sg.Timer()
+        thp, ep, nev = sg.nelder_mead_search(Tn[i], seed=13, nseeds=cfg["plain_seeds"],
+                                             budget=cfg["plain_budget"], rng_seed=i, evaluator=ev)
+        Vp = sg.plain_spectra(thp[None, :].astype(np.float32), seed=12, nseeds=64, timer=tc).cpu().numpy()
+        ps.append((nev, (ev.timer.ms - before + tc.ms) / 1e3, float(sg.rel_err(Vp, Tn[i:i + 1])[0])))
+    ev.close()
     clk = clocks.stop(None)
     plain_s = float(np.mean([p[1] for p in ps]))
     plain_ok = sum(1 for p in ps if p[2] <= sg.CONFIRM)
@@ -472,9 +478,14 @@ def run_surrogate(args):
                           "verify": round(verify_s, 3)},
                 "train_losses": [round(x, 5) for x in log.losses],
                 "gpu_s_per_confirmed_design": {"amortised": sur_total, "marginal": sur_marginal}},
-            "plain_search": {"targets": len(ps), "confirmed": plain_ok, "evaluations_mean": float(np.mean([p[0] for p in ps])),
+            "plain_search": {"targets": len(ps), "confirmed": plain_ok,
+                             "evaluations_mean": float(np.mean([p[0] for p in ps])),
                              "gpu_s_mean": plain_s, "gpu_s_per_confirmed_design": plain_per_confirmed,
                              "errors": [round(p[2], 4) for p in ps]},
+            "generator_fields_per_confirmed_design": {
+                "plain_search": (sum(p[0] for p in ps) * cfg["plain_seeds"] + 64 * len(ps)) / max(plain_ok, 1),
+                "surrogate_marginal": 64 * (cfg["designs"] + len(retry)) / max(confirmed, 1),
+                "surrogate_amortised": (64 * (cfg["designs"] + len(retry)) + n) / max(confirmed, 1)},
             "ratio_marginal": plain_per_confirmed / sur_marginal,
             "clocks": clk}
     print(json.dumps(line), flush=True)

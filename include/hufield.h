@@ -293,9 +293,26 @@ typedef struct hufield_batch hufield_batch;
  * many small fields, whose passes each fill only a few SMs, run side by side. */
 #define HUFIELD_BATCH_LANES(l) (((uint32_t)(l) & 15u) << 8)
 
+/* Batch flag: run every item through its own calls (hufield_ensemble of one
+ * field), as for a size class whose items differ in their number of bins.
+ * Without it, a class whose items share nr runs a chunk of items at a time
+ * (as many as 512 MB of half spectra per lane hold) through the passes of the
+ * path, each pass one launch over the whole chunk with every field's own
+ * filter, seed, index and level; the filter's band edge is the chunk's
+ * largest (the environment variable HUFIELD_BATCH_CHUNK_BYTES, read when the
+ * batch is planned, sets another budget).  Both give the same fields and maps;
+ * bin sums agree to rounding. */
+#define HUFIELD_BATCH_PER_ITEM 2u
+
+/* Batch flag: the items' parameters may be replaced after planning
+ * (hufield_batch_set_params) without capturing the graph again; the filter's
+ * band edge then prunes nothing. */
+#define HUFIELD_BATCH_UPDATABLE 4u
+
 /* Plan a batch of n >= 1 items on the current device (copies the items;
- * flags: HUFIELD_BATCH_AUTOTUNE and/or HUFIELD_BATCH_LANES(l)).  Allocates the
- * size-class plans and streams. */
+ * flags: HUFIELD_BATCH_AUTOTUNE, HUFIELD_BATCH_PER_ITEM and/or
+ * HUFIELD_BATCH_LANES(l)).  Allocates the size-class plans, streams and the
+ * batched classes' parameter arrays. */
 int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, int32_t n, uint32_t flags);
 
 /* Output layout (host arrays of n entries, either may be NULL): item i's
@@ -309,6 +326,16 @@ int hufield_batch_layout(const hufield_batch *batch, int64_t *f_offset, int64_t 
  * first run, and any run with other buffers, captures the graph. */
 int hufield_batch_run(hufield_batch *batch, float *out_f, int8_t *out_maps, double *sums_f, int64_t *counts_f,
                       double *sums_m, int64_t *counts_m, void *ws, size_t ws_bytes, void *stream);
+
+/* Kernels one hufield_batch_run launches (inside its graph): per batched
+ * chunk or per item run on its own, 5 for a 2D and 8 for a 3D lattice. */
+int hufield_batch_launches(const hufield_batch *batch, int64_t *launches);
+
+/* Replace the parameters (filter, seed, field index, level) of every item of
+ * a batch planned with HUFIELD_BATCH_UPDATABLE; item i keeps its lattice and
+ * nr.  Copies on `stream` and waits for it; later runs use the new values
+ * (a size class run item by item captures its graph again). */
+int hufield_batch_set_params(hufield_batch *batch, const hufield_batch_item *items, int32_t n, void *stream);
 
 int hufield_batch_destroy(hufield_batch *batch);
 
@@ -357,6 +384,13 @@ int hufield_filter_modes(hufield_plan *plan, const hufield_filter *f, float *out
  * bytes those passes move.  Host only, nothing is enqueued.  Errors:
  * HUFIELD_ERR_INVALID_ARG (null pointer or a filter hufield_generate rejects). */
 int hufield_filter_band_edge(const hufield_plan *plan, const hufield_filter *f, int64_t *kz);
+
+/* Group means of per-item bins laid out item after item (nbins each, as a
+ * batch whose items share nbins lays them out): out[g][b] = (sum over the
+ * group_size items of group g of sums) / (sum of their counts), FP32, 0 when
+ * empty; groups x nbins entries. */
+int hufield_bins_group_mean(const double *sums, const int64_t *counts, int64_t groups, int32_t group_size,
+                            int32_t nbins, float *out, void *stream);
 
 /* Bin means: out_mean[b] = counts[b] ? sums[b] / counts[b] : 0. */
 int hufield_bins_mean(const double *sums, const int64_t *counts, int32_t nbins, double *out_mean,

@@ -117,6 +117,28 @@ int hufield_mlp_adam(float *params, float *m, float *v, const float *grad, uint1
 int hufield_mlp_gather(const float *x_all, const float *S_all, int64_t n, int64_t rows, uint64_t seed, int64_t step,
                        float *x_out, float *S_out, void *stream);
 
+/* One whole training step, enqueued with no host-side per-step arguments so
+ * that a CUDA graph of many steps can be replayed: the step counter s lives
+ * in the training workspace (hufield_mlp_train_reset sets it).  The step
+ * gathers `rows` rows as hufield_mlp_gather with step s and sched->seed,
+ * runs forward, the deviance (adding to *loss_sum), backward into grad, and
+ * Adam at t = s + 1 with the learning rate
+ * lr (f + (1 - f) (1 + cos(pi s / total_steps)) / 2), f = lr_min_frac, and
+ * decoupled decay wd; then s += 1.  m, v, grad: param-shaped FP32. */
+typedef struct {
+    float lr, lr_min_frac, beta1, beta2, eps, wd;
+    int64_t total_steps;
+    uint64_t seed;
+} hufield_mlp_sched;
+
+/* Bytes of the training workspace for `rows` rows per step (0 for rows < 1). */
+size_t hufield_mlp_train_workspace_bytes(int64_t rows);
+int hufield_mlp_train_reset(void *tws, int64_t step, void *stream);
+int hufield_mlp_train_step(float *params, uint16_t *wq, float *m, float *v, float *grad, const float *x_all,
+                           const float *S_all, int64_t n, int64_t rows, const float *mu, const float *sigma,
+                           const hufield_mlp_sched *sched, double *loss_sum, void *tws, size_t tws_bytes,
+                           void *stream);
+
 /* Inverse-design loss per row against a target spectrum T [rows][128]
  * (bin means, all > 0): with y = mu + sigma y_hat,
  * loss_row = sum_{b>=1} (e^{y_b} - T_b)^2 / sum_{b>=1} T_b^2

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include <cuda.h>
@@ -27,15 +28,18 @@ KernelInfo cols_kernel_plain(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_filter(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_bins(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_kspace(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_filter_batch(int log2l, bool big, int mode, int dir);
 
 KernelInfo r2c_kernel(int log2m, bool big, int src) {
-    return src == kSrcNoise ? r2c_kernel_noise(log2m, big, src) : r2c_kernel_src(log2m, big, src);
+    return (src == kSrcNoise || src == kSrcNoiseBatch) ? r2c_kernel_noise(log2m, big, src)
+                                                       : r2c_kernel_src(log2m, big, src);
 }
 KernelInfo cols_kernel(int log2l, bool big, int mode, int dir) {
     switch (mode) {
         case kModePlain: return cols_kernel_plain(log2l, big, mode, dir);
         case kModeFilter: return cols_kernel_filter(log2l, big, mode, dir);
         case kModeKspace: return cols_kernel_kspace(log2l, big, mode, dir);
+        case kModeFilterBatch: return cols_kernel_filter_batch(log2l, big, mode, dir);
         default: return cols_kernel_bins(log2l, big, mode, dir);
     }
 }
@@ -171,6 +175,57 @@ __global__ void k_add_counts(const __grid_constant__ AddCountsArgs a) {
 __global__ void k_add_doubles(double* dst, const double* src, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] += src[i];
+}
+
+// The fields of a batched chunk after the filter pass (one block per field):
+// its c2r scale sigma_f / sqrt(P) (0, with the no-power status bit, when the
+// filter passed no power), its field bins sums_f = raw N / P, its counts, and
+// its map bins cleared for the binning pass to add to.
+struct FinishArgs {
+    const double* acc;        // field f: P at acc[f stride], raw bins after it
+    long long stride;
+    const float* sigma_f;     // per field
+    const long long* boff;    // per field: first bin
+    const long long* counts;  // per bin (the lattice's)
+    int nbins;
+    double N;
+    float* fscale;
+    double* sums_f;
+    long long* counts_f;
+    double* sums_m;
+    long long* counts_m;
+    unsigned* status;
+};
+__global__ void k_fields_finish(const __grid_constant__ FinishArgs a) {
+    const int f = blockIdx.x;
+    const double P = a.acc[f * a.stride];
+    const bool empty = !(P > 0.0);
+    if (threadIdx.x == 0) {
+        a.fscale[f] = empty ? 0.0f : (float)((double)a.sigma_f[f] / sqrt(P));
+        if (empty) atomicOr(a.status, kStatusNoPower);
+    }
+    const long long o = a.boff[f];
+    for (int b = threadIdx.x; b < a.nbins; b += blockDim.x) {
+        a.sums_f[o + b] = empty ? 0.0 : a.acc[f * a.stride + 1 + b] * (a.N / P);
+        a.counts_f[o + b] = a.counts[b];
+        a.sums_m[o + b] = 0.0;
+        a.counts_m[o + b] = a.counts[b];
+    }
+}
+
+// out[g][b] = sum over the group's items of sums / sum of counts (0 when empty).
+__global__ void k_group_mean(const double* sums, const long long* counts, long long groups, int gsize, int nbins,
+                             float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= groups * nbins) return;
+    const long long g = i / nbins, b = i - g * nbins;
+    double s = 0.0;
+    long long c = 0;
+    for (int k = 0; k < gsize; ++k) {
+        s += sums[(g * gsize + k) * nbins + b];
+        c += counts[(g * gsize + k) * nbins + b];
+    }
+    out[i] = c ? (float)(s / (double)c) : 0.0f;
 }
 
 __global__ void k_bins_mean(const double* sums, const long long* counts, int nbins, double* out) {
@@ -325,7 +380,8 @@ bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
     L.smem = k.fixed_smem + extra_smem;
-    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm, p->col_cap[mode & 3]);
+    L.grid = occupancy_grid(k.fn, L.block, L.smem, A * (B >> k.log2_lines), p->nsm,
+                            p->col_cap[mode == kModeFilterBatch ? kModeFilter : mode & 3]);
     return L.grid > 0;
 }
 
@@ -635,8 +691,12 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
 // filter passes run only the columns k_last < kz (kz < 0: all).
 int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const FilterParams* fp,
                const BinParams& bp, const unsigned short* bintab, double* gbins, double* gP, unsigned* status,
-               cudaStream_t s, uint64_t seed = 0, uint32_t field_idx = 0, long long kz = -1) {
+               cudaStream_t s, uint64_t seed = 0, uint32_t field_idx = 0, long long kz = -1,
+               const FilterParams* fparr = nullptr, long long acc_stride = 0, const long long* boff = nullptr) {
     ColArgs ca{};
+    ca.fparr = fparr;
+    ca.acc_stride = acc_stride;
+    ca.boff = boff;
     ca.seed = seed;
     ca.field_idx = field_idx;
     ca.kscale = (float)sqrt(0.5 * (double)p->N);
@@ -659,7 +719,8 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     ca.scale = (float)(1.0 / (double)p->N);
     const size_t extra = mode == kModePlain ? 0
                                             : (size_t)(bp.nbins + 1) * (sizeof(double) + sizeof(float)) +
-                                                  (mode == kModeFilter || mode == kModeKspace
+                                                  (mode == kModeFilter || mode == kModeKspace ||
+                                                           mode == kModeFilterBatch
                                                        ? sizeof(float) << p->log2n[0]
                                                        : 0);
     Launch L;
@@ -667,7 +728,7 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
     if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, 1, extra, k, L)) return HUFIELD_ERR_CUDA;
     set_tiles(p, ca, k.log2_lines, kz < 0 ? (1ll << p->logM) : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
-    const int kind = (mode == kModeFilter || mode == kModeKspace) ? kPassFilter
+    const int kind = (mode == kModeFilter || mode == kModeKspace || mode == kModeFilterBatch) ? kPassFilter
                      : mode == kModeBins                           ? kPassBins
                                                                    : kPassMidFwd;
     HF_CUDA(launch(p, kind, k.fn, L, &ca, s));
@@ -1488,6 +1549,16 @@ int hufield_filter_band_edge(const hufield_plan* p, const hufield_filter* f, int
     return HUFIELD_OK;
 }
 
+int hufield_bins_group_mean(const double* sums, const int64_t* counts, int64_t groups, int32_t group_size,
+                            int32_t nbins, float* out, void* stream) {
+    if (!sums || !counts || !out || groups < 1 || group_size < 1 || nbins < 1) return HUFIELD_ERR_INVALID_ARG;
+    const long long n = groups * (long long)nbins;
+    k_group_mean<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        sums, reinterpret_cast<const long long*>(counts), groups, group_size, nbins, out);
+    HF_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
 int hufield_bins_mean(const double* sums, const int64_t* counts, int32_t nbins, double* out, void* stream) {
     if (!sums || !counts || !out || nbins < 1) return HUFIELD_ERR_INVALID_ARG;
     k_bins_mean<<<(nbins + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
@@ -1639,6 +1710,13 @@ extern "C" int hufield_spectrum_noalloc_status(void* stream) {
 constexpr int kBatchLanes = 2;
 constexpr int kMaxBatchLanes = 8;
 
+// A class whose items share the number of radial bins runs a chunk of its
+// items at a time through the batched passes (every pass covers the whole
+// chunk in one launch, each field with its own filter, seed and level); the
+// items' parameters live in device arrays in member order.  Chunks hold up to
+// kChunkBytes of half spectra per lane.
+constexpr size_t kChunkBytes = 512ull << 20;
+
 struct hufield_batch {
     struct Class {
         hufield_plan* plan = nullptr;
@@ -1647,6 +1725,20 @@ struct hufield_batch {
         cudaEvent_t join[kMaxBatchLanes] = {};
         std::vector<int> members;
         size_t ws_off = 0, ws_bytes = 0;  // lane l's slice starts at ws_off + l * align256(ws_bytes)
+        // batched chunks
+        bool fused = false;
+        int nr = 0;
+        long long chunk = 1;                // items per chunk
+        long long acc_stride = 0;           // doubles per field: P, then the raw field bins
+        std::vector<long long> chunk_kz;    // per chunk: the largest band edge of its items
+        void* dmem = nullptr;               // the device arrays below, one allocation
+        FilterParams* d_fp = nullptr;
+        unsigned long long* d_seed = nullptr;
+        unsigned* d_idx = nullptr;
+        float* d_level = nullptr;
+        float* d_sigma = nullptr;
+        long long* d_fout = nullptr;
+        long long* d_boff = nullptr;
     };
     std::vector<hufield_batch_item> items;
     std::vector<Class> classes;
@@ -1658,6 +1750,7 @@ struct hufield_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void* key[8] = {};  // buffers the graph was captured with
+    bool updatable = false;   // HUFIELD_BATCH_UPDATABLE: no band-edge pruning; parameters replaceable
 };
 
 namespace {
@@ -1667,6 +1760,7 @@ void batch_free(hufield_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto& c : b->classes) {
         if (c.plan) hufield_plan_destroy(c.plan);
+        cudaFree(c.dmem);
         for (int l = 0; l < kMaxBatchLanes; ++l) {
             if (c.stream[l]) cudaStreamDestroy(c.stream[l]);
             if (c.join[l]) cudaEventDestroy(c.join[l]);
@@ -1684,13 +1778,167 @@ bool same_dims(const hufield_dims& a, const hufield_dims& b) {
     return true;
 }
 
+// Lane workspace of a batched class: [header: status][chunk x N/2 complex64]
+// [chunk x acc_stride doubles][chunk floats: scales].
+size_t chunk_ws_bytes(const hufield_plan* p, long long chunk, long long acc_stride) {
+    return kWsHeader + align256((size_t)chunk * (size_t)p->half * sizeof(float2)) +
+           align256((size_t)chunk * (size_t)acc_stride * sizeof(double)) + align256((size_t)chunk * sizeof(float));
+}
+
+// The whole path for items i0 .. i0 + nk - 1 (member order) of a batched class
+// on one lane: every pass covers the chunk in one launch.
+int run_chunk(hufield_batch::Class& C, long long i0, long long nk, long long kz, char* lws, float* out_f,
+              int8_t* out_maps, double* sums_f, int64_t* counts_f, double* sums_m, int64_t* counts_m,
+              cudaStream_t s) {
+    hufield_plan* p = C.plan;
+    unsigned* status = reinterpret_cast<unsigned*>(lws);
+    float2* spec = reinterpret_cast<float2*>(lws + kWsHeader);
+    double* acc = reinterpret_cast<double*>(lws + kWsHeader + align256((size_t)C.chunk * (size_t)p->half * sizeof(float2)));
+    float* fscale = reinterpret_cast<float*>(reinterpret_cast<char*>(acc) +
+                                             align256((size_t)C.chunk * (size_t)C.acc_stride * sizeof(double)));
+    BinParams bp;
+    int rc = make_bins(p, C.nr, 1, bp);
+    if (rc) return rc;
+    if (!p->cache_tab || p->cache_logtb != axis0_logtb(p)) return HUFIELD_ERR_CUDA;
+    const unsigned short* tab = p->cache_tab;
+    HF_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+    HF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)(nk * C.acc_stride), s));
+    // noise and the forward transform of every field of the chunk
+    // the row kernels run whole tiles: the chunk's rows are rounded up to a tile and
+    // the tail of the last tile (past the last field) is neither read nor written
+    const int log2_rows = p->log2n[0] + (p->ndim == 3 ? p->log2n[1] : 0);
+    const long long nrows_valid = nk << log2_rows;
+    RowArgs ra{};
+    ra.out = spec;
+    ra.tw = p->tw;
+    ra.fseed = C.d_seed + i0;
+    ra.fidx = C.d_idx + i0;
+    ra.log2_rows_field = log2_rows;
+    ra.nrows_valid = nrows_valid;
+    Launch L;
+    KernelInfo k = pick_row(p->logM, nrows_valid, r2c_kernel, kSrcNoiseBatch);
+    const long long nrows = (nrows_valid + (1ll << k.log2_lines) - 1) >> k.log2_lines << k.log2_lines;
+    ra.nrows = nrows;
+    if (!row_launch(p, k, nrows, L)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassR2C, k.fn, L, &ra, s));
+    if (p->ndim == 3 && (rc = mid_pass(p, -1, spec, nk, kPassMidFwd, status, s, kz))) return rc;
+    // each field's filter, Parseval sum and raw field bins, then the inverse along axis 0
+    rc = axis0_pass(p, kModeFilterBatch, spec, nk, nullptr, bp, tab, acc + 1, acc, status, s, 0, 0, kz,
+                    C.d_fp + i0, C.acc_stride, nullptr);
+    if (rc) return rc;
+    if (p->ndim == 3 && (rc = mid_pass(p, +1, spec, nk, kPassMidInv, status, s, kz))) return rc;
+    FinishArgs fa{};
+    fa.acc = acc;
+    fa.stride = C.acc_stride;
+    fa.sigma_f = C.d_sigma + i0;
+    fa.boff = C.d_boff + i0;
+    fa.counts = p->cache_counts;
+    fa.nbins = bp.nbins;
+    fa.N = (double)p->N;
+    fa.fscale = fscale;
+    fa.sums_f = sums_f;
+    fa.counts_f = reinterpret_cast<long long*>(counts_f);
+    fa.sums_m = sums_m;
+    fa.counts_m = reinterpret_cast<long long*>(counts_m);
+    fa.status = status;
+    HF_CUDA(profiled(p, kPassMisc, s, [&] {
+        k_fields_finish<<<(unsigned)nk, 128, 0, s>>>(fa);
+        return cudaGetLastError();
+    }));
+    // fields, maps and the maps' first transform
+    C2RArgs ca{};
+    ca.kz = (int)kz;
+    ca.spec = spec;
+    ca.nrows_valid = nrows_valid;
+    ca.half = p->half;
+    ca.N = p->N;
+    ca.out_f = out_f;
+    ca.out_maps = reinterpret_cast<signed char*>(out_maps);
+    ca.nlev = 1;
+    ca.tw = p->tw;
+    ca.status = status;
+    ca.wait_budget = p->wait_budget;
+    ca.inject_skip = p->inject_timeout ? 1 : 0;
+    ca.log2_rows_field = log2_rows;
+    ca.fscale = fscale;
+    ca.flevel = C.d_level + i0;
+    ca.fout = C.d_fout + i0;
+    k = pick_row(p->logM, nrows_valid, c2r_kernel, kOutBatch);
+    ca.nrows = (nrows_valid + (1ll << k.log2_lines) - 1) >> k.log2_lines << k.log2_lines;
+    if (!row_launch(p, k, ca.nrows, L)) return HUFIELD_ERR_CUDA;
+    HF_CUDA(launch(p, kPassC2R, k.fn, L, &ca, s));
+    if (p->ndim == 3 && (rc = mid_pass(p, -1, spec, nk, kPassMidMaps, status, s))) return rc;
+    return axis0_pass(p, kModeBins, spec, nk, nullptr, bp, tab, sums_m, nullptr, status, s, 0, 0, -1, nullptr, 0,
+                      C.d_boff + i0);
+}
+
+// Device arrays of a batched class's item parameters (member order) and its
+// chunks' band edges (none in an updatable batch, whose parameters may change
+// after the graph is captured); copied on `s` (0: synchronously).
+int setup_fused(hufield_batch* b, hufield_batch::Class& C, cudaStream_t s = nullptr, bool copy_only = false) {
+    const long long nm = (long long)C.members.size();
+    std::vector<FilterParams> fp(nm);
+    std::vector<unsigned long long> seed(nm);
+    std::vector<unsigned> idx(nm);
+    std::vector<float> level(nm), sigma(nm);
+    std::vector<long long> fout(nm), boff(nm), kz(nm);
+    for (long long m = 0; m < nm; ++m) {
+        const int i = C.members[m];
+        const hufield_batch_item& it = b->items[i];
+        fp[m] = make_filter(C.plan, &it.filt);
+        seed[m] = it.seed;
+        idx[m] = it.field_idx;
+        level[m] = it.level;
+        sigma[m] = it.filt.sigma_f;
+        fout[m] = b->f_off[i];
+        boff[m] = b->bin_off[i];
+        kz[m] = b->updatable ? (1ll << C.plan->logM) : zero_kz(C.plan, fp[m]);
+    }
+    if (copy_only) {
+        if (cudaMemcpyAsync(C.d_fp, fp.data(), sizeof(FilterParams) * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(C.d_seed, seed.data(), 8 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(C.d_idx, idx.data(), 4 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(C.d_level, level.data(), 4 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(C.d_sigma, sigma.data(), 4 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)  // the host vectors go out of scope
+            return HUFIELD_ERR_CUDA;
+        return HUFIELD_OK;
+    }
+    const long long nchunks = (nm + C.chunk - 1) / C.chunk;
+    C.chunk_kz.assign(nchunks, 0);
+    for (long long m = 0; m < nm; ++m) C.chunk_kz[m / C.chunk] = std::max(C.chunk_kz[m / C.chunk], kz[m]);
+    const size_t o_fp = 0, o_seed = align256(sizeof(FilterParams) * nm), o_idx = o_seed + align256(8 * nm),
+                 o_level = o_idx + align256(4 * nm), o_sigma = o_level + align256(4 * nm),
+                 o_fout = o_sigma + align256(4 * nm), o_boff = o_fout + align256(8 * nm),
+                 total = o_boff + align256(8 * nm);
+    if (cudaMalloc(&C.dmem, total) != cudaSuccess) return HUFIELD_ERR_CUDA;
+    char* base = static_cast<char*>(C.dmem);
+    C.d_fp = reinterpret_cast<FilterParams*>(base + o_fp);
+    C.d_seed = reinterpret_cast<unsigned long long*>(base + o_seed);
+    C.d_idx = reinterpret_cast<unsigned*>(base + o_idx);
+    C.d_level = reinterpret_cast<float*>(base + o_level);
+    C.d_sigma = reinterpret_cast<float*>(base + o_sigma);
+    C.d_fout = reinterpret_cast<long long*>(base + o_fout);
+    C.d_boff = reinterpret_cast<long long*>(base + o_boff);
+    if (cudaMemcpy(C.d_fp, fp.data(), sizeof(FilterParams) * nm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C.d_seed, seed.data(), 8 * nm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C.d_idx, idx.data(), 4 * nm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C.d_level, level.data(), 4 * nm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C.d_sigma, sigma.data(), 4 * nm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C.d_fout, fout.data(), 8 * nm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C.d_boff, boff.data(), 8 * nm, cudaMemcpyHostToDevice) != cudaSuccess)
+        return HUFIELD_ERR_CUDA;
+    return HUFIELD_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int32_t n, uint32_t flags) {
     const int want_lanes = (int)((flags >> 8) & 15u);
-    if (!out || !items || n < 1 || (flags & ~(HUFIELD_BATCH_AUTOTUNE | (15u << 8))) != 0 ||
+    if (!out || !items || n < 1 ||
+        (flags & ~(HUFIELD_BATCH_AUTOTUNE | HUFIELD_BATCH_PER_ITEM | HUFIELD_BATCH_UPDATABLE | (15u << 8))) != 0 ||
         want_lanes > kMaxBatchLanes)
         return HUFIELD_ERR_INVALID_ARG;
     const int max_lanes = want_lanes > 0 ? want_lanes : kBatchLanes;
@@ -1698,6 +1946,7 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
     hufield_batch* b = new (std::nothrow) hufield_batch();
     if (!b) return HUFIELD_ERR_CUDA;
     b->items.assign(items, items + n);
+    b->updatable = (flags & HUFIELD_BATCH_UPDATABLE) != 0;
     std::vector<int> cls(n, -1);
     std::vector<hufield_dims> cdims;
     for (int i = 0; i < n; ++i) {
@@ -1747,9 +1996,25 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
     for (size_t c = 0; c < b->classes.size(); ++c) {
         auto& C = b->classes[c];
         C.lanes = (int)C.members.size() < max_lanes ? (int)C.members.size() : max_lanes;
+        if (uniform[c] && !(flags & HUFIELD_BATCH_PER_ITEM)) {
+            // batched chunks: as many items per lane as kChunkBytes of spectra hold
+            C.fused = true;
+            C.nr = class_nr[c];
+            const long long per_lane = ((long long)C.members.size() + C.lanes - 1) / C.lanes;
+            size_t budget = kChunkBytes;
+            if (const char* e = getenv("HUFIELD_BATCH_CHUNK_BYTES")) {
+                const long long v = atoll(e);
+                if (v > 0) budget = (size_t)v;
+            }
+            const long long fit = (long long)(budget / ((size_t)C.plan->half * sizeof(float2)));
+            C.chunk = std::max(1ll, std::min(per_lane, fit));
+            C.acc_stride = (1 + C.nr + 31) / 32 * 32;
+            C.ws_bytes = chunk_ws_bytes(C.plan, C.chunk, C.acc_stride);
+        }
         C.ws_off = b->ws_total;
         b->ws_total += (size_t)C.lanes * align256(C.ws_bytes);
         if (uniform[c] && hufield_plan_set_bins(C.plan, class_nr[c], 1) != HUFIELD_OK) rc = HUFIELD_ERR_CUDA;
+        if (!rc && C.fused) rc = setup_fused(b, C);
         for (int l = 0; l < C.lanes; ++l)
             if (cudaStreamCreateWithFlags(&C.stream[l], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&C.join[l], cudaEventDisableTiming) != cudaSuccess)
@@ -1800,7 +2065,14 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
                 cudaStream_t ls = C.stream[l];
                 char* lws = reinterpret_cast<char*>(ws) + C.ws_off + (size_t)l * align256(C.ws_bytes);
                 if (cudaStreamWaitEvent(ls, b->fork, 0) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
-                for (size_t m = (size_t)l; m < C.members.size() && !rc; m += (size_t)C.lanes) {
+                const long long nchunks = C.fused ? (long long)C.chunk_kz.size() : 0;
+                for (long long c = l; c < nchunks && !rc; c += C.lanes) {
+                    const long long i0 = c * C.chunk;
+                    const long long nk = std::min(C.chunk, (long long)C.members.size() - i0);
+                    rc = run_chunk(C, i0, nk, C.chunk_kz[c], lws, out_f, out_maps, sums_f, counts_f, sums_m,
+                                   counts_m, ls);
+                }
+                for (size_t m = (size_t)l; !C.fused && m < C.members.size() && !rc; m += (size_t)C.lanes) {
                     const int i = C.members[m];
                     const hufield_batch_item& it = b->items[i];
                     const long long fo = b->f_off[i], bo = b->bin_off[i];
@@ -1829,6 +2101,48 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
         for (int k = 0; k < 8; ++k) b->key[k] = key[k];
     }
     HF_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return HUFIELD_OK;
+}
+
+int hufield_batch_launches(const hufield_batch* b, int64_t* launches) {
+    if (!b || !launches) return HUFIELD_ERR_INVALID_ARG;
+    long long total = 0;
+    for (const auto& C : b->classes) {
+        const int per = C.plan->ndim == 3 ? 8 : 5;  // r2c, [axis 1], filter, [axis 1], finish or counts, c2r, [axis 1], bins
+        total += (C.fused ? (long long)C.chunk_kz.size() : (long long)C.members.size()) * per;
+    }
+    *launches = total;
+    return HUFIELD_OK;
+}
+
+int hufield_batch_set_params(hufield_batch* b, const hufield_batch_item* items, int32_t n, void* stream) {
+    if (!b || !items || !b->updatable || n != (int32_t)b->items.size()) return HUFIELD_ERR_INVALID_ARG;
+    // each item keeps its lattice and bins; the classes' plans check the filters
+    for (auto& C : b->classes) {
+        for (int i : C.members) {
+            const hufield_batch_item& it = items[i];
+            if (!same_dims(it.dims, b->items[i].dims) || it.nr != b->items[i].nr) return HUFIELD_ERR_INVALID_ARG;
+            int rc = check_filter(C.plan, &it.filt);
+            if (!rc && !isfinite(it.level)) rc = HUFIELD_ERR_INVALID_ARG;
+            if (rc) return rc;
+        }
+    }
+    b->items.assign(items, items + n);
+    bool recapture = false;
+    for (auto& C : b->classes) {
+        if (!C.fused) {
+            recapture = true;  // its calls carry the parameters by value: capture again
+            continue;
+        }
+        const int rc = setup_fused(b, C, (cudaStream_t)stream, true);
+        if (rc) return rc;
+    }
+    if (recapture && b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
     return HUFIELD_OK;
 }
 

@@ -26,8 +26,13 @@
 
 namespace hf {
 
-enum NoiseSource { kSrcNoise = 0, kSrcF32 = 1, kSrcBF16 = 2, kSrcI8 = 3 };
-enum ColMode { kModePlain = 0, kModeFilter = 1, kModeBins = 2, kModeKspace = 3 };
+// kSrcNoiseBatch: noise of many fields of one lattice in one launch (a field's
+// rows are consecutive; see RowArgs).  kModeFilterBatch: the filter pass over
+// many fields, each batch with its own filter (see ColArgs).
+enum NoiseSource { kSrcNoise = 0, kSrcF32 = 1, kSrcBF16 = 2, kSrcI8 = 3, kSrcNoiseBatch = 4 };
+enum ColMode { kModePlain = 0, kModeFilter = 1, kModeBins = 2, kModeKspace = 3, kModeFilterBatch = 4 };
+// c2r output: FP32 or BF16 field; kOutBatch: FP32 fields of many fields of one lattice
+enum C2ROut { kOutF32 = 0, kOutBF16 = 1, kOutBatch = 2 };
 
 struct RowArgs {
     const void* src;        // real input rows (kSrcF32/BF16/I8)
@@ -36,6 +41,12 @@ struct RowArgs {
     unsigned long long seed;
     unsigned int field_idx;
     const float2* tw;       // plan twiddles (4096)
+    // kSrcNoiseBatch: row r belongs to field f = r >> log2_rows_field, whose noise
+    // is that of (fseed[f], fidx[f]) with blocks counted from the field's first row
+    const unsigned long long* fseed;
+    const unsigned* fidx;
+    int log2_rows_field;
+    long long nrows_valid;  // kSrcNoiseBatch: rows at or past this (the last tile's tail) are not written
 };
 
 struct C2RArgs {
@@ -60,6 +71,15 @@ struct C2RArgs {
     long long wait_budget;  // clock cycles allowed per mbarrier wait
     int inject_skip;        // test hook: 1 = the first tile's load is never issued
     int kz;                 // entries k_last >= kz of each row are zero (<= M)
+    // kOutBatch (one level per field): row r belongs to field f = r >> log2_rows_field,
+    // scaled by fscale[f] (sigma_f / sqrt(P_f), set by k_fields_scale), thresholded at
+    // flevel[f]; its field and map start fout[f] reals into out_f / out_maps.  P,
+    // sums_f and next_acc are not used.
+    int log2_rows_field;
+    const float* fscale;
+    const float* flevel;
+    const long long* fout;
+    long long nrows_valid;  // kOutBatch: rows at or past this are neither loaded nor written
 };
 
 struct ColArgs {
@@ -92,6 +112,12 @@ struct ColArgs {
     unsigned long long seed;
     unsigned int field_idx;
     float kscale;           // sqrt(N / 2)
+    // FILTER_BATCH: batch ab (a field) is filtered with fparr[ab] and gathers its
+    // Parseval sum at gP + ab acc_stride and its raw field bins at gbins + ab acc_stride
+    const FilterParams* fparr;
+    long long acc_stride;
+    // BINS: batch ab's bins at gbins + boff[ab] when boff is set (else + ab nbins)
+    const long long* boff;
 };
 
 // Minimum resident CTAs per SM asked of the compiler: keeps the kernels of
@@ -322,6 +348,15 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks_r2c(LOG
             float4 x;
             if constexpr (SRC == kSrcNoise) {
                 x = box_muller(noise_block(a.seed, a.field_idx, (unsigned long long)gq));
+            } else if constexpr (SRC == kSrcNoiseBatch) {
+                // a row holds M / 2 blocks of four reals; the last tile may run past the fields
+                if ((gq >> (LOG2M - 1)) < a.nrows_valid) {
+                    const long long f = gq >> (LOG2M - 1 + a.log2_rows_field);
+                    const long long jl = gq - (f << (LOG2M - 1 + a.log2_rows_field));
+                    x = box_muller(noise_block(a.fseed[f], a.fidx[f], (unsigned long long)jl));
+                } else {
+                    x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
             } else if constexpr (SRC == kSrcF32) {
                 x = __ldg(reinterpret_cast<const float4*>(a.src) + gq);
             } else if constexpr (SRC == kSrcBF16) {
@@ -347,7 +382,8 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks_r2c(LOG
         __syncthreads();
         for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int k) {
             const float2 zc = cconj(sm[smem_slot<G>((M - k) & (M - 1), b)]);
-            a.out[(row0 + b) * M + k] = r2c_post(v[e], zc, tw[k]);
+            if (SRC != kSrcNoiseBatch || row0 + b < a.nrows_valid)
+                a.out[(row0 + b) * M + k] = r2c_post(v[e], zc, tw[k]);
         });
     }
 }
@@ -376,18 +412,24 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     const int t = threadIdx.x;
     // f = sigma_f * u / sqrt(sum |G|^2), u the unnormalised inverse (the mean
     // is zero because A(0) = 0): Var = sum|G|^2 / N^2 by Parseval.
-    const double Pv = *a.P;
-    // no power at all (a band beyond the lattice): Eq. (15) is read as f = 0
-    const bool empty = !(Pv > 0.0);
-    const float scale = empty ? 0.0f : (float)((double)a.sigma_f / sqrt(Pv));
-    if (blockIdx.x == 0) {
-        if (empty && t == 0) atomicOr(a.status, kStatusNoPower);
-        if (a.sums_f && !empty) {
-            const double sN = (double)a.N / Pv;
-            for (int b = t; b < a.nbins; b += G::T) a.sums_f[b] += a.P[1 + b] * sN;
+    // (batched fields: each field's scale comes from fscale)
+    float scale = 0.0f;
+    if constexpr (OUTDT != kOutBatch) {
+        const double Pv = *a.P;
+        // no power at all (a band beyond the lattice): Eq. (15) is read as f = 0
+        const bool empty = !(Pv > 0.0);
+        scale = empty ? 0.0f : (float)((double)a.sigma_f / sqrt(Pv));
+        if (blockIdx.x == 0) {
+            if (empty && t == 0) atomicOr(a.status, kStatusNoPower);
+            if (a.sums_f && !empty) {
+                const double sN = (double)a.N / Pv;
+                for (int b = t; b < a.nbins; b += G::T) a.sums_f[b] += a.P[1 + b] * sN;
+            }
+            for (int i = t; i < a.next_len; i += G::T) a.next_acc[i] = 0.0;
         }
-        for (int i = t; i < a.next_len; i += G::T) a.next_acc[i] = 0.0;
     }
+    // field of row r and its first row (batched fields)
+    [[maybe_unused]] auto field_of = [&](long long r) { return r >> a.log2_rows_field; };
     long long t0, t1;
     chunk_of(a.nrows >> LOGTR, t0, t1);
     // Entries k_last >= kz are zero (the filter's band ends before them) and
@@ -396,8 +438,13 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
     // entries below kz) and read as zero.
     const int kz = a.kz;
     auto issue = [&](long long tile, float2* dst, uint64_t* b) {
-        mbar_arrive_expect_tx(b, tile_bytes);
-        bulk_load(dst, a.spec + tile * tile_elems, tile_bytes, b);
+        uint32_t bytes = tile_bytes;
+        if constexpr (OUTDT == kOutBatch) {  // the last tile may hold fewer rows
+            const long long rows = a.nrows_valid - (tile << LOGTR);
+            if (rows < G::TB) bytes = (uint32_t)rows * (uint32_t)(M * sizeof(float2));
+        }
+        mbar_arrive_expect_tx(b, bytes);
+        bulk_load(dst, a.spec + tile * tile_elems, bytes, b);
     };
     load_half_twiddles<LOG2M>(tw, a.tw, t, G::T);
     float2* twi = load_plan_twiddles<LOG2M>(twf, a.tw, t, G::T);
@@ -438,31 +485,57 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
             v[e] = cadd(ep, cmul_i<+1>(op));
         });
         fft<G, +1, true>(v, buf, twi, t);
+        if constexpr (OUTDT == kOutBatch) {
+            for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
+                v[e] = cscale(v[e], row0 + b < a.nrows_valid ? __ldg(a.fscale + field_of(row0 + b)) : 0.0f);
+            });
+        } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cscale(v[e], scale);
-        // v[e] now holds f[2j], f[2j+1] of row b at the forward plan's input positions
+            for (int e = 0; e < E; ++e) v[e] = cscale(v[e], scale);
+        }
+        // v[e] now holds f[2j], f[2j+1] of row b at the forward plan's input positions;
+        // out_pair: its index in pairs of reals in the field and map outputs
+        auto out_pair = [&](int b, int j) -> long long {
+            if constexpr (OUTDT == kOutBatch) {
+                const long long r = row0 + b, f = field_of(r);
+                return (__ldg(a.fout + f) >> 1) + ((r - (f << a.log2_rows_field)) << LOG2M) + j;
+            } else {
+                return (row0 + b) * M + j;
+            }
+        };
+        // rows past the fields (the last tile of a batch) hold stale data: nothing of them is written
+        auto valid = [&](int b) { return OUTDT != kOutBatch || row0 + b < a.nrows_valid; };
         if (a.out_f != nullptr) {
             for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
-                const long long off = (row0 + b) * M + j;  // in pairs of reals
-                if constexpr (OUTDT == 0) {
-                    reinterpret_cast<float2*>(a.out_f)[off] = v[e];
-                } else {
+                if (!valid(b)) return;
+                const long long off = out_pair(b, j);
+                if constexpr (OUTDT == kOutBF16) {
                     reinterpret_cast<__nv_bfloat162*>(a.out_f)[off] = __floats2bfloat162_rn(v[e].x, v[e].y);
+                } else {
+                    reinterpret_cast<float2*>(a.out_f)[off] = v[e];
                 }
             });
         }
         for (int lev = 0; lev < a.nlev; ++lev) {
-            const float th = a.levels[lev];
             float2 u[E];
+            if constexpr (OUTDT == kOutBatch) {  // one level per field
+                for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
+                    const float th = valid(b) ? __ldg(a.flevel + field_of(row0 + b)) : 0.0f;
+                    u[e] = make_float2(v[e].x >= th ? 1.0f : -1.0f, v[e].y >= th ? 1.0f : -1.0f);
+                });
+            } else {
+                const float th = a.levels[lev];
 #pragma unroll
-            for (int e = 0; e < E; ++e)
-                u[e] = make_float2(v[e].x >= th ? 1.0f : -1.0f, v[e].y >= th ? 1.0f : -1.0f);
+                for (int e = 0; e < E; ++e)
+                    u[e] = make_float2(v[e].x >= th ? 1.0f : -1.0f, v[e].y >= th ? 1.0f : -1.0f);
+            }
             if (a.out_maps != nullptr) {
                 for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
+                    if (!valid(b)) return;
                     char2 m;
                     m.x = u[e].x > 0.0f ? (signed char)1 : (signed char)-1;
                     m.y = u[e].y > 0.0f ? (signed char)1 : (signed char)-1;
-                    reinterpret_cast<char2*>(a.out_maps + (long long)lev * a.N)[(row0 + b) * M + j] = m;
+                    reinterpret_cast<char2*>(a.out_maps + (long long)lev * a.N)[out_pair(b, j)] = m;
                 });
             }
             fft<G, -1, false>(u, buf, twf, t);
@@ -472,7 +545,7 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
             float2* dst = a.spec + (long long)lev * a.half;
             for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int k) {
                 const float2 zc = cconj(buf[smem_slot<G>((M - k) & (M - 1), b)]);
-                dst[(row0 + b) * M + k] = r2c_post(u[e], zc, tw[k]);
+                if (valid(b)) dst[(row0 + b) * M + k] = r2c_post(u[e], zc, tw[k]);
             });
         }
         // buf is free once every thread is past its last read: refill it with tile + 2
@@ -668,7 +741,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     using PI = Plan<LOG2L, true>;
     constexpr bool kAcc = MODE != kModePlain;
     constexpr bool kStore = MODE != kModeBins;
-    constexpr bool kFilt = MODE == kModeFilter || MODE == kModeKspace;
+    constexpr bool kFilt = MODE == kModeFilter || MODE == kModeKspace || MODE == kModeFilterBatch;
+    constexpr bool kFiltBatch = MODE == kModeFilterBatch;
     // paired staging needs 16 values per thread (L >= 16); left out of the
     // 512-thread tiles, where the second binning variant costs spills
     constexpr bool kPairable = kAcc && pairable_tile(E, T);
@@ -686,6 +760,24 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     float* fbin = reinterpret_cast<float*>(dbin + nb + 1);  // nb + 1
     float* tab0 = fbin + nb + 1;                          // FILTER: p log2 |kappa_0 / a|, L
     const int t = threadIdx.x;
+    // the filter: the call's, or (batched fields) the current batch's copy in shared memory
+    __shared__ FilterParams sfp;
+    const FilterParams* fpp;
+    if constexpr (kFiltBatch) {
+        fpp = &sfp;
+    } else {
+        fpp = &a.fp;
+    }
+    const FilterParams& fpr = *fpp;
+    // the filter's per-row terms p log2 |kappa_0 / a_0| (separable case)
+    auto fill_tab0 = [&]() {
+        if (!fpr.rotated) {
+            for (int l = t; l < L; l += T) {
+                const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                tab0[l] = plog2_exact(fabsf(x) * fpr.inv_a[0], fpr.p);
+            }
+        }
+    };
 
     long long t0, t1;
     chunk_of(a.ntiles, t0, t1);
@@ -719,14 +811,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
         for (int q = 0; q < NBUF; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
-    if constexpr (kFilt) {
-        if (!a.fp.rotated) {
-            for (int l = t; l < L; l += T) {
-                const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                tab0[l] = plog2_exact(fabsf(x) * a.fp.inv_a[0], a.fp.p);
-            }
-        }
-    }
+    if constexpr (kFilt && !kFiltBatch) fill_tab0();
     if constexpr (kAcc) {
         for (int i = t; i <= nb; i += T) {
             dbin[i] = 0.0;
@@ -750,7 +835,14 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     int since_merge = 0;
     auto flush = [&](long long batch) {
         __syncthreads();
-        double* g = MODE == kModeBins ? a.gbins + batch * nb : a.gbins;
+        double* g = a.gbins;
+        double* gp = a.gP;
+        if constexpr (MODE == kModeBins) {
+            g += a.boff ? a.boff[batch] : batch * nb;
+        } else if constexpr (kFiltBatch) {
+            g += batch * a.acc_stride;
+            gp += batch * a.acc_stride;
+        }
         for (int i = t; i < nb; i += T) {
             const double v = dbin[i] + (double)fbin[i];
             if (v != 0.0) atomicAdd(g + i, v);
@@ -759,7 +851,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
         }
         since_merge = 0;
         if (kFilt && t == 0) {
-            atomicAdd(a.gP, dbin[nb]);
+            atomicAdd(gp, dbin[nb]);
             dbin[nb] = 0.0;
         }
         __syncthreads();
@@ -786,10 +878,18 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
         long long ab, tcol;
         tile_of(ti, ab, tcol);
         const long long c0 = tcol << LOGTB;
-        if constexpr (MODE == kModeBins) {
+        if constexpr (MODE == kModeBins || kFiltBatch) {
             if (ab != cur) {
                 if (cur >= 0) flush(cur);
                 cur = ab;
+                if constexpr (kFiltBatch) {
+                    // the new batch's filter and its per-row terms (flush ended with a
+                    // barrier, so no thread still reads the previous ones)
+                    if (t == 0) sfp = a.fparr[ab];
+                    __syncthreads();
+                    fill_tab0();
+                    __syncthreads();
+                }
             }
         }
         // the bins of the E modes this thread will own after the staging
@@ -861,10 +961,10 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                     nyq_col = a.ndim == 3 && n1 == -(1 << (a.log2n[1] - 1));
                     y = (float)n1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
                     z = a.ndim == 3 ? (float)n2 * __int_as_float((127 + 1 - a.log2n[2]) << 23) : 0.0f;
-                    if (!a.fp.rotated) {  // separable case: the column's terms of the sum
-                        u_col = plog2_exact(fabsf(y) * a.fp.inv_a[1], a.fp.p);
+                    if (!fpr.rotated) {  // separable case: the column's terms of the sum
+                        u_col = plog2_exact(fabsf(y) * fpr.inv_a[1], fpr.p);
                         if (a.ndim == 3) {
-                            const float u2 = plog2_exact(fabsf(z) * a.fp.inv_a[2], a.fp.p);
+                            const float u2 = plog2_exact(fabsf(z) * fpr.inv_a[2], fpr.p);
                             const float m = fmaxf(u_col, u2);
                             u_col = m + log2f(1.0f + exp2f(fminf(u_col, u2) - m));
                         }
@@ -897,21 +997,21 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                         if constexpr (kFilt) {
                             float h = 0.0f;
                             const bool live = !nyq_col && l != L / 2;
-                            if (!a.fp.rotated) {
+                            if (!fpr.rotated) {
                                 // log2 S >= the larger term: from u_zero on A is 0 exactly.
                                 // The warp skips the amplitude when none of its
                                 // lanes needs it (every thread of the CTA runs this loop).
                                 constexpr unsigned kWarp = T >= 32 ? 0xffffffffu : (1u << T) - 1u;
                                 const float t0 = tab0[l];
-                                const bool need = live && fmaxf(t0, u_col) < a.fp.u_zero;
+                                const bool need = live && fmaxf(t0, u_col) < fpr.u_zero;
                                 if (__any_sync(kWarp, need)) {
-                                    const float hv = amplitude_from_log2s(a.fp, log2_sum2(t0, u_col));
+                                    const float hv = amplitude_from_log2s(fpr, log2_sum2(t0, u_col));
                                     h = need ? hv : 0.0f;
                                 }
                             } else if (live) {
                                 const float x =
                                     (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                                h = filter_amplitude(a.fp, x, y, z, a.ndim);
+                                h = filter_amplitude(fpr, x, y, z, a.ndim);
                             }
                             v[e] = cscale(v[e], h);
                         }
@@ -1019,7 +1119,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     if constexpr (kStore) {
         if (t == 0) bulk_wait_all();
     }
-    if constexpr (MODE == kModeBins) {
+    if constexpr (MODE == kModeBins || kFiltBatch) {
         if (cur >= 0) flush(cur);
     } else if constexpr (kFilt) {
         flush(0);

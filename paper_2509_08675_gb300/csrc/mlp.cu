@@ -12,6 +12,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -44,16 +46,21 @@ static_assert(w_off(1) % 8 == 0 && w_off(2) % 8 == 0 && w_off(3) % 8 == 0, "16-b
 using bf16 = __nv_bfloat16;
 
 // Workspace: [X0 bf16 R x 32][Z_l f32 R x 256, X_l bf16 R x 256 for l = 1..3][dY bf16 R x 128][dZ bf16 2 x R x 256]
+//            [split-K partial sums of a weight gradient: kSplits x 256 x 256 f32][of a bias gradient: kSplits x 256]
+constexpr int kSplits = 16;
 struct Ws {
     bf16* X[kLayers];  // X[0] = input, X[l] = output of hidden layer l
     float* Z[kLayers - 1];
     bf16* dY;
     bf16* dZ[2];
+    float* part;
+    float* part_b;
 };
 __host__ __device__ inline long long padded_rows(long long rows) { return (rows + 63) / 64 * 64; }
 inline size_t ws_bytes_for(long long rows) {
     const long long R = padded_rows(rows);
-    return (size_t)R * (kInPad * 2 + 3 * (kHidden * 4 + kHidden * 2) + kOut * 2 + 2 * kHidden * 2);
+    return (size_t)R * (kInPad * 2 + 3 * (kHidden * 4 + kHidden * 2) + kOut * 2 + 2 * kHidden * 2) +
+           (size_t)kSplits * (kHidden * kHidden + kHidden) * 4;
 }
 inline Ws carve(void* ws, long long rows) {
     const long long R = padded_rows(rows);
@@ -72,6 +79,10 @@ inline Ws carve(void* ws, long long rows) {
     w.dZ[0] = reinterpret_cast<bf16*>(p);
     p += R * kHidden * 2;
     w.dZ[1] = reinterpret_cast<bf16*>(p);
+    p += R * kHidden * 2;
+    w.part = reinterpret_cast<float*>(p);
+    p += (size_t)kSplits * kHidden * kHidden * 4;
+    w.part_b = reinterpret_cast<float*>(p);
     return w;
 }
 
@@ -87,7 +98,9 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // M and K are multiples of 64 and 32; N a multiple of 8 (columns >= N are
 // zero-filled on load and not stored).
 // ---------------------------------------------------------------------------
-enum Epi { kEpiHidden = 0, kEpiOut = 1, kEpiGeluBack = 2, kEpiStore = 3 };
+// kEpiPartial: split K over gridDim.z; slice z stores its partial product at
+// outf + z M N (row-major M x N), summed in a fixed order by k_reduce_splits.
+enum Epi { kEpiHidden = 0, kEpiOut = 1, kEpiGeluBack = 2, kEpiStore = 3, kEpiPartial = 4 };
 
 struct GemmArgs {
     const bf16* A;
@@ -147,7 +160,9 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
 
-    for (int k0 = 0; k0 < g.K; k0 += kBK) {
+    const int kslice = g.K / gridDim.z;
+    const int kbeg = blockIdx.z * kslice, kend = kbeg + kslice;
+    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
         // 64 x 32 tiles: 256 chunks of 8 BF16 (16 bytes) each, two per thread
 #pragma unroll
         for (int c = t; c < 256; c += 128) {
@@ -237,6 +252,9 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                     const float2 z = *reinterpret_cast<const float2*>(g.zin + (size_t)m * g.ldz + n);
                     *reinterpret_cast<__nv_bfloat162*>(g.outb + (size_t)m * g.ldb_out + n) =
                         __floats2bfloat162_rn(v0 * gelu_grad(z.x), v1 * gelu_grad(z.y));
+                } else if constexpr (EPI == kEpiPartial) {
+                    *reinterpret_cast<float2*>(g.outf + (size_t)blockIdx.z * g.M * g.N + (size_t)m * g.N + n) =
+                        make_float2(v0, v1);
                 } else {
                     if (m < g.rows_valid) {
                         if (n < g.cols_valid) g.outf[(size_t)m * g.ldo + n] = v0;
@@ -320,13 +338,23 @@ __global__ void k_dy(const float* dy, long long rows, long long R, bf16* out) {
     out[i] = __float2bfloat16_rn(i < rows * kOut ? dy[i] : 0.0f);
 }
 
-// db[n] = sum over rows of dZ[r][n] (FP32), one thread per column.
-__global__ void k_colsum(const bf16* dZ, long long R, int ncol, float* db) {
+// out[i] = sum over z < splits of part[z n + i], in order of z.
+__global__ void k_reduce_splits(const float* part, int splits, long long n, float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += part[(long long)z * n + i];
+    out[i] = s;
+}
+
+// Partial column sums of dZ [R][ncol] over the row slice z (grid.y = slices).
+__global__ void k_colsum_part(const bf16* dZ, long long R, int ncol, float* part) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= ncol) return;
+    const long long rs = R / gridDim.y, r0 = blockIdx.y * rs;
     float s = 0.0f;
-    for (long long r = 0; r < R; ++r) s += __bfloat162float(dZ[r * ncol + n]);
-    db[n] = s;
+    for (long long r = r0; r < r0 + rs; ++r) s += __bfloat162float(dZ[r * ncol + n]);
+    part[(long long)blockIdx.y * ncol + n] = s;
 }
 
 __global__ void k_adam(float* p, float* m, float* v, const float* g, bf16* q, long long n, float lr, float b1,
@@ -422,6 +450,51 @@ __global__ void k_gather(const float* xa, const float* Sa, long long n, long lon
     if (threadIdx.x < kIn) xo[r * kIn + threadIdx.x] = xa[idx * kIn + threadIdx.x];
 }
 
+// Training-step variants that read the step counter from device memory, so a
+// CUDA graph of many steps replays with the schedule advancing on the device.
+struct Sched {
+    float lr, lr_min_frac, b1, b2, eps, wd;
+    long long total;
+};
+
+__global__ void k_gather_dev(const float* xa, const float* Sa, long long n, long long rows, unsigned long long seed,
+                             const long long* step, float* xo, float* So) {
+    const long long r = blockIdx.x;
+    if (r >= rows) return;
+    const unsigned long long s = (unsigned long long)*step;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)s, (uint32_t)(s >> 32), kGatherStream),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const long long idx = (long long)(w.x % (unsigned long long)n);
+    for (int c = threadIdx.x; c < kOut; c += blockDim.x) So[r * kOut + c] = Sa[idx * kOut + c];
+    if (threadIdx.x < kIn) xo[r * kIn + threadIdx.x] = xa[idx * kIn + threadIdx.x];
+}
+
+// Adam at step t = counter + 1 with the learning rate of a half cosine from lr
+// to lr * lr_min_frac over `total` steps.
+__global__ void k_adam_sched(float* p, float* m, float* v, const float* g, bf16* q, long long n, const Sched sc,
+                             const long long* step) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // per-step scalars in FP32 (FP64 is a slow path on this part); the same in every thread
+    const long long s = *step;
+    const float frac = (float)s / (float)sc.total;
+    const float lr = sc.lr * (sc.lr_min_frac + (1.0f - sc.lr_min_frac) * 0.5f * (1.0f + cospif(frac)));
+    const float t = (float)(s + 1);
+    const float c1 = 1.0f - powf(sc.b1, t);
+    const float c2 = 1.0f - powf(sc.b2, t);
+    const float gi = g[i];
+    const float mi = sc.b1 * m[i] + (1.0f - sc.b1) * gi;
+    const float vi = sc.b2 * v[i] + (1.0f - sc.b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + sc.eps) + sc.wd * p[i]);
+    p[i] = pi;
+    if (q) q[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void k_step_set(long long* step, long long value) { *step = value; }
+__global__ void k_step_advance(long long* step) { *step += 1; }
+
 // One warp per row: the design loss and its gradient (4 bins per lane).
 __global__ void k_design_loss(const float* yh, const float* T, const float* mu, const float* sg, long long rows,
                               float lam, float* dy, float* loss) {
@@ -471,8 +544,8 @@ __global__ void k_design_step(float* x, float* m, float* v, const float* dx, lon
 }
 
 template <int AKM, int BKN, int EPI>
-cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
-    const dim3 grid((g.N + kBN - 1) / kBN, g.M / kBM);
+cudaError_t gemm(const GemmArgs& g, cudaStream_t s, int splits = 1) {
+    const dim3 grid((g.N + kBN - 1) / kBN, g.M / kBM, splits);
     k_gemm<AKM, BKN, EPI><<<grid, 128, 0, s>>>(g);
     return cudaGetLastError();
 }
@@ -578,7 +651,11 @@ int hufield_mlp_backward(const float* params, const uint16_t* wq_raw, const floa
     int cur = 0;
     for (int l = kLayers - 1; l >= 0; --l) {
         if (grad) {
-            // dW_l = dZ_l^T X_{l-1}: A stored [R][n_out] = [K][M], B stored [R][n_in] = [K][N]
+            // dW_l = dZ_l^T X_{l-1}: A stored [R][n_out] = [K][M], B stored [R][n_in] = [K][N].
+            // K = R is long and M x N small: the rows are split over `splits` CTAs per
+            // tile, whose partial products are then summed in a fixed order (the
+            // result does not depend on the schedule)
+            const int splits = (int)std::min<long long>(kSplits, R / 64);
             GemmArgs g{};
             g.A = dz;
             g.lda = n_out(l);
@@ -587,12 +664,14 @@ int hufield_mlp_backward(const float* params, const uint16_t* wq_raw, const floa
             g.M = n_out(l);
             g.N = n_in(l);
             g.K = (int)R;
-            g.outf = grad + w_off(l);
-            g.ldo = n_in(l);
-            g.rows_valid = n_out(l);
-            g.cols_valid = n_in(l);
-            HF_MLP_CUDA((gemm<1, 1, kEpiStore>(g, s)));
-            k_colsum<<<blocks(n_out(l), 128), 128, 0, s>>>(dz, R, n_out(l), grad + b_off(l));
+            g.outf = w.part;
+            HF_MLP_CUDA((gemm<1, 1, kEpiPartial>(g, s, splits)));
+            const long long mn = (long long)n_out(l) * n_in(l);
+            k_reduce_splits<<<blocks(mn, 256), 256, 0, s>>>(w.part, splits, mn, grad + w_off(l));
+            HF_MLP_CUDA(cudaGetLastError());
+            k_colsum_part<<<dim3(blocks(n_out(l), 128), splits), 128, 0, s>>>(dz, R, n_out(l), w.part_b);
+            HF_MLP_CUDA(cudaGetLastError());
+            k_reduce_splits<<<blocks(n_out(l), 256), 256, 0, s>>>(w.part_b, splits, n_out(l), grad + b_off(l));
             HF_MLP_CUDA(cudaGetLastError());
         }
         // dA = dZ_l W_l: A stored [R][n_out] = [M][K], B = W_l stored [n_out][n_in] = [K][N]
@@ -663,6 +742,60 @@ int hufield_mlp_adam(float* params, float* m, float* v, const float* grad, uint1
     const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
     k_adam<<<blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(params, m, v, grad, reinterpret_cast<bf16*>(wq), n, lr,
                                                              beta1, beta2, eps, wd, c1, c2);
+    HF_MLP_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
+// Training workspace: [256 B: step counter][xb R x 8][Sb R x 128][y R x 128][dy R x 128][forward workspace]
+static size_t train_ws_bytes(long long rows) {
+    const long long R = padded_rows(rows);
+    return 256 + (size_t)R * 4 * (kIn + 3 * kOut) + ws_bytes_for(rows);
+}
+
+size_t hufield_mlp_train_workspace_bytes(int64_t rows) { return rows < 1 ? 0 : train_ws_bytes(rows); }
+
+int hufield_mlp_train_reset(void* tws, int64_t step, void* stream) {
+    if (!tws || !aligned16(tws) || step < 0) return HUFIELD_ERR_INVALID_ARG;
+    k_step_set<<<1, 1, 0, (cudaStream_t)stream>>>(reinterpret_cast<long long*>(tws), step);
+    HF_MLP_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
+int hufield_mlp_train_step(float* params, uint16_t* wq, float* m, float* v, float* grad, const float* x_all,
+                           const float* S_all, int64_t n, int64_t rows, const float* mu, const float* sigma,
+                           const hufield_mlp_sched* sched, double* loss_sum, void* tws, size_t tws_bytes,
+                           void* stream) {
+    if (!params || !wq || !m || !v || !grad || !x_all || !S_all || !mu || !sigma || !sched || !loss_sum || !tws)
+        return HUFIELD_ERR_INVALID_ARG;
+    if (n < 1 || rows < 1 || rows > (1ll << 24) || !aligned16(tws) || !aligned16(params) || !aligned16(wq))
+        return HUFIELD_ERR_INVALID_ARG;
+    if (!(sched->lr >= 0.0f) || !(sched->lr_min_frac >= 0.0f) || !(sched->beta1 >= 0.0f && sched->beta1 < 1.0f) ||
+        !(sched->beta2 >= 0.0f && sched->beta2 < 1.0f) || !(sched->eps > 0.0f) || sched->total_steps < 1)
+        return HUFIELD_ERR_INVALID_ARG;
+    if (tws_bytes < train_ws_bytes(rows)) return HUFIELD_ERR_WS_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long R = padded_rows(rows);
+    long long* step = reinterpret_cast<long long*>(tws);
+    float* xb = reinterpret_cast<float*>(static_cast<char*>(tws) + 256);
+    float* Sb = xb + R * kIn;
+    float* y = Sb + R * kOut;
+    float* dy = y + R * kOut;
+    void* fws = dy + R * kOut;
+    const size_t fws_bytes = ws_bytes_for(rows);
+    k_gather_dev<<<(unsigned)rows, 128, 0, s>>>(x_all, S_all, n, rows, sched->seed, step, xb, Sb);
+    HF_MLP_CUDA(cudaGetLastError());
+    int rc = hufield_mlp_forward(params, wq, xb, rows, y, fws, fws_bytes, stream);
+    if (rc) return rc;
+    rc = hufield_mlp_deviance(y, Sb, mu, sigma, rows, dy, loss_sum, stream);
+    if (rc) return rc;
+    rc = hufield_mlp_backward(params, wq, dy, rows, grad, nullptr, fws, fws_bytes, stream);
+    if (rc) return rc;
+    const Sched sc{sched->lr, sched->lr_min_frac, sched->beta1, sched->beta2, sched->eps, sched->wd,
+                   (long long)sched->total_steps};
+    k_adam_sched<<<blocks(kParams, 256), 256, 0, s>>>(params, m, v, grad, reinterpret_cast<bf16*>(wq), kParams, sc,
+                                                      step);
+    HF_MLP_CUDA(cudaGetLastError());
+    k_step_advance<<<1, 1, 0, s>>>(step);
     HF_MLP_CUDA(cudaGetLastError());
     return HUFIELD_OK;
 }

@@ -118,6 +118,9 @@ def _load():
     lib.hufield_batch_layout.argtypes = [vp, vp, vp, vp]
     lib.hufield_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.hufield_batch_destroy.argtypes = [vp]
+    lib.hufield_batch_set_params.argtypes = [vp, C.POINTER(_BatchItem), i32, vp]
+    lib.hufield_batch_launches.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.hufield_bins_group_mean.argtypes = [vp, vp, C.c_int64, i32, i32, vp, vp]
     lib.hufield_profile_names.argtypes = []
     lib.hufield_profile_names.restype = C.c_char_p
     return lib
@@ -378,25 +381,34 @@ def hufield_plan_set_bins(plan: Plan, nr: int, ntheta: int = 1):
     _check(_lib.hufield_plan_set_bins(plan.handle, nr, ntheta), "hufield_plan_set_bins")
 
 
+def _batch_items(items):
+    arr = (_BatchItem * len(items))()
+    for i, (shape, filt, seed, field_idx, level, nr) in enumerate(items):
+        shape = tuple(int(v) for v in shape)
+        arr[i].dims = _Dims(len(shape), 0, (C.c_int64 * 3)(*(shape + (1,) * (3 - len(shape)))))
+        arr[i].filt = filt._c()
+        arr[i].seed = seed
+        arr[i].field_idx = field_idx
+        arr[i].level = level
+        arr[i].nr = nr
+    return arr
+
+
 class Batch:
     """hufield_batch: a ragged batch of fields run as one CUDA graph launch.
 
     items: sequence of (shape, Filter, seed, field_idx, level, nr); autotune = True
     tunes every size class's plan (HUFIELD_BATCH_AUTOTUNE); lanes (1..8, 0 = the
-    default of two) sets the lanes per size class (HUFIELD_BATCH_LANES)."""
+    default of two) sets the lanes per size class (HUFIELD_BATCH_LANES); per_item =
+    True runs every item through its own calls instead of batched chunks
+    (HUFIELD_BATCH_PER_ITEM); updatable = True allows set_params
+    (HUFIELD_BATCH_UPDATABLE)."""
 
-    def __init__(self, items, autotune: bool = False, lanes: int = 0):
-        arr = (_BatchItem * len(items))()
-        for i, (shape, filt, seed, field_idx, level, nr) in enumerate(items):
-            shape = tuple(int(v) for v in shape)
-            arr[i].dims = _Dims(len(shape), 0, (C.c_int64 * 3)(*(shape + (1,) * (3 - len(shape)))))
-            arr[i].filt = filt._c()
-            arr[i].seed = seed
-            arr[i].field_idx = field_idx
-            arr[i].level = level
-            arr[i].nr = nr
+    def __init__(self, items, autotune: bool = False, lanes: int = 0, per_item: bool = False,
+                 updatable: bool = False):
+        arr = _batch_items(items)
         h = C.c_void_p()
-        flags = (1 if autotune else 0) | ((int(lanes) & 15) << 8)
+        flags = (1 if autotune else 0) | (2 if per_item else 0) | (4 if updatable else 0) | ((int(lanes) & 15) << 8)
         _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), flags), "hufield_batch_plan")
         self._h = h
         self.n = len(items)
@@ -408,6 +420,17 @@ class Batch:
         self.bin_offset = list(b_off)
         self.total_voxels, self.total_bins, self.ws_bytes = tot[0], tot[1], tot[2]
 
+    def launches(self) -> int:
+        """Kernels one run launches."""
+        v = C.c_int64()
+        _check(_lib.hufield_batch_launches(self._h, C.byref(v)), "hufield_batch_launches")
+        return int(v.value)
+
+    def set_params(self, items, stream=None):
+        """Replace every item's filter, seed, index and level (updatable batches)."""
+        _check(_lib.hufield_batch_set_params(self._h, _batch_items(items), len(items), _stream(stream)),
+               "hufield_batch_set_params")
+
     def close(self):
         if self._h:
             _lib.hufield_batch_destroy(self._h)
@@ -418,6 +441,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def hufield_bins_group_mean(sums, counts, groups: int, group_size: int, nbins: int, out, stream=None):
+    """Mean bins of groups of consecutive items (FP32 out, groups x nbins)."""
+    if sums.numel() < groups * group_size * nbins or counts.numel() < groups * group_size * nbins \
+            or out.numel() < groups * nbins or out.dtype != torch.float32:
+        raise HufieldError(ERR_INVALID_ARG, "hufield_bins_group_mean: buffer sizes")
+    _check(_lib.hufield_bins_group_mean(_ptr(sums), _ptr(counts), groups, group_size, nbins, _ptr(out),
+                                        _stream(stream)), "hufield_bins_group_mean")
 
 
 def hufield_batch_run(batch: Batch, out_f, out_maps, sums_f, counts_f, sums_m, counts_m, ws, stream=None):

@@ -14,6 +14,11 @@ NIN = 8
 NOUT = 128
 
 
+class _Sched(C.Structure):
+    _fields_ = [("lr", C.c_float), ("lr_min_frac", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("wd", C.c_float), ("total_steps", C.c_int64), ("seed", C.c_uint64)]
+
+
 def _declare(lib):
     vp, sz, i32, i64, u32, u64, f32 = C.c_void_p, C.c_size_t, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float
     lib.hufield_mlp_param_count.argtypes = []
@@ -34,6 +39,11 @@ def _declare(lib):
     lib.hufield_mlp_gather.argtypes = [vp, vp, i64, i64, u64, i64, vp, vp, vp]
     lib.hufield_mlp_design_loss.argtypes = [vp, vp, vp, vp, i64, f32, vp, vp, vp]
     lib.hufield_mlp_design_step.argtypes = [vp, vp, vp, vp, i64, u32, i32, f32, vp]
+    lib.hufield_mlp_train_workspace_bytes.argtypes = [i64]
+    lib.hufield_mlp_train_workspace_bytes.restype = sz
+    lib.hufield_mlp_train_reset.argtypes = [vp, i64, vp]
+    lib.hufield_mlp_train_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i64, vp, vp, C.POINTER(_Sched), vp, vp,
+                                           sz, vp]
 
 
 _declare(_lib)
@@ -163,3 +173,31 @@ def design_step(x, m, v, dx, frozen_mask: int, step: int, lr: float, stream=None
     rows = _rows(x, NIN, "hufield_mlp_design_step")
     _check(_lib.hufield_mlp_design_step(_ptr(x), _ptr(m), _ptr(v), _ptr(dx), rows, frozen_mask, step, lr,
                                         _stream(stream)), "hufield_mlp_design_step")
+
+
+class Trainer:
+    """Whole training steps (hufield_mlp_train_step) with the step counter on the
+    device: the same call replays for every step, so steps can be captured in a
+    CUDA graph."""
+
+    def __init__(self, P: Params, x_all, S_all, mu, sigma, rows: int, total_steps: int, lr: float, seed: int,
+                 lr_min_frac=0.02, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0, device="cuda"):
+        self.n = _rows(x_all, NIN, "hufield_mlp_train_step")
+        if S_all.shape != (self.n, NOUT):
+            raise HufieldError(1, "hufield_mlp_train_step: S_all must be [n, 128]")
+        self.P, self.x_all, self.S_all, self.mu, self.sigma = P, x_all, S_all, mu, sigma
+        self.rows = int(rows)
+        self.sched = _Sched(lr, lr_min_frac, beta1, beta2, eps, wd, int(total_steps), int(seed))
+        self.tws = torch.empty(int(_lib.hufield_mlp_train_workspace_bytes(self.rows)), dtype=torch.uint8,
+                               device=device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+
+    def reset(self, step: int = 0, stream=None):
+        _check(_lib.hufield_mlp_train_reset(_ptr(self.tws), int(step), _stream(stream)), "hufield_mlp_train_reset")
+
+    def step(self, stream=None):
+        P = self.P
+        _check(_lib.hufield_mlp_train_step(_ptr(P.p), _ptr(P.wq), _ptr(P.m), _ptr(P.v), _ptr(P.grad),
+                                           _ptr(self.x_all), _ptr(self.S_all), self.n, self.rows, _ptr(self.mu),
+                                           _ptr(self.sigma), C.byref(self.sched), _ptr(self.loss), _ptr(self.tws),
+                                           self.tws.numel(), _stream(stream)), "hufield_mlp_train_step")

@@ -98,10 +98,11 @@ class DataSet:
     wall_s: float = 0.0
 
 
-def generate_dataset(thetas: np.ndarray, seed: int, field0: int = 0, chunk: int = 2000, lanes: int = 8) -> DataSet:
+def generate_dataset(thetas: np.ndarray, seed: int, field0: int = 0, chunk: int = 20000, lanes: int = 2) -> DataSet:
     """One plain-generator field per parameter row (field index field0 + i): the
     map's 128 radial bin means as labels.  Runs as ragged batches of `chunk`
-    items (one CUDA graph launch each, `lanes` lanes side by side)."""
+    items (one CUDA graph launch each); the batch runs its items a chunk of
+    fields at a time through the batched passes, on `lanes` lanes."""
     n = len(thetas)
     S = torch.empty((n, NR), dtype=torch.float32, device="cuda")
     x = torch.empty((n, 8), dtype=torch.float32, device="cuda")
@@ -133,38 +134,67 @@ def generate_dataset(thetas: np.ndarray, seed: int, field0: int = 0, chunk: int 
     return DataSet(thetas, x, S, (gpu_ms + t.ms) / 1e3, wall + t.wall)
 
 
-def plain_spectra(thetas: np.ndarray, seed: int, nseeds: int = VERIFY_SEEDS, field0: int = 0) -> torch.Tensor:
+def plain_spectra(thetas: np.ndarray, seed: int, nseeds: int = VERIFY_SEEDS, field0: int = 0,
+                  timer: "Timer | None" = None) -> torch.Tensor:
     """Mean map spectrum of nseeds plain-generator fields per parameter row
-    (fields field0 .. field0 + nseeds - 1 of `seed`), [n, 128] on the device."""
+    (fields field0 .. field0 + nseeds - 1 of `seed`), [n, 128] on the device: one
+    ragged batch of n x nseeds items (the fields of a row consecutive), run in
+    batched chunks, and the group means of their bins.  `timer` (if given)
+    brackets the device work only; the batch's planning is host work."""
     n = len(thetas)
+    items = [(SHAPE, theta_filter(thetas[i]), seed, field0 + k, float(thetas[i][7]), NR)
+             for i in range(n) for k in range(nseeds)]
+    batch = hf.Batch(items)
     out = torch.empty((n, NR), dtype=torch.float32, device="cuda")
-    plan = _plan()
-    ws = _ens_ws(plan)
-    sf = torch.empty(NR, dtype=torch.float64, device="cuda")
-    cf = torch.empty(NR, dtype=torch.int64, device="cuda")
-    sm = torch.empty(NR, dtype=torch.float64, device="cuda")
-    cm = torch.empty(NR, dtype=torch.int64, device="cuda")
-    for i in range(n):
-        hf.hufield_ensemble(plan, theta_filter(thetas[i]), seed, field0, nseeds, None, (float(thetas[i][7]),), None,
-                            NR, 1, False, sf, cf, sm, cm, ws)
-        mlp.labels(sm, cm, out[i:i + 1])
+    nb = batch.total_bins
+    bins = [torch.empty(nb, dtype=dt, device="cuda") for dt in (torch.float64, torch.int64, torch.float64, torch.int64)]
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+    with (timer if timer is not None else _NoTimer()):
+        hf.hufield_batch_run(batch, None, None, *bins, ws)
+        hf.hufield_bins_group_mean(bins[2], bins[3], n, nseeds, NR, out)
+    torch.cuda.current_stream().synchronize()
+    batch.close()
     return out
 
 
-_PLAN = {}
+class _NoTimer:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
 
 
-def _plan():
-    dev = torch.cuda.current_device()
-    if dev not in _PLAN:
-        p = hf.Plan(SHAPE)
-        hf.hufield_plan_set_bins(p, NR, 1)
-        _PLAN[dev] = (p, p.workspace(1, NR, lanes=2))
-    return _PLAN[dev][0]
+class Evaluator:
+    """The plain generator as a search evaluates it: the mean map spectrum of
+    nseeds fields (common random numbers: the same fields every time) of one
+    parameter row, through an updatable batch whose graph is captured once."""
 
+    def __init__(self, seed: int, nseeds: int, field0: int = 1000):
+        self.seed, self.nseeds, self.field0 = seed, nseeds, field0
+        self.batch = hf.Batch(self._items(draw_thetas(1, 0)[0]), updatable=True)
+        nb = self.batch.total_bins
+        self.bins = [torch.empty(nb, dtype=dt, device="cuda")
+                     for dt in (torch.float64, torch.int64, torch.float64, torch.int64)]
+        self.ws = torch.empty(self.batch.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.out = torch.empty((1, NR), dtype=torch.float32, device="cuda")
+        self.timer = Timer()  # device time of the evaluations' runs
+        self.calls = 0
 
-def _ens_ws(plan):
-    return _PLAN[torch.cuda.current_device()][1]
+    def _items(self, th):
+        f = theta_filter(th)
+        return [(SHAPE, f, self.seed, self.field0 + k, float(th[7]), NR) for k in range(self.nseeds)]
+
+    def __call__(self, th) -> torch.Tensor:
+        self.batch.set_params(self._items(th))
+        with self.timer:
+            hf.hufield_batch_run(self.batch, None, None, *self.bins, self.ws)
+            hf.hufield_bins_group_mean(self.bins[2], self.bins[3], 1, self.nseeds, NR, self.out)
+        self.calls += 1
+        return self.out
+
+    def close(self):
+        self.batch.close()
 
 
 def rel_err(S: np.ndarray, T: np.ndarray) -> np.ndarray:
@@ -194,28 +224,40 @@ class Surrogate:
         mlp.label_stats(data.S[:rows], self.mu, self.sigma)
 
     def train(self, data: DataSet, n_train: int, steps: int, batch: int = 1024, lr: float = 2e-3, seed: int = 1,
-              wd: float = 1e-5, log_every: int = 500) -> TrainLog:
+              wd: float = 1e-5, log_every: int = 500, graph_steps: int = 50) -> TrainLog:
         """Adam on minibatches drawn with replacement from the first n_train rows;
-        the learning rate decays as a half cosine to 2% of lr."""
+        the learning rate decays as a half cosine to 2% of lr.  Whole steps
+        (hufield_mlp_train_step) are captured `graph_steps` at a time into one
+        CUDA graph and replayed; the schedule advances on the device."""
         log = TrainLog()
-        xb = torch.empty((batch, 8), dtype=torch.float32, device="cuda")
-        Sb = torch.empty((batch, NR), dtype=torch.float32, device="cuda")
-        y = torch.empty((batch, NR), dtype=torch.float32, device="cuda")
-        dy = torch.empty_like(y)
-        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-        ws = mlp.Workspace(batch)
-        xa, Sa = data.x[:n_train], data.S[:n_train]
+        tr = mlp.Trainer(self.P, data.x[:n_train], data.S[:n_train], self.mu, self.sigma, batch, steps, lr, seed,
+                         wd=wd)
+        tr.reset(0)
+        graph = None
+        if graph_steps > 1 and steps >= graph_steps:
+            # the capture runs on a side stream; the captured steps do not execute
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                for _ in range(graph_steps):
+                    tr.step()
+            torch.cuda.current_stream().wait_stream(s)
+        done, since = 0, 0
         with Timer() as t:
-            for s in range(steps):
-                mlp.gather(xa, Sa, seed, s, xb, Sb)
-                mlp.forward(self.P, xb, y, ws)
-                mlp.deviance(y, Sb, self.mu, self.sigma, dy, loss)
-                mlp.backward(self.P, dy, ws, self.P.grad, None)
-                rate = lr * (0.02 + 0.98 * 0.5 * (1.0 + math.cos(math.pi * s / steps)))
-                mlp.adam(self.P, rate, wd=wd)
-                if log_every and (s + 1) % log_every == 0:
-                    log.losses.append(float(loss.item()) / (log_every * batch * NR))
-                    loss.zero_()
+            while done < steps:
+                if graph is not None and steps - done >= graph_steps:
+                    graph.replay()
+                    done += graph_steps
+                    since += graph_steps
+                else:
+                    tr.step()
+                    done += 1
+                    since += 1
+                if log_every and since >= log_every:
+                    log.losses.append(float(tr.loss.item()) / (since * batch * NR))
+                    tr.loss.zero_()
+                    since = 0
         log.steps = steps
         log.gpu_s = t.ms / 1e3
         log.wall_s = t.wall
@@ -270,21 +312,23 @@ class Surrogate:
 
 
 def nelder_mead_search(target: np.ndarray, seed: int, nseeds: int = 16, budget: int = 400, tol: float = CONFIRM,
-                       rng_seed: int = 0):
+                       rng_seed: int = 0, evaluator: "Evaluator | None" = None):
     """The plain generator alone: Nelder-Mead over the seven continuous encoded
     parameters (s tried as each of 2, 4, 6 on a sample, the best kept) on the
     relative error of the nseeds-field mean spectrum against the target, from
     the best of a 12-point random sample; stops at `tol` or after `budget`
-    evaluations.  Returns (theta, error, evaluations)."""
+    evaluations.  Each evaluation is one run of an updatable batch of nseeds
+    fields (Evaluator).  Returns (theta, error, evaluations)."""
     rng = np.random.Generator(np.random.Philox(rng_seed))
     evals = [0]
     Tn = np.asarray(target, np.float64)
+    ev = evaluator or Evaluator(seed, nseeds)
 
     def f(xv, s):
         xv = np.clip(xv, -1.0, 1.0)
         th = _decode_host(np.concatenate([xv[:6], [(s - 4.0) / 2.0], xv[6:7]]))
         # common random numbers: every evaluation uses the same nseeds fields
-        S = plain_spectra(th[None, :].astype(np.float32), seed, nseeds, field0=1000)
+        S = ev(th)
         evals[0] += 1
         return float(rel_err(S.cpu().numpy(), Tn)[0]), th
 

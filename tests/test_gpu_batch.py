@@ -55,6 +55,43 @@ def test_batch_matches_oracle_and_replays(hf, lanes):
     batch.close()
 
 
+@pytest.mark.parametrize("chunk_bytes", [None, 300000])
+def test_batched_chunks_equal_per_item_calls(hf, monkeypatch, chunk_bytes):
+    # a size class runs its items a chunk at a time through the batched passes; with a
+    # small chunk budget (a few fields per chunk: 2D 64^2 spectra are 16 KB, 3D 32^3
+    # 128 KB) every lane runs several chunks.  Fields equal the item-by-item path's to
+    # FP32 rounding (the row passes may take another tile width, whose code the
+    # compiler contracts differently), maps except at sites within that rounding of
+    # the level, bins to rounding.
+    if chunk_bytes:
+        monkeypatch.setenv("HUFIELD_BATCH_CHUNK_BYTES", str(chunk_bytes))
+    items, _ = _items(hf, 40, 3)
+    outs = []
+    for per_item in (False, True):
+        batch = hf.Batch(items, per_item=per_item)
+        out_f = dev_zeros(batch.total_voxels, torch.float32)
+        maps = dev_zeros(batch.total_voxels, torch.int8)
+        bins = [dev_zeros(batch.total_bins, dt) for dt in (torch.float64, torch.int64, torch.float64, torch.int64)]
+        ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+        hf.hufield_batch_run(batch, out_f, maps, *bins, ws)
+        torch.cuda.synchronize()
+        assert hf.hufield_workspace_status(ws) == hf.OK
+        outs.append((np_(out_f), np_(maps), [np_(b) for b in bins]))
+        batch.close()
+    (fa, ma, ba), (fb, mb, bb) = outs
+    np.testing.assert_allclose(fa, fb, rtol=0, atol=2e-6 * float(np.abs(fb).max()))
+    level = np.zeros_like(fa)
+    for i, (shape, _, _, _, lv, _) in enumerate(items):
+        o = batch.f_offset[i]
+        level[o:o + int(np.prod(shape))] = lv
+    diff = ma != mb
+    assert not np.any(diff & (np.abs(fb - level) > 1e-5)), "sign differs away from the level"
+    np.testing.assert_array_equal(ba[1], bb[1])
+    np.testing.assert_array_equal(ba[3], bb[3])
+    for x, y in zip(ba[::2], bb[::2]):
+        np.testing.assert_allclose(x, y, rtol=1e-5, atol=1e-9 * float(np.abs(y).max()) + 8.0 * int(diff.sum()))
+
+
 def test_batch_rejects_bad_lane_counts(hf):
     items, _ = _items(hf, 3, 2)
     with pytest.raises(hf.HufieldError) as e:

@@ -253,3 +253,56 @@ def test_training_step_matches_oracle_and_learns(M):
     # the deviance's floor is sum(log S_mean + 1) per element; compare the excess
     floor = float(np.sum(np.log(mean) + 1.0))
     assert (last - floor) < 0.5 * (first - floor), (first, last, floor)
+
+
+def test_train_step_is_the_explicit_step_and_replays_in_a_graph(M):
+    # hufield_mlp_train_step (gather, forward, deviance, backward, scheduled Adam, counter
+    # advance) against the same calls made one by one, and a CUDA graph of steps
+    # against steps called directly: the graph replays bit for bit
+    n, rows, total = 3000, 256, 40
+    r = np.random.default_rng(21)
+    xa = torch.from_numpy(inputs.mlp_rows(n, 22)).cuda()
+    Sa = torch.from_numpy(r.exponential(1.0, (n, 128)).astype(np.float32)).cuda()
+    mu = torch.zeros(128, device="cuda")
+    sg = torch.ones(128, device="cuda")
+    flat = torch.from_numpy(inputs.mlp_params(23)).cuda()
+    A, B, C = M.Params(0), M.Params(0), M.Params(0)
+    for P in (A, B, C):
+        P.load(flat)
+    lr, lo = 1e-3, 0.1
+    tr = M.Trainer(A, xa, Sa, mu, sg, rows, total, lr, seed=9, lr_min_frac=lo)
+    tr.reset(0)
+    tr.step()
+    # the same step by hand: the learning rate at step 0 is lr, Adam's t is 1
+    xb = torch.empty((rows, 8), device="cuda")
+    Sb = torch.empty((rows, 128), device="cuda")
+    y = torch.empty((rows, 128), device="cuda")
+    dy = torch.empty_like(y)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = M.Workspace(rows)
+    M.gather(xa, Sa, 9, 0, xb, Sb)
+    M.forward(B, xb, y, ws)
+    M.deviance(y, Sb, mu, sg, dy, loss)
+    M.backward(B, dy, ws, B.grad, None)
+    M.adam(B, lr)
+    torch.cuda.synchronize()
+    assert torch.equal(A.grad, B.grad)
+    assert float((A.p - B.p).abs().max()) < 1e-6 * max(1.0, float(B.p.abs().max()))
+    assert abs(float(tr.loss.item()) - float(loss.item())) < 1e-9 * abs(float(loss.item()))
+    # ten more steps directly, against a graph of ten steps replayed once on a twin
+    trC = M.Trainer(C, xa, Sa, mu, sg, rows, total, lr, seed=9, lr_min_frac=lo)
+    trC.reset(0)
+    trC.step()
+    for _ in range(10):
+        tr.step()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(10):
+            trC.step()
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(A.p, C.p) and torch.equal(A.m, C.m) and torch.equal(A.v, C.v)
+    assert torch.equal(A.wq, C.wq)
