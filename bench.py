@@ -415,6 +415,11 @@ def run_surrogate(args):
     cfg = dict(SURROGATE)
     if args.fields > 0:
         cfg["fields"] = args.fields
+    # smaller runs (profiling): fewer training steps, designs or searched targets
+    for key in ("train_steps", "designs", "plain_sample"):
+        v = getattr(args, key)
+        if v > 0:
+            cfg["steps" if key == "train_steps" else key] = v
     n = cfg["fields"]
     ntr = int(cfg["train_frac"] * n)
     clocks = ClockSampler()
@@ -503,6 +508,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparator (context line)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--train-steps", type=int, default=0, help="surrogate: training steps (default 20000)")
+    ap.add_argument("--designs", type=int, default=0, help="surrogate: inverse designs (default 500)")
+    ap.add_argument("--plain-sample", type=int, default=0, help="surrogate: targets searched by the plain generator")
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
     ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
     ap.add_argument("--noise", default="real", choices=["real", "kspace"],

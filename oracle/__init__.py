@@ -111,6 +111,7 @@ def _lib():
             lib.or_bin_of.argtypes = [C.c_int, i64p, i64p, C.c_int, C.c_int, i64p, i64p]
             lib.or_bin_of.restype = C.c_int
             lib.or_spectrum_bins.argtypes = [C.c_int, i64p, f64p, C.c_int, C.c_int, f64p, i64p]
+            lib.or_half_bins.argtypes = [C.c_int, i64p, C.c_int, C.c_int, np.ctypeslib.ndpointer(np.int32, flags="C")]
             lib.or_spectrum_modes.argtypes = [C.c_int, i64p, f64p, f64p]
             lib.or_pipeline.argtypes = [C.c_int, i64p, fp, C.c_uint64, C.c_uint32, C.c_double, f64p, C.c_int,
                                         C.c_int, C.c_int, f64p, i8p, f64p, i64p, f64p, i64p]
@@ -235,6 +236,13 @@ def angle_table(ntheta: int):
 def bin_of(shape, idx, nr: int, ntheta: int = 1) -> int:
     c, s = angle_table(ntheta)
     return int(_lib().or_bin_of(len(shape), _dims(shape), _dims(idx), nr, ntheta, c, s))
+
+
+def half_bins(shape, nr: int, ntheta: int = 1) -> np.ndarray:
+    """Bin of every mode of the stored half spectrum [..][n_last/2] (-1: dropped)."""
+    out = np.zeros(int(np.prod(shape)) // 2, np.int32)
+    _lib().or_half_bins(len(shape), _dims(shape), nr, ntheta, out)
+    return out
 
 
 def spectrum_bins(y: np.ndarray, nr: int, ntheta: int = 1):

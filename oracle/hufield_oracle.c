@@ -493,6 +493,30 @@ int or_bin_of(int ndim, const int64_t *n, const int64_t *idx, int nr, int ntheta
     return (int)b * ntheta + sector;
 }
 
+/* Bin (or_bin_of) of every mode of the stored half spectrum: the axes before
+ * the last in FFT order (index i is the signed i < n/2 ? i : i - n), the last
+ * k = 0 .. n_last/2 - 1; -1 where |kappa| >= 1.  out has N/2 entries. */
+void or_half_bins(int ndim, const int64_t *n, int nr, int ntheta, int32_t *out) {
+    int64_t C[64], S[64];
+    or_angle_table(ntheta, C, S);
+    const int64_t M = n[ndim - 1] / 2;
+    int64_t count = M;
+    for (int d = 0; d < ndim - 1; ++d) count *= n[d];
+#pragma omp parallel for schedule(static)
+    for (int64_t lin = 0; lin < count; ++lin) {
+        int64_t idx[3] = {0, 0, 0};
+        int64_t rem = lin;
+        idx[ndim - 1] = rem % M;
+        rem /= M;
+        for (int d = ndim - 2; d >= 0; --d) {
+            const int64_t i = rem % n[d];
+            rem /= n[d];
+            idx[d] = i < n[d] / 2 ? i : i - n[d];
+        }
+        out[lin] = or_bin_of(ndim, n, idx, nr, ntheta, C, S);
+    }
+}
+
 /* S(n) = |DFT(y)(n)|^2 / N over the full lattice, summed per bin; counts
  * are the number of lattice modes per bin.  Bins are overwritten. */
 void or_spectrum_bins(int ndim, const int64_t *n, const double *y, int nr, int ntheta,

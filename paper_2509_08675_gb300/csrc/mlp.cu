@@ -141,13 +141,26 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 constexpr int kBM = 64, kBN = 64, kBK = 32, kPadE = 8;
+// K chunks in flight: chunk k + kStages - 1 loads (cp.async) while chunk k is multiplied
+constexpr int kStages = 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    // 16 bytes global -> shared, bypassing L1; zero-filled (nothing read) when !valid
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+                 "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
 
 template <int AKM, int BKN, int EPI>
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     constexpr int AR = AKM ? kBK : kBM, AC = (AKM ? kBM : kBK) + kPadE;
     constexpr int BR = BKN ? kBK : kBN, BC = (BKN ? kBN : kBK) + kPadE;
-    __shared__ __align__(16) bf16 As[AR][AC];
-    __shared__ __align__(16) bf16 Bs[BR][BC];
+    __shared__ __align__(16) bf16 As[kStages][AR][AC];
+    __shared__ __align__(16) bf16 Bs[kStages][BR][BC];
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
@@ -161,33 +174,43 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
 
     const int kslice = g.K / gridDim.z;
-    const int kbeg = blockIdx.z * kslice, kend = kbeg + kslice;
-    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
-        // 64 x 32 tiles: 256 chunks of 8 BF16 (16 bytes) each, two per thread
+    const int kbeg = blockIdx.z * kslice;
+    const int nk = kslice / kBK;
+    // chunk c of this CTA's K slice into stage st: 64 x 32 tiles, 256 pieces of
+    // 8 BF16 (16 bytes), two per thread; B columns >= N are zero-filled
+    auto load = [&](int c, int st) {
+        const int k0 = kbeg + c * kBK;
 #pragma unroll
-        for (int c = t; c < 256; c += 128) {
+        for (int i = t; i < 256; i += 128) {
             if constexpr (!AKM) {
-                const int r = c >> 2, cc = (c & 3) * 8;
-                *reinterpret_cast<uint4*>(&As[r][cc]) =
-                    *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + cc);
+                const int r = i >> 2, cc = (i & 3) * 8;
+                cp_async16(&As[st][r][cc], g.A + (size_t)(m0 + r) * g.lda + k0 + cc, true);
             } else {
-                const int r = c >> 3, cc = (c & 7) * 8;
-                *reinterpret_cast<uint4*>(&As[r][cc]) =
-                    *reinterpret_cast<const uint4*>(g.A + (size_t)(k0 + r) * g.lda + m0 + cc);
+                const int r = i >> 3, cc = (i & 7) * 8;
+                cp_async16(&As[st][r][cc], g.A + (size_t)(k0 + r) * g.lda + m0 + cc, true);
             }
             if constexpr (!BKN) {
-                const int r = c >> 2, cc = (c & 3) * 8;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (n0 + r < g.N) v = *reinterpret_cast<const uint4*>(g.B + (size_t)(n0 + r) * g.ldb + k0 + cc);
-                *reinterpret_cast<uint4*>(&Bs[r][cc]) = v;
+                const int r = i >> 2, cc = (i & 3) * 8;
+                const bool ok = n0 + r < g.N;
+                cp_async16(&Bs[st][r][cc], ok ? g.B + (size_t)(n0 + r) * g.ldb + k0 + cc : g.B, ok);
             } else {
-                const int r = c >> 3, cc = (c & 7) * 8;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (n0 + cc < g.N) v = *reinterpret_cast<const uint4*>(g.B + (size_t)(k0 + r) * g.ldb + n0 + cc);
-                *reinterpret_cast<uint4*>(&Bs[r][cc]) = v;
+                const int r = i >> 3, cc = (i & 7) * 8;
+                const bool ok = n0 + cc < g.N;
+                cp_async16(&Bs[st][r][cc], ok ? g.B + (size_t)(k0 + r) * g.ldb + n0 + cc : g.B, ok);
             }
         }
-        __syncthreads();
+    };
+#pragma unroll
+    for (int c = 0; c < kStages - 1; ++c) {
+        if (c < nk) load(c, c);
+        cp_async_commit();  // one group per chunk, empty past the slice, so the counts stay uniform
+    }
+    for (int c = 0; c < nk; ++c) {
+        cp_async_wait<kStages - 2>();  // chunk c has landed (this thread's part)
+        __syncthreads();               // ... every thread's; and stage (c - 1) % kStages is free
+        if (c + kStages - 1 < nk) load(c + kStages - 1, (c + kStages - 1) % kStages);
+        cp_async_commit();
+        const int st = c % kStages;
 #pragma unroll
         for (int kk = 0; kk < kBK; kk += 16) {
             uint32_t a[2][4], b[4][2];
@@ -196,10 +219,10 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                 const int mb = wm + mi * 16;
                 if constexpr (!AKM) {
                     // matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15): lane gives row lane & 15, k (lane >> 4) 8
-                    ldsm_x4(a[mi], &As[mb + (lane & 15)][kk + (lane >> 4) * 8]);
+                    ldsm_x4(a[mi], &As[st][mb + (lane & 15)][kk + (lane >> 4) * 8]);
                 } else {
                     // stored [k][m]: transposed 8x8 blocks (k 0-7, m 0-7), (k 0-7, m 8-15), (k 8-15, m 0-7), ...
-                    ldsm_x4_t(a[mi], &As[kk + ((q >> 1) << 3) + r8][mb + ((q & 1) << 3)]);
+                    ldsm_x4_t(a[mi], &As[st][kk + ((q >> 1) << 3) + r8][mb + ((q & 1) << 3)]);
                 }
             }
 #pragma unroll
@@ -208,10 +231,10 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                 uint32_t r[4];
                 if constexpr (!BKN) {
                     // stored [n][k]: (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
-                    ldsm_x4(r, &Bs[nb + ((q >> 1) << 3) + r8][kk + ((q & 1) << 3)]);
+                    ldsm_x4(r, &Bs[st][nb + ((q >> 1) << 3) + r8][kk + ((q & 1) << 3)]);
                 } else {
                     // stored [k][n]: transposed (k 0-7, n 0-7), (k 8-15, n 0-7), (k 0-7, n 8-15), (k 8-15, n 8-15)
-                    ldsm_x4_t(r, &Bs[kk + ((q & 1) << 3) + r8][nb + ((q >> 1) << 3)]);
+                    ldsm_x4_t(r, &Bs[st][kk + ((q & 1) << 3) + r8][nb + ((q >> 1) << 3)]);
                 }
                 b[2 * nj][0] = r[0];
                 b[2 * nj][1] = r[1];
@@ -223,8 +246,8 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
 #pragma unroll
                 for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni][0], b[ni][1]);
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
 
     // epilogue: accumulator (mi, ni, e) is row wm + 16 mi + (lane >> 2) + 8 (e >> 1),
     // column wn + 8 ni + 2 (lane & 3) + (e & 1)

@@ -151,3 +151,40 @@ def test_bf16_storage_error_512(hf):
     assert 1.3e-3 < rel < 2.0e-3, rel
     # round to nearest: every stored value within half an ulp of BF16
     assert float((d.abs() / f32.double().abs().clamp_min(1e-30)).max()) <= 2.0 ** -8
+
+
+def test_ensemble_bin_sums_against_fp64_accumulation(hf):
+    # The binning passes gather each CTA's sums in FP32 over up to four tiles before
+    # folding them into FP64.  Against an FP64 sum of the same per-mode map spectra
+    # (hufield_spectrum_modes of the stored maps, binned on the host by the oracle's
+    # bin of every stored mode, weight 2 off the k_last = 0 plane), the 4096^2
+    # ensemble's 64 x 36 map bins agree far inside the 1e-4 gate.
+    shape, levels, nr, nt, nf = (4096, 4096), (0.0, 0.5, -0.5), 64, 36, 4
+    nb, nlev = nr * nt, len(levels)
+    gf, _ = filters(hf, **inputs.filter_kwargs(inputs.C1))
+    plan = hf.Plan(shape)
+    hf.hufield_plan_set_bins(plan, nr, nt)
+    ws = plan.workspace(nlev, nb, lanes=2)
+    out_f = torch.empty((nf,) + shape, dtype=torch.float32, device="cuda")
+    maps = torch.empty((nf, nlev) + shape, dtype=torch.int8, device="cuda")
+    sf, cf = dev_zeros(nb, torch.float64), dev_zeros(nb, torch.int64)
+    sm, cm = dev_zeros(nlev * nb, torch.float64), dev_zeros(nlev * nb, torch.int64)
+    hf.hufield_ensemble(plan, gf, SEED, 0, nf, out_f, levels, maps, nr, nt, False, sf, cf, sm, cm, ws)
+    torch.cuda.synchronize()
+    bins = oracle.half_bins(shape, nr, nt)
+    keep = bins >= 0
+    M = shape[-1] // 2
+    w = np.where(np.arange(bins.size) % M == 0, 1.0, 2.0)
+    ref = np.zeros((nlev, nb))
+    S = torch.empty(bins.size, dtype=torch.float32, device="cuda")
+    ws1 = plan.workspace(1, 0)
+    for e in range(nf):
+        for t in range(nlev):
+            hf.hufield_spectrum_modes(plan, maps[e, t], S, ws1)
+            s = np_(S).astype(np.float64) * w
+            ref[t] += np.bincount(bins[keep], weights=s[keep], minlength=nb)
+    got = np_(sm).reshape(nlev, nb)
+    sig = ref > 1e-9 * ref.max()
+    rel = float(np.max(np.abs(got - ref)[sig] / ref[sig]))
+    print(f"\n4096^2 x {nf} map bins against FP64 sums of the per-mode spectra: largest relative difference {rel:.2e}")
+    assert rel < 2e-5

@@ -281,3 +281,12 @@ def test_filter_without_power_gives_a_zero_field():
     assert np.all(r["f"] == 0.0)
     assert np.all(r["maps"][0] == 1) and np.all(r["maps"][1] == -1)
     assert np.all(r["sums_f"] == 0.0)
+
+
+@pytest.mark.parametrize("shape,nr,nt", [((8, 16), 4, 3), ((16, 8), 8, 1), ((4, 8, 8), 4, 1)])
+def test_half_bins_are_bin_of_each_stored_mode(shape, nr, nt):
+    # the stored half spectrum [..][n_last/2], axes before the last in FFT order
+    got = oracle.half_bins(shape, nr, nt).reshape(shape[:-1] + (shape[-1] // 2,))
+    for pos in itertools.product(*[range(n) for n in shape[:-1]], range(shape[-1] // 2)):
+        idx = [signed(pos[d], shape[d]) for d in range(len(shape) - 1)] + [pos[-1]]
+        assert got[pos] == oracle.bin_of(shape, idx, nr, nt)
