@@ -47,8 +47,8 @@ METRIC = "voxels/s for gen+threshold+S(k)"
 # dominant pass from an ncu capture of the current kernels, keyed by
 # (workload, pass); None until captured.
 TRAFFIC = {
-    ("ensemble-2d-4096", "cols_bins"): 320.7e6,  # k_cols<12, 1, 2, -1>, 3 maps of 4096^2, per launch
-    ("3d-512", "r2c"): 477.1e6,  # k_r2c<8, 4, 0>, 512^3
+    ("ensemble-2d-4096", "cols_bins"): 318.4e6,  # k_cols<12, 1, 2, -1>, 3 maps of 4096^2, per launch
+    ("3d-512", "r2c"): 476.6e6,  # k_r2c<8, 4, 0>, 512^3
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 E2E_CHUNK = 8  # fields per ensemble call in the end-to-end leg
@@ -133,7 +133,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms during the timed region."""
+    """nvidia-smi sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -147,7 +147,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
