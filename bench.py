@@ -54,11 +54,12 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 E2E_CHUNK = 8  # fields per ensemble call in the end-to-end leg
 
 
-def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0):
+def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0, map_bytes=1.0):
     """Bytes each pass kind must move per launch (one field), by the pass plan:
     r2c writes the half spectrum (4 B/voxel); a strided pass reads and writes it
     (8 B/voxel per spectrum; the filter pass of k-space noise only writes it);
-    c2r reads it, writes the field, nlev sign maps and nlev map spectra; the
+    c2r reads it, writes the field, nlev sign maps (map_bytes per site: 1 for
+    int8, 1/8 for one-bit maps) and nlev map spectra; the
     bins pass reads the nlev map spectra.  Only the columns below the filter's
     band edge hold nonzero data after the filter (a fraction `live` = kz /
     (n_last / 2) of the half spectrum): the axis-1 forward, the filter pass and
@@ -72,7 +73,7 @@ def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0):
         "cols_mid_fwd": 2 * h * live,
         "cols_filter": (1 if kspace else 2) * h * live,
         "cols_mid_inv": 2 * h * live,
-        "c2r": h * live + field_bytes * N + nlev * N + nlev * h,
+        "c2r": h * live + field_bytes * N + nlev * N * map_bytes + nlev * h,
         "cols_mid_maps": 2 * h * nlev,
         "cols_bins": h * nlev,
         "counts": 0,
@@ -91,9 +92,9 @@ def overhead_bytes(shape, nlev, live=1.0):
     return {"cols_filter": tab * live, "cols_bins": tab * nlev, "counts": tab}
 
 
-def field_bytes(shape, nlev, live, kspace=False, out_bytes=4):
+def field_bytes(shape, nlev, live, kspace=False, out_bytes=4, map_bytes=1.0):
     """Algorithmic bytes of one field's pipeline (the passes it runs, bin table cached)."""
-    algo = algorithmic_bytes(shape, nlev, out_bytes, kspace, live)
+    algo = algorithmic_bytes(shape, nlev, out_bytes, kspace, live, map_bytes)
     keys = ["cols_filter", "c2r"] + (["cols_bins"] if nlev else [])
     keys += [] if kspace else ["r2c"]
     if len(shape) == 3:
@@ -513,6 +514,8 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=0, help="surrogate: targets searched by the plain generator")
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
     ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
+    ap.add_argument("--maps", default="bits", choices=["bits", "i8"],
+                    help="sign-map storage: one bit per site (default) or one int8 per site")
     ap.add_argument("--noise", default="real", choices=["real", "kspace"],
                     help="white noise in real space (forward FFT) or drawn as k-space coefficients")
     args = ap.parse_args()
@@ -578,7 +581,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "shape": list(shape), "fields_per_step": wl["nfields"],
                            "levels": list(wl["levels"]), "bins": [wl["nr"], wl["ntheta"]],
-                           "noise": args.noise, "l2": "flushed between timed steps",
+                           "noise": args.noise, "maps": args.maps, "l2": "flushed between timed steps",
                            "parallelism": f"replicas x{world}", "lanes": res["lanes"]},
                 "ms_per_step_one_lane": res["ms_per_step_one_lane"],
                 "roofline": res["roofline"],
@@ -611,11 +614,16 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"], supp=wl["supp"])
     plan = hf.Plan(shape, profile=True, kspace=args.noise == "kspace")
     hf.hufield_plan_set_bins(plan, nr, nt)  # plan-time bin table and counts, as a production caller would
+    bits = args.maps == "bits"
+    hf.hufield_plan_set_maps_format(plan, hf.MAPS_BITS if bits else hf.MAPS_I8)
     ws = plan.workspace(nlev, nb, lanes=2 if nf >= 2 else 1)
     slice_bytes = (hf.hufield_workspace_bytes(plan, nlev, nb) + 255) & ~255
     ws_one = ws[:slice_bytes]  # the first slice alone: one lane
     out_f = torch.empty((nf,) + tuple(shape), dtype=fdt, device="cuda")
-    maps = torch.empty((nf, nlev) + tuple(shape), dtype=torch.int8, device="cuda")
+    if bits:  # one bit per site, 32-bit words
+        maps = torch.empty((nf, nlev, N // 32), dtype=torch.int32, device="cuda")
+    else:
+        maps = torch.empty((nf, nlev) + tuple(shape), dtype=torch.int8, device="cuda")
     sf = torch.zeros(nb, dtype=torch.float64, device="cuda")
     cf = torch.zeros(nb, dtype=torch.int64, device="cuda")
     sm = torch.zeros(nlev * nb, dtype=torch.float64, device="cuda")
@@ -679,7 +687,8 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
 
     # roofline of the dominant pass (per-launch CUDA-event times of the one-lane steps)
     live = band_live(hf, plan, filt, shape)
-    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2, args.noise == "kspace", live)
+    algo = algorithmic_bytes(shape, nlev, 4 if args.dtype == "f32" else 2, args.noise == "kspace", live,
+                             0.125 if bits else 1.0)
     peak, peak_kind = peaks()
     passes = {}
     for k, (ms, cnt) in prof.items():
@@ -831,12 +840,13 @@ def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws
         times.append(max_over_ranks(dist, time.perf_counter() - t0, "cuda"))
     hf.hufield_profile_read(plan)
     dt = sorted(times)[len(times) // 2]
-    d2h = (out_f.numel() * out_f.element_size() + maps.numel() + sum(t.numel() * t.element_size()
-                                                                      for t in (sf, cf, sm, cm)))
+    d2h = (out_f.numel() * out_f.element_size() + maps.numel() * maps.element_size()
+           + sum(t.numel() * t.element_size() for t in (sf, cf, sm, cm)))
     return {"value": world * nf * N / dt, "unit": "voxels/s", "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": int(d2h), "steps": steps, "step_ms_median": round(1e3 * dt, 3),
             "step_ms_min": round(1e3 * min(times), 3), "step_ms_max": round(1e3 * max(times), 3),
-            "note": "inputs are seeds and filter parameters passed by value; every output copied to pinned host"}
+            "note": "inputs are seeds and filter parameters passed by value; every output (field, sign maps in "
+                    "the plan's format, bins) copied to pinned host"}
 
 
 if __name__ == "__main__":

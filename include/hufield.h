@@ -168,6 +168,21 @@ int hufield_plan_tuning(const hufield_plan *plan, int32_t out[5]);
 int hufield_plan_set_tile(hufield_plan *plan, int32_t tile);
 int hufield_plan_tile(const hufield_plan *plan, int32_t *tile);
 
+/* Storage of the sign maps (the +-1 maps of Sec. II.B, last paragraph) that
+ * hufield_threshold, hufield_pipeline and hufield_ensemble write through this
+ * plan.  HUFIELD_MAPS_I8 (the default): one int8 per site, +1 or -1, a map of
+ * N sites at out_maps + t * N.  HUFIELD_MAPS_BITS: one bit per site, site i of
+ * a map at bit (i mod 32) of the 32-bit little-endian word i / 32, 1 for +1
+ * and 0 for -1; a map takes N / 8 bytes, map t of field e of an ensemble at
+ * byte (e * nlev + t) * N / 8 (out_maps 16-byte aligned as for int8).  The
+ * same maps either way, 8 times fewer bytes to store or copy; the maps'
+ * spectra and the batch calls (int8 maps) are unaffected.  Returns
+ * HUFIELD_ERR_INVALID_ARG for another format; hufield_plan_maps_format reads
+ * the setting. */
+enum hufield_maps_format { HUFIELD_MAPS_I8 = 0, HUFIELD_MAPS_BITS = 1 };
+int hufield_plan_set_maps_format(hufield_plan *plan, int32_t format);
+int hufield_plan_maps_format(const hufield_plan *plan, int32_t *format);
+
 /* Bytes of device workspace a call needs: nlev sign maps (0 for
  * hufield_generate, 1 for hufield_spectrum) and nbins = nr * ntheta bins
  * (0 when no spectrum is taken).  Returns 0 for invalid arguments. */
@@ -192,7 +207,8 @@ int hufield_generate(hufield_plan *plan, const hufield_filter *filt, uint64_t se
                      int32_t out_dtype, void *out_f, void *ws, size_t ws_bytes, void *stream);
 
 /* Sign maps of a field (Sec. II.B, last paragraph): out_maps[t * N + i] =
- * f[i] >= levels[t] ? +1 : -1 for t < nlev (1 <= nlev <= 8).  dtype of f is
+ * f[i] >= levels[t] ? +1 : -1 for t < nlev (1 <= nlev <= 8), stored as the
+ * plan's maps format says (hufield_plan_set_maps_format).  dtype of f is
  * HUFIELD_F32 or HUFIELD_BF16. */
 int hufield_threshold(hufield_plan *plan, const void *f, int32_t dtype, const float *levels, int32_t nlev,
                       int8_t *out_maps, void *stream);
@@ -219,6 +235,7 @@ int hufield_pipeline(hufield_plan *plan, const hufield_filter *filt, uint64_t se
 /* Ensemble: hufield_pipeline for field_idx = field0 .. field0 + nfields - 1
  * with the same seed and filter, bins accumulated over the ensemble.  Field e
  * is written at out_f + e * N elements and its maps at out_maps + e * nlev * N
+ * (bytes; e * nlev * N / 8 with one-bit maps, hufield_plan_set_maps_format)
  * (either may be NULL).  accumulate applies to the first field.  A workspace
  * of two slices, ws_bytes >= 2 * W with W = hufield_workspace_bytes(plan,
  * nlev, nr * ntheta) rounded up to a multiple of 256, runs the odd fields on

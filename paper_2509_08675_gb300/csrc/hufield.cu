@@ -70,6 +70,26 @@ struct Levels {
     float t[kMaxLevels];
 };
 
+// Sign maps one bit per site: warp-strided 32-site words, each lane one site.
+template <int DT>
+__global__ void k_threshold_bits(long long nwords, const void* f, Levels lv, int nlev, long long N, uint32_t* maps) {
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < nwords; w += nwarps) {
+        const long long i = (w << 5) + lane;
+        float x;
+        if constexpr (DT == 0) {
+            x = __ldg(reinterpret_cast<const float*>(f) + i);
+        } else {
+            x = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(f)[i]);
+        }
+        for (int l = 0; l < nlev; ++l) {
+            const uint32_t m = __ballot_sync(0xffffffffu, x >= lv.t[l]);
+            if (lane == 0) maps[(long long)l * (N >> 5) + w] = m;
+        }
+    }
+}
+
 template <int DT>
 __global__ void k_threshold(long long nblk, const void* f, Levels lv, int nlev, long long N, char4* maps) {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nblk;
@@ -288,6 +308,7 @@ struct hufield_plan {
     // 1 the wide tile wherever the columns fill it, 2 the two-column tile
     int col_tile = 0;
     int cache_logtb = -1;  // axis-0 tile width the cached bin table was built for
+    int maps_format = HUFIELD_MAPS_I8;  // sign maps: one int8 or one bit per site
     // second lane of ensembles (odd fields) and its fork/join events
     cudaStream_t lane = nullptr;
     cudaEvent_t lane_fork = nullptr, lane_join = nullptr;
@@ -840,6 +861,7 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     ca.N = p->N;
     ca.out_f = out_f;
     ca.out_maps = reinterpret_cast<signed char*>(out_maps);
+    ca.map_bits = p->maps_format == HUFIELD_MAPS_BITS ? 1 : 0;
     ca.nlev = nlev;
     for (int t = 0; t < nlev; ++t) ca.levels[t] = levels[t];
     ca.P = P;
@@ -851,6 +873,9 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     Launch L;
     const KernelInfo k = pick_row(p->logM, ca.nrows, c2r_kernel, out_dtype == HUFIELD_BF16 ? 1 : 0);
     if (!row_launch(p, k, ca.nrows, L)) return HUFIELD_ERR_CUDA;
+    // one-bit maps of short rows are ORed into words that must start clear
+    if (out_maps && ca.map_bits && !k.map_bits_packed && nlev > 0)
+        HF_CUDA(cudaMemsetAsync(out_maps, 0, (size_t)nlev * (size_t)(p->N / 8), s));
     HF_CUDA(launch(p, kPassC2R, k.fn, L, &ca, s));
     if (bp && nlev > 0 && sums_m) {
         if (p->ndim == 3) {
@@ -1138,6 +1163,18 @@ int hufield_plan_set_tile(hufield_plan* p, int32_t tile) {
     return set_tile(p, tile);
 }
 
+int hufield_plan_set_maps_format(hufield_plan* p, int32_t format) {
+    if (!p || (format != HUFIELD_MAPS_I8 && format != HUFIELD_MAPS_BITS)) return HUFIELD_ERR_INVALID_ARG;
+    p->maps_format = format;
+    return HUFIELD_OK;
+}
+
+int hufield_plan_maps_format(const hufield_plan* p, int32_t* format) {
+    if (!p || !format) return HUFIELD_ERR_INVALID_ARG;
+    *format = p->maps_format;
+    return HUFIELD_OK;
+}
+
 int hufield_plan_tile(const hufield_plan* p, int32_t* tile) {
     if (!p || !tile) return HUFIELD_ERR_INVALID_ARG;
     *tile = p->col_tile;
@@ -1242,9 +1279,20 @@ int hufield_threshold(hufield_plan* p, const void* f, int32_t dtype, const float
     if (rc) return rc;
     Levels lv{};
     for (int t = 0; t < nlev; ++t) lv.t[t] = levels[t];
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->maps_format == HUFIELD_MAPS_BITS) {
+        const long long nwords = p->N >> 5;  // one warp per word
+        const long long gw = (nwords + 7) / 8 < (long long)p->nsm * 8 ? (nwords + 7) / 8 : (long long)p->nsm * 8;
+        uint32_t* words = reinterpret_cast<uint32_t*>(out_maps);
+        if (dtype == HUFIELD_F32)
+            k_threshold_bits<0><<<(int)gw, 256, 0, s>>>(nwords, f, lv, nlev, p->N, words);
+        else
+            k_threshold_bits<1><<<(int)gw, 256, 0, s>>>(nwords, f, lv, nlev, p->N, words);
+        HF_CUDA(cudaGetLastError());
+        return HUFIELD_OK;
+    }
     const long long nblk = p->N / 4;
     const long long g = (nblk + 255) / 256 < (long long)p->nsm * 8 ? (nblk + 255) / 256 : (long long)p->nsm * 8;
-    cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HUFIELD_F32)
         k_threshold<0><<<(int)g, 256, 0, s>>>(nblk, f, lv, nlev, p->N, reinterpret_cast<char4*>(out_maps));
     else
@@ -1341,7 +1389,8 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     const size_t esize = out_dtype == HUFIELD_BF16 ? 2 : 4;
     for (int e = 0; e < nfields; ++e) {
         void* fo = out_f ? reinterpret_cast<char*>(out_f) + (size_t)e * (size_t)p->N * esize : nullptr;
-        int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * (size_t)p->N : nullptr;
+        const size_t map_bytes = p->maps_format == HUFIELD_MAPS_BITS ? (size_t)p->N / 8 : (size_t)p->N;
+        int8_t* mo = out_maps ? out_maps + (size_t)e * (size_t)nlev * map_bytes : nullptr;
         const bool odd = lanes == 2 && (e & 1);
         rc = run_field(p, f, seed, field0 + (uint32_t)e, out_dtype, fo, levels, nlev, mo, &bp,
                        odd ? w1.lane_sums : sums_f, sums_m, tab, odd ? w1 : w, lanes == 2 ? (e >> 1) & 1 : e & 1,

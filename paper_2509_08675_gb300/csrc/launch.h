@@ -15,6 +15,7 @@ struct KernelInfo {
     int threads = 0;           // threads per CTA
     int log2_lines = 0;        // log2 of rows (row kernels) or columns (column kernels) per tile
     size_t fixed_smem = 0;     // dynamic shared memory before any per-call tables
+    bool map_bits_packed = false;  // c2r: packs one-bit map words itself (else ORs into cleared words)
 };
 
 // log2 lines per tile of each variant

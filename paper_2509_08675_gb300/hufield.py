@@ -100,6 +100,8 @@ def _load():
     lib.hufield_plan_tuning.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_plan_set_tile.argtypes = [vp, i32]
     lib.hufield_plan_tile.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.hufield_plan_set_maps_format.argtypes = [vp, i32]
+    lib.hufield_plan_maps_format.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_window_variance_filter.argtypes = [vp, fptr, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
     lib.hufield_pipeline.argtypes = [vp, fptr, u64, u32, i32, vp, C.POINTER(C.c_float), i32, vp, i32, i32, i32,
@@ -285,6 +287,21 @@ def hufield_plan_autotune(plan: Plan, filt: Filter, nlev: int, nr: int, ntheta: 
 def hufield_plan_set_tile(plan: Plan, tile: int) -> None:
     """Tile width of the strided passes: 0 by size, 1 wide, 2 two-column (see include/hufield.h)."""
     _check(_lib.hufield_plan_set_tile(plan.handle, int(tile)), "hufield_plan_set_tile")
+
+
+MAPS_I8, MAPS_BITS = 0, 1
+
+
+def hufield_plan_set_maps_format(plan: Plan, fmt: int) -> None:
+    """Sign-map storage of the plan's threshold/pipeline/ensemble calls: MAPS_I8 (one int8
+    per site) or MAPS_BITS (one bit per site, site i at bit i % 32 of 32-bit word i // 32)."""
+    _check(_lib.hufield_plan_set_maps_format(plan.handle, int(fmt)), "hufield_plan_set_maps_format")
+
+
+def hufield_plan_maps_format(plan: Plan) -> int:
+    v = C.c_int32()
+    _check(_lib.hufield_plan_maps_format(plan.handle, C.byref(v)), "hufield_plan_maps_format")
+    return int(v.value)
 
 
 def hufield_plan_tile(plan: Plan) -> int:

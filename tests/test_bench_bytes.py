@@ -22,6 +22,16 @@ def test_pass_plan_without_band_edge():
     assert per_voxel((64, 64, 64), 1, 1.0, kspace=True) == pytest.approx(53.0 - 4 - 8 - 4)
 
 
+def test_one_bit_maps_cut_only_the_map_writes():
+    # c2r writes each map at 1/8 byte per site instead of 1: 3 levels save 3 x 7/8 B/voxel
+    n = 256 * 256
+    assert bench.field_bytes((256, 256), 3, 1.0, map_bytes=0.125) / n == pytest.approx(47.0 - 3 * 0.875)
+    a = bench.algorithmic_bytes((256, 256), 3, map_bytes=0.125)
+    b = bench.algorithmic_bytes((256, 256), 3)
+    assert b["c2r"] - a["c2r"] == pytest.approx(3 * 0.875 * n)
+    assert all(a[k] == b[k] for k in a if k != "c2r")
+
+
 def test_band_edge_scales_only_the_pruned_passes():
     # half the columns live: filter 8, axis-1 forward and inverse 8 + 8 and c2r's read 4 halve
     assert per_voxel((64, 64, 64), 1, 0.5) == pytest.approx(53.0 - (8 + 8 + 8 + 4) / 2)
