@@ -51,7 +51,7 @@ TRAFFIC = {
     ("3d-512", "r2c"): 476.6e6,  # k_r2c<8, 4, 0>, 512^3
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
-E2E_CHUNK = 8  # fields per ensemble call in the end-to-end leg
+E2E_CHUNK = 4  # fields per ensemble call in the end-to-end leg (--e2e-chunk)
 
 
 def algorithmic_bytes(shape, nlev, field_bytes=4, kspace=False, live=1.0, map_bytes=1.0):
@@ -514,6 +514,8 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=0, help="surrogate: targets searched by the plain generator")
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
     ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
+    ap.add_argument("--e2e-chunk", type=int, default=0,
+                    help="fields per ensemble call in the end-to-end leg (default %d)" % E2E_CHUNK)
     ap.add_argument("--maps", default="bits", choices=["bits", "i8"],
                     help="sign-map storage: one bit per site (default) or one int8 per site")
     ap.add_argument("--noise", default="real", choices=["real", "kspace"],
@@ -795,7 +797,8 @@ def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws
     """The same step through the public ensemble call in chunks of E2E_CHUNK
     fields (two lanes each), with every output (fields, sign maps, bins) copied
     to pinned host memory on a second stream that overlaps the next chunk's
-    compute."""
+    compute.  The first chunk's compute and the last chunk's copy stay exposed,
+    so smaller chunks shorten the step while the copies dominate."""
     shape, nf, levels = wl["shape"], wl["nfields"], wl["levels"]
     nlev, nr, nt = len(levels), wl["nr"], wl["ntheta"]
     N = math.prod(shape)
@@ -807,7 +810,8 @@ def measure_e2e(hf, torch, plan, filt, wl, args, out_f, maps, sf, cf, sm, cm, ws
     host_bins = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (sf, cf, sm, cm)]
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
-    chunks = [(c, min(nf, c + E2E_CHUNK)) for c in range(0, nf, E2E_CHUNK)]
+    step_chunk = args.e2e_chunk if args.e2e_chunk > 0 else E2E_CHUNK
+    chunks = [(c, min(nf, c + step_chunk)) for c in range(0, nf, step_chunk)]
     done = [torch.cuda.Event() for _ in chunks]
 
     def step(i):
