@@ -34,6 +34,9 @@ WORKLOADS = {
     # 3D 512^3 single field, superellipsoid p = 6, semi-axes 1:1:0.5
     "3d-512": dict(shape=(512, 512, 512), nfields=1, p=6.0, axes=(1.0, 1.0, 0.5), rot=0.0, k0=0.2, width=0.04,
                    supp=2.0, levels=(0.0,), nr=256, ntheta=1),
+    # the same single 512^3 fields, eight per step: two in flight on the ensemble's two lanes
+    "3d-512x8": dict(shape=(512, 512, 512), nfields=8, p=6.0, axes=(1.0, 1.0, 0.5), rot=0.0, k0=0.2, width=0.04,
+                     supp=2.0, levels=(0.0,), nr=256, ntheta=1),
     "3d-1024": dict(shape=(1024, 1024, 1024), nfields=1, p=6.0, axes=(1.0, 1.0, 0.5), rot=0.0, k0=0.2, width=0.04,
                     supp=2.0, levels=(0.0,), nr=256, ntheta=1),
     # 2D 256^2 isotropic single field (the small oracle case)
@@ -49,6 +52,7 @@ METRIC = "voxels/s for gen+threshold+S(k)"
 TRAFFIC = {
     ("ensemble-2d-4096", "cols_bins"): 318.4e6,  # k_cols<12, 1, 2, -1>, 3 maps of 4096^2, per launch
     ("3d-512", "r2c"): 476.6e6,  # k_r2c<8, 4, 0>, 512^3
+    ("3d-512x8", "r2c"): 476.6e6,  # the same kernel on the same lattice
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 E2E_CHUNK = 4  # fields per ensemble call in the end-to-end leg (--e2e-chunk)
@@ -513,7 +517,8 @@ def main():
     ap.add_argument("--designs", type=int, default=0, help="surrogate: inverse designs (default 500)")
     ap.add_argument("--plain-sample", type=int, default=0, help="surrogate: targets searched by the plain generator")
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
-    ap.add_argument("--also", default="3d-512", help="second workload timed in the same run ('' for none)")
+    ap.add_argument("--also", default="3d-512,3d-512x8",
+                    help="comma-separated workloads timed in the same run ('' for none)")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="fields per ensemble call in the end-to-end leg (default %d)" % E2E_CHUNK)
     ap.add_argument("--maps", default="bits", choices=["bits", "i8"],
@@ -562,17 +567,17 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(hf, torch, res["plan"], res["filt"], wl, args, *res["bufs"], res["field0"], dist, world)
     also = {}
-    if args.also and args.also != args.workload and world == 1:
-        wl2 = dict(WORKLOADS[args.also])
-        r2 = measure(hf, torch, wl2, args.also, args, rank, world, dist)
-        also[args.also] = {k: r2[k] for k in ("value", "ms_per_step", "ms_per_step_one_lane", "lanes", "roofline",
-                                              "pipeline", "passes", "clocks")}
+    for name in [n for n in args.also.split(",") if n and n != args.workload] if world == 1 else []:
+        r2 = measure(hf, torch, dict(WORKLOADS[name]), name, args, rank, world, dist)
+        also[name] = {k: r2[k] for k in ("value", "ms_per_step", "ms_per_step_one_lane", "lanes", "roofline",
+                                         "pipeline", "passes", "clocks")}
         del r2
     comp = {}
     if world == 1 and not args.no_cufft:
         comp[args.workload] = cufft_comparator(hf, torch, wl)
-        if also:
-            comp[args.also] = cufft_comparator(hf, torch, dict(WORKLOADS[args.also]))
+        for name in also:
+            if WORKLOADS[name]["nfields"] == 1:
+                comp[name] = cufft_comparator(hf, torch, dict(WORKLOADS[name]))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(wl, wl["nfields"], args.noise)

@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <mutex>
 #include <stdio.h>
 #include <string>
@@ -264,6 +266,11 @@ using namespace hf;
 enum PassKind { kPassR2C = 0, kPassMidFwd, kPassFilter, kPassMidInv, kPassC2R, kPassMidMaps, kPassBins,
                 kPassCounts, kPassMisc, kPassCount };
 static const char* kPassNames = "r2c,cols_mid_fwd,cols_filter,cols_mid_inv,c2r,cols_mid_maps,cols_bins,counts,misc";
+// NVTX range names of the pass kinds (host-side ranges around each enqueue, for
+// profilers that correlate them with the kernels they launch)
+static const char* const kPassRanges[kPassCount] = {
+    "hufield:r2c", "hufield:cols_mid_fwd", "hufield:cols_filter", "hufield:cols_mid_inv", "hufield:c2r",
+    "hufield:cols_mid_maps", "hufield:cols_bins", "hufield:counts", "hufield:misc"};
 
 struct ProfRecord {
     int kind;
@@ -438,10 +445,15 @@ cudaEvent_t pool_event(hufield_plan* p) {
     return e;
 }
 
-// Runs `body` (which enqueues one kernel on s); with profiling on, brackets it
-// with two events on the same stream.
+// Runs `body` (which enqueues one kernel on s) inside an NVTX range named for
+// its pass; with profiling on, also brackets it with two events on the same
+// stream.
 template <class F>
 cudaError_t profiled(hufield_plan* p, int kind, cudaStream_t s, F&& body) {
+    struct Range {
+        explicit Range(int k) { nvtxRangePushA(kPassRanges[k]); }
+        ~Range() { nvtxRangePop(); }
+    } range(kind);
     if (!p->profile) return body();
     ProfRecord r{kind, pool_event(p), pool_event(p)};
     if (r.start) cudaEventRecord(r.start, s);
