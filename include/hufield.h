@@ -339,8 +339,11 @@ int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, i
 int hufield_batch_layout(const hufield_batch *batch, int64_t *f_offset, int64_t *bin_offset, int64_t totals[3]);
 
 /* Run the batch (asynchronous on `stream`): out_f FP32 fields, out_maps int8
- * sign maps (either may be NULL), field and map bins (overwritten).  The
- * first run, and any run with other buffers, captures the graph. */
+ * sign maps (either may be NULL), field and map bins (overwritten).  A run
+ * with a set of buffers (outputs, bins, workspace) that none of the last two
+ * sets used captures the graph; the graphs of the two most recent sets are
+ * kept, so outputs alternating between two sets replay without a capture.
+ * Runs sharing a workspace must not overlap in time (one stream, or ordered). */
 int hufield_batch_run(hufield_batch *batch, float *out_f, int8_t *out_maps, double *sums_f, int64_t *counts_f,
                       double *sums_m, int64_t *counts_m, void *ws, size_t ws_bytes, void *stream);
 

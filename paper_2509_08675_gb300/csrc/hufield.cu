@@ -1808,17 +1808,29 @@ struct hufield_batch {
     size_t ws_total = 0;
     cudaStream_t origin = nullptr;
     cudaEvent_t fork = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    const void* key[8] = {};  // buffers the graph was captured with
+    // graphs captured for the two most recently used sets of buffers (outputs
+    // alternating between two sets replay without a capture)
+    struct Captured {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const void* key[8] = {};  // buffers the graph was captured with
+        unsigned long long used = 0;
+    };
+    Captured cap[2];
+    unsigned long long runs = 0;
     bool updatable = false;   // HUFIELD_BATCH_UPDATABLE: no band-edge pruning; parameters replaceable
 };
 
 namespace {
 
+void drop_graph(hufield_batch::Captured& c) {
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c = hufield_batch::Captured{};
+}
+
 void batch_free(hufield_batch* b) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto& c : b->cap) drop_graph(c);
     for (auto& c : b->classes) {
         if (c.plan) hufield_plan_destroy(c.plan);
         cudaFree(c.dmem);
@@ -2112,13 +2124,16 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
     if (!aligned(ws) || (out_f && !aligned(out_f)) || (out_maps && !aligned(out_maps))) return HUFIELD_ERR_INVALID_ARG;
     if (bytes < b->ws_total) return HUFIELD_ERR_WS_TOO_SMALL;
     const void* key[8] = {out_f, out_maps, sums_f, counts_f, sums_m, counts_m, ws, (const void*)bytes};
-    bool same = b->exec != nullptr;
-    for (int k = 0; k < 8 && same; ++k) same = key[k] == b->key[k];
-    if (!same) {
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        if (b->graph) cudaGraphDestroy(b->graph);
-        b->exec = nullptr;
-        b->graph = nullptr;
+    hufield_batch::Captured* hit = nullptr;
+    for (auto& c : b->cap) {
+        bool same = c.exec != nullptr;
+        for (int k = 0; k < 8 && same; ++k) same = key[k] == c.key[k];
+        if (same) hit = &c;
+    }
+    if (!hit) {
+        // capture into the empty or least recently used slot
+        hit = b->cap[0].used <= b->cap[1].used ? &b->cap[0] : &b->cap[1];
+        drop_graph(*hit);
         HF_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
         int rc = cudaEventRecord(b->fork, b->origin) == cudaSuccess ? HUFIELD_OK : HUFIELD_ERR_CUDA;
         for (auto& C : b->classes) {
@@ -2154,14 +2169,16 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
             if (g) cudaGraphDestroy(g);
             return rc ? rc : HUFIELD_ERR_CUDA;
         }
-        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+        if (cudaGraphInstantiate(&hit->exec, g, 0) != cudaSuccess) {
+            hit->exec = nullptr;
             cudaGraphDestroy(g);
             return HUFIELD_ERR_CUDA;
         }
-        b->graph = g;
-        for (int k = 0; k < 8; ++k) b->key[k] = key[k];
+        hit->graph = g;
+        for (int k = 0; k < 8; ++k) hit->key[k] = key[k];
     }
-    HF_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    hit->used = ++b->runs;
+    HF_CUDA(cudaGraphLaunch(hit->exec, (cudaStream_t)stream));
     return HUFIELD_OK;
 }
 
@@ -2198,12 +2215,8 @@ int hufield_batch_set_params(hufield_batch* b, const hufield_batch_item* items, 
         const int rc = setup_fused(b, C, (cudaStream_t)stream, true);
         if (rc) return rc;
     }
-    if (recapture && b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        cudaGraphDestroy(b->graph);
-        b->exec = nullptr;
-        b->graph = nullptr;
-    }
+    if (recapture)
+        for (auto& c : b->cap) drop_graph(c);
     return HUFIELD_OK;
 }
 

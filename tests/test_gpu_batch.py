@@ -55,6 +55,41 @@ def test_batch_matches_oracle_and_replays(hf, lanes):
     batch.close()
 
 
+def test_batch_outputs_alternating_between_three_sets(hf):
+    # sets A, B, A, C, B: the two most recent sets' graphs are kept, the third set's run
+    # captures over the least recently used one; every run writes its own buffers
+    items, _ = _items(hf, 10, 3)
+    batch = hf.Batch(items)
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+
+    def buffers():
+        return ([dev_zeros(batch.total_voxels, torch.float32), dev_zeros(batch.total_voxels, torch.int8)] +
+                [dev_zeros(batch.total_bins, dt) for dt in (torch.float64, torch.int64, torch.float64, torch.int64)])
+
+    sets = {k: buffers() for k in "ABC"}
+    got = {}
+    for k in "ABACB":
+        for t in sets[k]:
+            t.zero_()
+        hf.hufield_batch_run(batch, *sets[k], ws)
+        torch.cuda.synchronize()
+        got.setdefault(k, []).append([np_(t) for t in sets[k]])
+    # the runs agree to the rounding of their atomically added sums: each field's
+    # normalisation (hence a map site within rounding of its level) and the bin sums
+    ref = got["A"][0]
+    for k, runs in got.items():
+        for outs in runs:
+            np.testing.assert_allclose(outs[0], ref[0], rtol=0, atol=1e-6 * float(np.abs(ref[0]).max()))
+            flips = int((outs[1] != ref[1]).sum())
+            assert flips <= 2
+            np.testing.assert_array_equal(outs[3], ref[3])
+            np.testing.assert_array_equal(outs[5], ref[5])
+            np.testing.assert_allclose(outs[2], ref[2], rtol=1e-5)
+            if flips == 0:
+                np.testing.assert_allclose(outs[4], ref[4], rtol=1e-5)
+    batch.close()
+
+
 @pytest.mark.parametrize("chunk_bytes", [None, 300000])
 def test_batched_chunks_equal_per_item_calls(hf, monkeypatch, chunk_bytes):
     # a size class runs its items a chunk at a time through the batched passes; with a
