@@ -291,9 +291,13 @@ def run_ragged(args):
 def ragged_line(hf, torch, args, e2e=True, cpu=True):
     """The ragged workload's bench line (also timed inside the default run)."""
     items = ragged_items(hf, RAGGED["count"])
-    batch = hf.Batch(items, autotune=True)  # launch choices tuned per size class
+    bits = args.maps == "bits"
+    batch = hf.Batch(items, autotune=True, maps_bits=bits)  # launch choices tuned per size class
     out_f = torch.empty(batch.total_voxels, dtype=torch.float32, device="cuda")
-    maps = torch.empty(batch.total_voxels, dtype=torch.int8, device="cuda")
+    if bits:  # one bit per site, 32-bit words
+        maps = torch.empty(batch.total_voxels // 32, dtype=torch.int32, device="cuda")
+    else:
+        maps = torch.empty(batch.total_voxels, dtype=torch.int8, device="cuda")
     z = lambda dt: torch.zeros(batch.total_bins, dtype=dt, device="cuda")  # noqa: E731
     sf, cf, sm, cm = z(torch.float64), z(torch.int64), z(torch.float64), z(torch.int64)
     ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
@@ -320,14 +324,15 @@ def ragged_line(hf, torch, args, e2e=True, cpu=True):
     # pass plan per field with one level (2D 4 + 9 + 13 + 5 = 31 B/voxel, 3D 55 B/voxel
     # without a band edge), each field's filter and band edge
     plans = {tuple(it[0]): hf.Plan(tuple(it[0])) for it in items}
-    nbytes = sum(field_bytes(tuple(it[0]), 1, band_live(hf, plans[tuple(it[0])], it[1], it[0])) for it in items)
+    nbytes = sum(field_bytes(tuple(it[0]), 1, band_live(hf, plans[tuple(it[0])], it[1], it[0]),
+                             map_bytes=0.125 if bits else 1.0) for it in items)
     peak, peak_kind = peaks()
     gbs = nbytes / (tot_ms / args.steps / 1e3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "ragged-2000", "fields_per_step": len(items), "fields_2d": n2, "fields_3d": n3,
-                       "voxels_per_step": voxels, "levels": "one per field, t in [-1, 1]",
+                       "voxels_per_step": voxels, "levels": "one per field, t in [-1, 1]", "maps": args.maps,
                        "l2": "flushed between timed steps", "parallelism": "replicas x1",
                        "launch": "one CUDA graph per step (hufield_batch_run)", "autotuned": True},
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
@@ -376,8 +381,10 @@ def ragged_oracle_sample(items, start, seconds):
 def ragged_e2e(hf, torch, batch, out_f, maps, bins, ws, stream, args):
     """The batch through its public call with every output (fields, maps, bins)
     copied to pinned host memory, steps pipelined: the outputs alternate between
-    two device sets, and a second stream copies step i's while step i + 1 runs
-    (time per step = wall time of all steps, last copy included, / steps)."""
+    two device sets, and a second stream copies step i's while step i + 1 runs.
+    A step ends when its copies have reached the host; the median of the steps'
+    times (CUDA events on the copy stream) is the figure, the wall-clock mean
+    beside it."""
     try:
         host_f = torch.empty(out_f.shape, dtype=out_f.dtype, pin_memory=True)
         host_m = torch.empty(maps.shape, dtype=maps.dtype, pin_memory=True)
@@ -391,10 +398,12 @@ def ragged_e2e(hf, torch, batch, out_f, maps, bins, ws, stream, args):
     copied = [torch.cuda.Event(), torch.cuda.Event()]
 
     def steps(n):
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        ends = []
         for i in range(n):
             f, m, b = sets[i & 1]
-            if i >= 2:
-                stream.wait_event(copied[i & 1])  # this set's previous copy has left the device
+            stream.wait_event(copied[i & 1])  # this set's previous copy has left the device
             hf.hufield_batch_run(batch, f, m, *b, ws, stream=stream)
             done[i & 1].record(stream)
             copy.wait_event(done[i & 1])
@@ -404,18 +413,26 @@ def ragged_e2e(hf, torch, batch, out_f, maps, bins, ws, stream, args):
                 for h, d in zip(host_b, b):
                     h.copy_(d, non_blocking=True)
             copied[i & 1].record(copy)
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(copy)
+            ends.append(e)
         copy.synchronize()
         stream.synchronize()
+        return [start.elapsed_time(ends[0])] + [ends[q - 1].elapsed_time(ends[q]) for q in range(1, n)]
 
     steps(2)  # warms the pinned pages and the second set's graph
     n = max(3, min(args.steps, 5))
     t0 = time.perf_counter()
-    steps(n)
-    dt = (time.perf_counter() - t0) / n
-    d2h = out_f.numel() * out_f.element_size() + maps.numel() + sum(b.numel() * b.element_size() for b in bins)
+    times = steps(n)
+    wall = (time.perf_counter() - t0) / n
+    dt = sorted(times)[len(times) // 2] / 1e3
+    d2h = (out_f.numel() * out_f.element_size() + maps.numel() * maps.element_size()
+           + sum(b.numel() * b.element_size() for b in bins))
     del sets
     return {"value": batch.total_voxels / dt, "unit": "voxels/s", "h2d_bytes_per_step": 0,
-            "d2h_bytes_per_step": int(d2h), "steps": n, "step_ms_mean": round(1e3 * dt, 3),
+            "d2h_bytes_per_step": int(d2h), "steps": n, "step_ms_median": round(1e3 * dt, 3),
+            "step_ms_min": round(min(times), 3), "step_ms_max": round(max(times), 3),
+            "wall_ms_mean": round(1e3 * wall, 3),
             "note": "inputs are seeds and filter parameters set at plan time; every output copied to pinned host, "
                     "step i's copies overlapping step i + 1"}
 

@@ -36,7 +36,10 @@
  * Memory and execution
  *   - Every buffer argument named out_*, ws, sums, counts, f or y is a DEVICE
  *     pointer owned by the caller; levels is a HOST pointer.  Device buffers
- *     must be 256-byte aligned.  The library allocates device memory only in
+ *     must be 256-byte aligned, except out_maps of hufield_threshold,
+ *     hufield_pipeline and hufield_ensemble, which needs 4 bytes (a map may
+ *     start at any field offset of a larger buffer, e.g. a batch item's).
+ *     The library allocates device memory only in
  *     hufield_plan_create (a 32 KB twiddle table) and hufield_plan_set_bins,
  *     never on a hot call.
  *   - All hot calls are asynchronous on the given CUDA stream (a cudaStream_t
@@ -174,9 +177,9 @@ int hufield_plan_tile(const hufield_plan *plan, int32_t *tile);
  * N sites at out_maps + t * N.  HUFIELD_MAPS_BITS: one bit per site, site i of
  * a map at bit (i mod 32) of the 32-bit little-endian word i / 32, 1 for +1
  * and 0 for -1; a map takes N / 8 bytes, map t of field e of an ensemble at
- * byte (e * nlev + t) * N / 8 (out_maps 16-byte aligned as for int8).  The
- * same maps either way, 8 times fewer bytes to store or copy; the maps'
- * spectra and the batch calls (int8 maps) are unaffected.  Returns
+ * byte (e * nlev + t) * N / 8.  The same maps either way, 8 times fewer
+ * bytes to store or copy; the maps' spectra are unaffected (batches take the
+ * format from HUFIELD_BATCH_MAPS_BITS).  Returns
  * HUFIELD_ERR_INVALID_ARG for another format; hufield_plan_maps_format reads
  * the setting. */
 enum hufield_maps_format { HUFIELD_MAPS_I8 = 0, HUFIELD_MAPS_BITS = 1 };
@@ -326,9 +329,15 @@ typedef struct hufield_batch hufield_batch;
  * band edge then prunes nothing. */
 #define HUFIELD_BATCH_UPDATABLE 4u
 
+/* Batch flag: sign maps one bit per site (HUFIELD_MAPS_BITS layout, see
+ * hufield_plan_set_maps_format): item i's map starts at bit f_offset[i] of
+ * out_maps, i.e. byte f_offset[i] / 8, and the whole buffer takes sum N_i / 8
+ * bytes. */
+#define HUFIELD_BATCH_MAPS_BITS 8u
+
 /* Plan a batch of n >= 1 items on the current device (copies the items;
- * flags: HUFIELD_BATCH_AUTOTUNE, HUFIELD_BATCH_PER_ITEM and/or
- * HUFIELD_BATCH_LANES(l)).  Allocates the size-class plans, streams and the
+ * flags: HUFIELD_BATCH_AUTOTUNE, HUFIELD_BATCH_PER_ITEM, HUFIELD_BATCH_UPDATABLE,
+ * HUFIELD_BATCH_MAPS_BITS and/or HUFIELD_BATCH_LANES(l)).  Allocates the size-class plans, streams and the
  * batched classes' parameter arrays. */
 int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, int32_t n, uint32_t flags);
 
@@ -338,8 +347,9 @@ int hufield_batch_plan(hufield_batch **batch, const hufield_batch_item *items, i
  * (may be NULL) receives {sum of N_i, sum of nr_i, workspace bytes}. */
 int hufield_batch_layout(const hufield_batch *batch, int64_t *f_offset, int64_t *bin_offset, int64_t totals[3]);
 
-/* Run the batch (asynchronous on `stream`): out_f FP32 fields, out_maps int8
- * sign maps (either may be NULL), field and map bins (overwritten).  A run
+/* Run the batch (asynchronous on `stream`): out_f FP32 fields, out_maps sign
+ * maps, int8 or one bit per site (HUFIELD_BATCH_MAPS_BITS) (either may be
+ * NULL), field and map bins (overwritten).  A run
  * with a set of buffers (outputs, bins, workspace) that none of the last two
  * sets used captures the graph; the graphs of the two most recent sets are
  * kept, so outputs alternating between two sets replay without a capture.

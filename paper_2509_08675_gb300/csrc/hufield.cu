@@ -616,6 +616,8 @@ int axis0_logtb(const hufield_plan* p) {
 }
 
 bool aligned(const void* ptr) { return ((uintptr_t)ptr & 255) == 0; }
+// Sign maps are written in 4-byte units at most (int8 quads, one-bit words).
+bool maps_aligned(const void* ptr) { return ((uintptr_t)ptr & 3) == 0; }
 
 #define HF_CUDA(expr)                              \
     do {                                           \
@@ -1284,7 +1286,7 @@ int hufield_generate(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
 
 int hufield_threshold(hufield_plan* p, const void* f, int32_t dtype, const float* levels, int32_t nlev,
                       int8_t* out_maps, void* stream) {
-    if (!p || !f || !out_maps || !aligned(f) || !aligned(out_maps)) return HUFIELD_ERR_INVALID_ARG;
+    if (!p || !f || !out_maps || !aligned(f) || !maps_aligned(out_maps)) return HUFIELD_ERR_INVALID_ARG;
     if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16) return HUFIELD_ERR_INVALID_ARG;
     if (nlev < 1) return HUFIELD_ERR_INVALID_ARG;
     int rc = check_levels(levels, nlev);
@@ -1350,7 +1352,7 @@ int hufield_ensemble(hufield_plan* p, const hufield_filter* f, uint64_t seed, ui
     rc = check_levels(levels, nlev);
     if (rc) return rc;
     if (out_dtype != HUFIELD_F32 && out_dtype != HUFIELD_BF16) return HUFIELD_ERR_INVALID_ARG;
-    if ((out_f && !aligned(out_f)) || (out_maps && !aligned(out_maps))) return HUFIELD_ERR_INVALID_ARG;
+    if ((out_f && !aligned(out_f)) || (out_maps && !maps_aligned(out_maps))) return HUFIELD_ERR_INVALID_ARG;
     if (accumulate != 0 && accumulate != 1) return HUFIELD_ERR_INVALID_ARG;
     if (!sums_f || !counts_f || (nlev > 0 && (!sums_m || !counts_m))) return HUFIELD_ERR_INVALID_ARG;
     BinParams bp;
@@ -1819,6 +1821,7 @@ struct hufield_batch {
     Captured cap[2];
     unsigned long long runs = 0;
     bool updatable = false;   // HUFIELD_BATCH_UPDATABLE: no band-edge pruning; parameters replaceable
+    bool maps_bits = false;   // HUFIELD_BATCH_MAPS_BITS: one-bit maps (the class plans' format)
 };
 
 namespace {
@@ -1927,6 +1930,7 @@ int run_chunk(hufield_batch::Class& C, long long i0, long long nk, long long kz,
     ca.N = p->N;
     ca.out_f = out_f;
     ca.out_maps = reinterpret_cast<signed char*>(out_maps);
+    ca.map_bits = p->maps_format == HUFIELD_MAPS_BITS ? 1 : 0;  // each field's map from site fout on
     ca.nlev = 1;
     ca.tw = p->tw;
     ca.status = status;
@@ -2011,7 +2015,8 @@ extern "C" {
 int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int32_t n, uint32_t flags) {
     const int want_lanes = (int)((flags >> 8) & 15u);
     if (!out || !items || n < 1 ||
-        (flags & ~(HUFIELD_BATCH_AUTOTUNE | HUFIELD_BATCH_PER_ITEM | HUFIELD_BATCH_UPDATABLE | (15u << 8))) != 0 ||
+        (flags & ~(HUFIELD_BATCH_AUTOTUNE | HUFIELD_BATCH_PER_ITEM | HUFIELD_BATCH_UPDATABLE | HUFIELD_BATCH_MAPS_BITS |
+                   (15u << 8))) != 0 ||
         want_lanes > kMaxBatchLanes)
         return HUFIELD_ERR_INVALID_ARG;
     const int max_lanes = want_lanes > 0 ? want_lanes : kBatchLanes;
@@ -2020,6 +2025,7 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
     if (!b) return HUFIELD_ERR_CUDA;
     b->items.assign(items, items + n);
     b->updatable = (flags & HUFIELD_BATCH_UPDATABLE) != 0;
+    b->maps_bits = (flags & HUFIELD_BATCH_MAPS_BITS) != 0;
     std::vector<int> cls(n, -1);
     std::vector<hufield_dims> cdims;
     for (int i = 0; i < n; ++i) {
@@ -2032,7 +2038,10 @@ int hufield_batch_plan(hufield_batch** out, const hufield_batch_item* items, int
     }
     b->classes.resize(cdims.size());
     int rc = HUFIELD_OK;
-    for (size_t c = 0; c < cdims.size() && rc == HUFIELD_OK; ++c) rc = hufield_plan_create(&b->classes[c].plan, &cdims[c], 0);
+    for (size_t c = 0; c < cdims.size() && rc == HUFIELD_OK; ++c) {
+        rc = hufield_plan_create(&b->classes[c].plan, &cdims[c], 0);
+        if (!rc && b->maps_bits) b->classes[c].plan->maps_format = HUFIELD_MAPS_BITS;
+    }
     if (rc) {
         batch_free(b);
         return rc;
@@ -2135,7 +2144,13 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
         hit = b->cap[0].used <= b->cap[1].used ? &b->cap[0] : &b->cap[1];
         drop_graph(*hit);
         HF_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
-        int rc = cudaEventRecord(b->fork, b->origin) == cudaSuccess ? HUFIELD_OK : HUFIELD_ERR_CUDA;
+        int rc = HUFIELD_OK;
+        // one-bit maps of batched rows under 16 pairs are ORed into cleared words
+        bool clear_maps = false;
+        for (const auto& C : b->classes) clear_maps |= b->maps_bits && C.fused && C.plan->logM < 4;
+        if (out_maps && clear_maps && cudaMemsetAsync(out_maps, 0, (size_t)(b->f_total / 8), b->origin) != cudaSuccess)
+            rc = HUFIELD_ERR_CUDA;
+        if (!rc && cudaEventRecord(b->fork, b->origin) != cudaSuccess) rc = HUFIELD_ERR_CUDA;
         for (auto& C : b->classes) {
             for (int l = 0; l < C.lanes && !rc; ++l) {
                 cudaStream_t ls = C.stream[l];
@@ -2152,8 +2167,9 @@ int hufield_batch_run(hufield_batch* b, float* out_f, int8_t* out_maps, double* 
                     const int i = C.members[m];
                     const hufield_batch_item& it = b->items[i];
                     const long long fo = b->f_off[i], bo = b->bin_off[i];
+                    int8_t* mo = out_maps ? out_maps + (b->maps_bits ? fo / 8 : fo) : nullptr;
                     rc = hufield_ensemble(C.plan, &it.filt, it.seed, it.field_idx, 1, HUFIELD_F32,
-                                          out_f ? out_f + fo : nullptr, &it.level, 1, out_maps ? out_maps + fo : nullptr,
+                                          out_f ? out_f + fo : nullptr, &it.level, 1, mo,
                                           it.nr, 1, 0, sums_f + bo, counts_f + bo, sums_m + bo, counts_m + bo, lws,
                                           C.ws_bytes, ls);
                 }

@@ -19,7 +19,7 @@ KernelInfo c2r_info() {
     using G = Geo<LOG2M, LOGTR, true>;
     return {reinterpret_cast<const void*>(&k_c2r<LOG2M, LOGTR, OUTDT>), G::T, LOGTR,
             (size_t)2 * G::TB * G::L * 8 + (size_t)G::L * 8 + (size_t)plan_twiddle_slots<LOG2M>() * 8 + 16,
-            map_bits_packed(LOG2M, LOGTR)};
+            map_bits_packed(LOG2M, LOGTR, OUTDT == kOutBatch)};
 }
 
 template <int LOG2L, int LOGTB, int MODE, int DIR>

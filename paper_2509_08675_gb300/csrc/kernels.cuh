@@ -81,7 +81,7 @@ struct C2RArgs {
     const long long* fout;
     long long nrows_valid;  // kOutBatch: rows at or past this are neither loaded nor written
     // 1: out_maps holds one bit per site (32-bit words, site i at bit i mod 32 of word
-    // i / 32 of its map, 1 for +1); not with kOutBatch
+    // i / 32 of its map, 1 for +1; a batched field's map from site fout[f] on)
     int map_bits;
 };
 
@@ -127,10 +127,13 @@ struct ColArgs {
 // 128 threads or more at 128 registers per thread or fewer (65536 / (128 T)
 // CTAs of T threads); the small tiles of tiny lattices are left unbounded.
 // Sign maps stored one bit per site (site i at bit i mod 32 of word i / 32).
-// A row tile of TR rows x M pairs covers whole 16-pair words when TR M >= 16:
-// the c2r kernel then packs its words itself; smaller tiles OR their bits
-// into words cleared beforehand.
-__host__ __device__ constexpr bool map_bits_packed(int log2m, int logtr) { return log2m + logtr >= 4; }
+// The c2r kernel packs whole 16-pair words itself when each row holds whole
+// words (M >= 16), or, for a single field (rows contiguous), when its tile of
+// TR rows does (TR M >= 16); otherwise it ORs bits into words cleared
+// beforehand.
+__host__ __device__ constexpr bool map_bits_packed(int log2m, int logtr, bool batch) {
+    return log2m >= 4 || (!batch && log2m + logtr >= 4);
+}
 
 // Four bytes holding 2-bit values b0..b3 -> b0 | b1 << 2 | b2 << 4 | b3 << 6.
 __device__ __forceinline__ uint32_t pack_two_bit_bytes(uint32_t x) {
@@ -544,31 +547,47 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
                 for (int e = 0; e < E; ++e)
                     u[e] = make_float2(v[e].x >= th ? 1.0f : -1.0f, v[e].y >= th ? 1.0f : -1.0f);
             }
-            if (OUTDT != kOutBatch && a.out_maps != nullptr && a.map_bits) {
+            if (a.out_maps != nullptr && a.map_bits) {
                 // one bit per site: sites 2 out_pair and 2 out_pair + 1 of each element
-                if constexpr (map_bits_packed(LOG2M, LOGTR)) {
-                    // the tile's pairs (whole words) stage as 2-bit bytes in buf, which
-                    // the inverse FFT and the previous level's spectrum no longer read;
-                    // a thread then packs 16 bytes into each word
+                // (one level per field in batches: lev = 0, each field's map at its fout)
+                uint32_t* words = reinterpret_cast<uint32_t*>(a.out_maps) + (long long)lev * (a.N >> 5);
+                if constexpr (map_bits_packed(LOG2M, LOGTR, OUTDT == kOutBatch)) {
+                    // the tile's pairs stage as 2-bit bytes in buf, which the inverse FFT
+                    // and the previous level's spectrum no longer read; a thread then
+                    // packs 16 bytes into each word
                     unsigned char* sb = reinterpret_cast<unsigned char*>(buf);
                     __syncthreads();
                     for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
                         sb[(b << LOG2M) + j] = (unsigned char)((u[e].x > 0.0f ? 1 : 0) | (u[e].y > 0.0f ? 2 : 0));
                     });
                     __syncthreads();
-                    uint32_t* tw_words = reinterpret_cast<uint32_t*>(a.out_maps) + (long long)lev * (a.N >> 5) +
-                                         ((row0 << LOG2M) >> 4);
+                    if constexpr (LOG2M >= 4) {
+                        // rows of whole words: row b's M / 16 words from its first pair on
+                        constexpr int kLogRowWords = LOG2M - 4;
 #pragma unroll 1
-                    for (int q = t; q < tile_elems / 16; q += G::T) {
-                        const uint4 c = reinterpret_cast<const uint4*>(sb)[q];
-                        tw_words[q] = pack_two_bit_bytes(c.x) | (pack_two_bit_bytes(c.y) << 8) |
-                                      (pack_two_bit_bytes(c.z) << 16) | (pack_two_bit_bytes(c.w) << 24);
+                        for (int q = t; q < (G::TB << kLogRowWords); q += G::T) {
+                            const int b = q >> kLogRowWords;
+                            if (!valid(b)) continue;
+                            const uint4 c = reinterpret_cast<const uint4*>(sb)[q];
+                            words[(out_pair(b, 0) >> 4) + (q & ((1 << kLogRowWords) - 1))] =
+                                pack_two_bit_bytes(c.x) | (pack_two_bit_bytes(c.y) << 8) |
+                                (pack_two_bit_bytes(c.z) << 16) | (pack_two_bit_bytes(c.w) << 24);
+                        }
+                    } else {
+                        // short rows, contiguous tile (single fields): the tile's whole words
+                        uint32_t* tw_words = words + ((row0 << LOG2M) >> 4);
+#pragma unroll 1
+                        for (int q = t; q < tile_elems / 16; q += G::T) {
+                            const uint4 c = reinterpret_cast<const uint4*>(sb)[q];
+                            tw_words[q] = pack_two_bit_bytes(c.x) | (pack_two_bit_bytes(c.y) << 8) |
+                                          (pack_two_bit_bytes(c.z) << 16) | (pack_two_bit_bytes(c.w) << 24);
+                        }
                     }
                     // the FFT below reaches a barrier before its first write to buf
                 } else {
-                    // tiles of under 16 pairs: words span tiles; the caller cleared them
-                    uint32_t* words = reinterpret_cast<uint32_t*>(a.out_maps) + (long long)lev * (a.N >> 5);
+                    // words span tiles: the caller cleared them
                     for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {
+                        if (!valid(b)) return;
                         const long long site = 2 * out_pair(b, j);
                         const uint32_t two = (u[e].x > 0.0f ? 1u : 0u) | (u[e].y > 0.0f ? 2u : 0u);
                         if (two) atomicOr(words + (site >> 5), two << (site & 31));

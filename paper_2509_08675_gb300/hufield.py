@@ -419,13 +419,15 @@ class Batch:
     default of two) sets the lanes per size class (HUFIELD_BATCH_LANES); per_item =
     True runs every item through its own calls instead of batched chunks
     (HUFIELD_BATCH_PER_ITEM); updatable = True allows set_params
-    (HUFIELD_BATCH_UPDATABLE)."""
+    (HUFIELD_BATCH_UPDATABLE); maps_bits = True writes the sign maps one bit per
+    site (HUFIELD_BATCH_MAPS_BITS: total_voxels / 8 bytes)."""
 
     def __init__(self, items, autotune: bool = False, lanes: int = 0, per_item: bool = False,
-                 updatable: bool = False):
+                 updatable: bool = False, maps_bits: bool = False):
         arr = _batch_items(items)
         h = C.c_void_p()
-        flags = (1 if autotune else 0) | (2 if per_item else 0) | (4 if updatable else 0) | ((int(lanes) & 15) << 8)
+        flags = ((1 if autotune else 0) | (2 if per_item else 0) | (4 if updatable else 0) |
+                 (8 if maps_bits else 0) | ((int(lanes) & 15) << 8))
         _check(_lib.hufield_batch_plan(C.byref(h), arr, len(items), flags), "hufield_batch_plan")
         self._h = h
         self.n = len(items)

@@ -39,6 +39,20 @@ def test_workspace_checks(hf):
     assert e.value.status == hf.ERR_INVALID_ARG  # misaligned
 
 
+def test_map_output_alignment(hf):
+    # maps are written in units of at most 4 bytes: any 4-byte offset works, others are refused
+    plan = hf.Plan((64, 64))
+    f = torch.randn((64, 64), device="cuda")
+    buf = torch.zeros(64 * 64 + 16, dtype=torch.int8, device="cuda")
+    hf.hufield_threshold(plan, f, (0.0,), buf[4:4 + 64 * 64])
+    torch.cuda.synchronize()
+    want = torch.where(f >= 0, 1, -1).to(torch.int8).flatten()
+    assert torch.equal(buf[4:4 + 64 * 64], want)
+    with pytest.raises(hf.HufieldError) as e:
+        hf.hufield_threshold(plan, f, (0.0,), buf[2:2 + 64 * 64])
+    assert e.value.status == hf.ERR_INVALID_ARG
+
+
 def test_bins_and_levels_checks(hf):
     plan = hf.Plan((16, 16, 16))
     ws = plan.workspace(8, 4096)

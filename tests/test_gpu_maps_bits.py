@@ -139,3 +139,37 @@ def test_bad_maps_format_refused(hf):
     with pytest.raises(hf.HufieldError):
         hf.hufield_plan_set_maps_format(plan, 2)
     assert hf.hufield_plan_maps_format(plan) == hf.MAPS_I8
+
+
+BATCH_SHAPES = [(8, 8), (16, 16), (32, 32), (64, 128), (8, 8, 8), (16, 16, 16), (32, 32, 32)]
+
+
+@pytest.mark.parametrize("per_item", [False, True], ids=["batched-chunks", "per-item"])
+def test_batch_bit_maps(hf, per_item):
+    # rows of 4 and 8 pairs (OR path into words cleared at the graph's start) and of 16
+    # or more (per-row words); each item's map from bit f_offset on, exact against the
+    # batch's own fields (each site compares its stored FP32 value with the item's level)
+    from tests import inputs
+
+    rng = np.random.default_rng(4)
+    items = []
+    for i in range(21):
+        shape = BATCH_SHAPES[i % len(BATCH_SHAPES)]
+        gf, _ = filters(hf, **inputs.random_filter(len(shape), 500 + i))
+        items.append((shape, gf, 9, i, float(np.float32(rng.uniform(-1, 1))), min(16, min(shape) // 2)))
+    batch = hf.Batch(items, per_item=per_item, maps_bits=True)
+    total = batch.total_voxels
+    out_f = dev_zeros(total, torch.float32)
+    words = torch.full((total // 32,), -1, dtype=torch.int32, device="cuda")
+    z = [dev_zeros(batch.total_bins, dt) for dt in (torch.float64, torch.int64, torch.float64, torch.int64)]
+    ws = torch.empty(batch.ws_bytes, dtype=torch.uint8, device="cuda")
+    for _ in range(2):  # capture, then replay over the same (dirty) words
+        hf.hufield_batch_run(batch, out_f, words, *z, ws)
+        torch.cuda.synchronize()
+        f_all, m_all = np_(out_f), unpack(np_(words), total)
+        for i, (shape, _, _, _, level, _) in enumerate(items):
+            N = int(np.prod(shape))
+            fo = batch.f_offset[i]
+            want = np.where(f_all[fo:fo + N] >= level, 1, -1).astype(np.int8)
+            np.testing.assert_array_equal(m_all[fo:fo + N], want)
+    batch.close()
