@@ -566,6 +566,8 @@ def main():
                     help="fields per ensemble call in the end-to-end leg (default %d)" % E2E_CHUNK)
     ap.add_argument("--maps", default="bits", choices=["bits", "i8"],
                     help="sign-map storage: one bit per site (default) or one int8 per site")
+    ap.add_argument("--order", type=int, default=0, choices=[0, 1, 2],
+                    help="strided passes' tile order: 0 default (interleaved), 1 contiguous chunks, 2 interleaved")
     ap.add_argument("--noise", default="real", choices=["real", "kspace"],
                     help="white noise in real space (forward FFT) or drawn as k-space coefficients")
     args = ap.parse_args()
@@ -673,6 +675,7 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
     hf.hufield_plan_set_bins(plan, nr, nt)  # plan-time bin table and counts, as a production caller would
     bits = args.maps == "bits"
     hf.hufield_plan_set_maps_format(plan, hf.MAPS_BITS if bits else hf.MAPS_I8)
+    hf.hufield_plan_set_order(plan, args.order)
     ws = plan.workspace(nlev, nb, lanes=2 if nf >= 2 else 1)
     slice_bytes = (hf.hufield_workspace_bytes(plan, nlev, nb) + 255) & ~255
     ws_one = ws[:slice_bytes]  # the first slice alone: one lane

@@ -171,6 +171,17 @@ int hufield_plan_tuning(const hufield_plan *plan, int32_t out[5]);
 int hufield_plan_set_tile(hufield_plan *plan, int32_t tile);
 int hufield_plan_tile(const hufield_plan *plan, int32_t *tile);
 
+/* Order in which the CTAs of the strided passes take their tiles: 0 the
+ * default (interleaved: neighbouring tiles, whose box rows share DRAM sectors
+ * and L2 lines, run at the same time on different CTAs), 1 contiguous chunks (CTA
+ * c runs tiles c T / G .. (c + 1) T / G - 1 of T on a grid of G), 2
+ * interleaved (CTA c runs tiles c, c + G, c + 2 G, ...).  Every order
+ * computes the same fields and maps; bin sums may differ in their rounding
+ * order.  Takes effect at the next call.  Errors: HUFIELD_ERR_INVALID_ARG.
+ * hufield_plan_order reads the choice.  Not in the paper: a launch choice. */
+int hufield_plan_set_order(hufield_plan *plan, int32_t order);
+int hufield_plan_order(const hufield_plan *plan, int32_t *order);
+
 /* Storage of the sign maps (the +-1 maps of Sec. II.B, last paragraph) that
  * hufield_threshold, hufield_pipeline and hufield_ensemble write through this
  * plan.  HUFIELD_MAPS_I8 (the default): one int8 per site, +1 or -1, a map of

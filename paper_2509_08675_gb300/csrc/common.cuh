@@ -63,45 +63,47 @@ __device__ __forceinline__ uint4 noise_block(uint64_t seed, uint32_t field_idx, 
                          (uint32_t)(seed >> 32));
 }
 
-// ln u for u = (x + 1/2) 2^-32, without the library logarithm.  The argument
-// is reduced exactly to u = 2^e m with m in [sqrt(1/2), sqrt(2)) and f = m - 1
-// (exact), then ln u = e ln2 + 2 atanh(f / (2 + f)) by the series
-// 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9), |s| <= 0.1716 (Abramowitz & Stegun
-// 4.1.27; the next term is below 2.5e-9 of the sum).  For u >= 1/2 the
-// complement d = 1 - u = (~x + 1/2) 2^-32 is exact in integers, so f = -d or
-// f = 1 - 2d stays exact and ln u keeps full relative precision near u = 1.
-__device__ __forceinline__ float log_uniform(uint32_t x) {
-    float f;
-    int e;
-    if (x >= 0x80000000u) {
-        const float d = fmaf(__uint2float_rn(~x), 0x1p-32f, 0x1p-33f);  // (0, 1/2]
-        const bool low = d > 0.29289321881345248f;                       // u < sqrt(1/2)
-        f = low ? fmaf(-2.0f, d, 1.0f) : -d;
-        e = low ? -1 : 0;
-    } else {
-        const float u = fmaf(__uint2float_rn(x), 0x1p-32f, 0x1p-33f);  // (0, 1/2)
-        const int bits = __float_as_int(u);
-        e = ((bits >> 23) & 0xff) - 127;
-        float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);  // [1, 2)
-        if (m > 1.41421356237309505f) {
-            m *= 0.5f;
-            e += 1;
-        }
-        f = m - 1.0f;
-    }
-    const float s = __fdividef(f, 2.0f + f);
-    const float s2 = s * s;
-    const float p = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
-    // e ln2 with ln2 split into a head exact in FP32 and a tail
-    const float fe = (float)e;
-    return fmaf(fe, 0.693145751953125f, fmaf(fe, 1.42860682030941723e-6f, 2.0f * s * p));
+// Hardware approximations (PTX): base-2 logarithm (absolute error about
+// 2^-22 for arguments in [1/2, 2)) and square root (relative error about
+// 2^-23).
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Box-Muller radius sqrt(-2 ln u) for u = (x + 1/2) 2^-32.  Near u = 1 the
+// complement d = 1 - u = (~x + 1/2) 2^-32 is exact, and for d < 1/16
+// -ln u = -ln(1 - d) = d + d^2/2 + ... + d^7/7 (Taylor series; the rest is
+// below 5e-10 of the sum), so the radius keeps full relative precision where
+// it is small.  Elsewhere |log2 u| >= 0.093 and -ln u = -ln2 log2 u with the
+// hardware log2: its absolute error of ~2^-22 is at most 2.6e-6 of -ln u,
+// 1.3e-6 of the radius (~5e-7 absolute at d = 1/16, less beyond).  Both
+// branches are evaluated and one is selected (no divergence).
+__device__ __forceinline__ float bm_radius(uint32_t x) {
+    const float u = fmaf(__uint2float_rn(x), 0x1p-32f, 0x1p-33f);
+    const float d = fmaf(__uint2float_rn(~x), 0x1p-32f, 0x1p-33f);
+    const float far = -0.693147180559945309f * lg2_approx(u);
+    const float near = fmaf(d * d,
+                            fmaf(d, fmaf(d, fmaf(d, fmaf(d, fmaf(d, 1.0f / 7.0f, 1.0f / 6.0f), 0.2f), 0.25f),
+                                         1.0f / 3.0f),
+                                 0.5f),
+                            d);
+    return sqrt_approx(2.0f * (d < 0.0625f ? near : far));
 }
 
 // (cos, sin)(2 pi u) for u = (x + 1/2) 2^-32: the quadrant comes from the top
 // two bits (after centring) and the remainder y = (2 rem + 1) 2^-32, |y| <= 1/4
 // (angle pi y), is formed exactly in integers before one rounding to FP32.
 // sin(pi y) and cos(pi y) are their Taylor series in pi y up to the y^9 and
-// y^10 terms (truncation below 2e-9 on |y| <= 1/4), evaluated by Horner.
+// y^10 terms (truncation below 2e-9 on |y| <= 1/4), evaluated by Horner.  The
+// quadrant swaps the pair (odd quadrants) and flips signs (cos negative in
+// quadrants 1 and 2, sin in 2 and 3) without branches.
 __device__ __forceinline__ float2 cis_uniform(uint32_t x) {
     const uint32_t xs = x + 0x20000000u;  // centre the quadrants
     const uint32_t q = xs >> 30;
@@ -119,19 +121,18 @@ __device__ __forceinline__ float2 cis_uniform(uint32_t x) {
                                           4.05871212641676822f),
                                -4.93480220054467931f),
                           1.0f);
-    switch (q) {
-        case 0: return make_float2(cp, sp);
-        case 1: return make_float2(-sp, cp);
-        case 2: return make_float2(-cp, -sp);
-        default: return make_float2(sp, -cp);
-    }
+    const bool odd = (q & 1u) != 0u;
+    const float c = odd ? sp : cp, s = odd ? cp : sp;
+    const uint32_t cneg = ((q + 1u) >> 1) & 1u, sneg = q >> 1;
+    return make_float2(__uint_as_float(__float_as_uint(c) ^ (cneg << 31)),
+                       __uint_as_float(__float_as_uint(s) ^ (sneg << 31)));
 }
 
 // Box-Muller on one block: z0,z1 from (x0,x1), z2,z3 from (x2,x3).
 __device__ __forceinline__ float4 box_muller(uint4 x) {
-    const float r0 = sqrtf(-2.0f * log_uniform(x.x));
+    const float r0 = bm_radius(x.x);
     const float2 a = cis_uniform(x.y);
-    const float r1 = sqrtf(-2.0f * log_uniform(x.z));
+    const float r1 = bm_radius(x.z);
     const float2 b = cis_uniform(x.w);
     return make_float4(r0 * a.x, r0 * a.y, r1 * b.x, r1 * b.y);
 }

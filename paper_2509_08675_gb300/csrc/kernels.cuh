@@ -121,6 +121,7 @@ struct ColArgs {
     long long acc_stride;
     // BINS: batch ab's bins at gbins + boff[ab] when boff is set (else + ab nbins)
     const long long* boff;
+    int interleave;         // 1: CTA c runs tiles c, c + grid, ...; 0: a contiguous chunk (see tiles_of)
 };
 
 // Minimum resident CTAs per SM asked of the compiler: keeps the kernels of
@@ -165,11 +166,7 @@ __device__ __forceinline__ int signed_index(int i, int log2n) {
 // tile) from log2f; an error in log2 S is divided by p in log2 K.
 constexpr float kLog2Zero = -1e30f;  // u of a zero term (kappa'_i = 0)
 
-__device__ __forceinline__ float fast_lg2(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
+__device__ __forceinline__ float fast_lg2(float x) { return lg2_approx(x); }
 __device__ __forceinline__ float fast_ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -306,6 +303,26 @@ __device__ __forceinline__ void chunk_of(long long ntiles, long long& t0, long l
     const long long G = gridDim.x;
     t0 = ntiles * (long long)blockIdx.x / G;
     t1 = ntiles * ((long long)blockIdx.x + 1) / G;
+}
+
+// The tiles a CTA of a strided pass runs: tile first + k step for k < cnt.
+// Contiguous chunks (step 1), or every grid-th tile (interleaved): then
+// neighbouring tiles run at about the same time on different CTAs, so the
+// narrow tiles whose box rows share DRAM sectors meet in L2 instead of each
+// fetching the sector again.
+__device__ __forceinline__ void tiles_of(long long ntiles, int interleave, long long& first, long long& step,
+                                         long long& cnt) {
+    if (interleave) {
+        first = blockIdx.x;
+        step = gridDim.x;
+        cnt = ntiles > first ? (ntiles - first + step - 1) / step : 0;
+    } else {
+        long long t0, t1;
+        chunk_of(ntiles, t0, t1);
+        first = t0;
+        step = 1;
+        cnt = t1 - t0;
+    }
 }
 
 // k-space noise: Philox block J of counter word 3 = 1 gives the coefficients
@@ -843,8 +860,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
         }
     };
 
-    long long t0, t1;
-    chunk_of(a.ntiles, t0, t1);
+    long long tfirst, tstep, tcnt;
+    tiles_of(a.ntiles, a.interleave, tfirst, tstep, tcnt);
+    auto tile_at = [&](long long k) { return tfirst + k * tstep; };
     // run tile ti: batch ab, tile tcol of the batch in the full tile order
     // (tile counts stay below 2^31: 32-bit divisions, the second one only
     // when columns are skipped)
@@ -884,10 +902,10 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     }
     __syncthreads();
     if (kLoad && t == 0) {
-        if (t0 < t1 && !a.inject_skip) issue(t0, buf0, &bar[0]);
+        if (tcnt > 0 && !a.inject_skip) issue(tile_at(0), buf0, &bar[0]);
 #pragma unroll
         for (int q = 1; q < NBUF; ++q)
-            if (t0 + q < t1) issue(t0 + q, buf0 + q * tile_elems, &bar[q]);
+            if (q < tcnt) issue(tile_at(q), buf0 + q * tile_elems, &bar[q]);
     }
 
     // The bins gather in FP32 (shared-memory atomics) over up to kMergeTiles
@@ -924,12 +942,13 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     uint32_t phases = 0u;  // bit s: parity of the next completion of bar[s]
     long long cur = -1;
     long long failed_at = -1;
-    for (long long ti = t0; ti < t1; ++ti) {
-        const int s = (int)((ti - t0) % NBUF);
+    for (long long k = 0; k < tcnt; ++k) {
+        const long long ti = tile_at(k);
+        const int s = (int)(k % NBUF);
         float2* buf = buf0 + s * tile_elems;
         if constexpr (kLoad) {
             if (!cta_wait(&bar[s], (phases >> s) & 1u, a.wait_budget)) {
-                failed_at = ti;
+                failed_at = k;
                 break;
             }
             phases ^= 1u << s;
@@ -1143,9 +1162,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                 for (int y = 0; y < L; y += LB) tma_store_3d(&a.map, (int)c0, y, (int)ab, buf + y * TB);
                 bulk_commit();
             }
-            if (kLoad && ti + NBUF < t1) {
+            if (kLoad && k + NBUF < tcnt) {
                 if constexpr (kStore) bulk_wait_read_all();
-                issue(ti + NBUF, buf, &bar[s]);
+                issue(tile_at(k + NBUF), buf, &bar[s]);
             }
         }
         if constexpr (kAcc) {
@@ -1170,9 +1189,9 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
             // drain this CTA's own loads still in flight (bounded): tiles
             // failed_at .. failed_at + NBUF - 1 were issued (all but a skipped
             // first load), none of them waited for yet; then its stores
-            for (int q = 0; q < NBUF && failed_at + q < t1; ++q) {
-                if (q == 0 && a.inject_skip && failed_at == t0) continue;
-                const int s = (int)((failed_at + q - t0) % NBUF);
+            for (int q = 0; q < NBUF && failed_at + q < tcnt; ++q) {
+                if (q == 0 && a.inject_skip && failed_at == 0) continue;
+                const int s = (int)((failed_at + q) % NBUF);
                 mbar_wait_bounded(&bar[s], (phases >> s) & 1u, a.wait_budget);
             }
             if constexpr (kStore) bulk_wait_all();

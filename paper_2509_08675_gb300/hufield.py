@@ -100,6 +100,8 @@ def _load():
     lib.hufield_plan_tuning.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_plan_set_tile.argtypes = [vp, i32]
     lib.hufield_plan_tile.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.hufield_plan_set_order.argtypes = [vp, i32]
+    lib.hufield_plan_order.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_plan_set_maps_format.argtypes = [vp, i32]
     lib.hufield_plan_maps_format.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.hufield_window_variance.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_float), vp, vp, sz, vp]
@@ -287,6 +289,17 @@ def hufield_plan_autotune(plan: Plan, filt: Filter, nlev: int, nr: int, ntheta: 
 def hufield_plan_set_tile(plan: Plan, tile: int) -> None:
     """Tile width of the strided passes: 0 by size, 1 wide, 2 two-column (see include/hufield.h)."""
     _check(_lib.hufield_plan_set_tile(plan.handle, int(tile)), "hufield_plan_set_tile")
+
+
+def hufield_plan_set_order(plan: Plan, order: int) -> None:
+    """Tile order of the strided passes: 0 default (interleaved), 1 contiguous chunks, 2 interleaved."""
+    _check(_lib.hufield_plan_set_order(plan.handle, int(order)), "hufield_plan_set_order")
+
+
+def hufield_plan_order(plan: Plan) -> int:
+    v = C.c_int32()
+    _check(_lib.hufield_plan_order(plan.handle, C.byref(v)), "hufield_plan_order")
+    return int(v.value)
 
 
 MAPS_I8, MAPS_BITS = 0, 1

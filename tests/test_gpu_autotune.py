@@ -86,3 +86,34 @@ def test_tile_widths_give_the_same_results(hf, shape, cfg, levels, nr, nt):
             np.testing.assert_array_equal(got["counts_m"], ref["counts_m"])
     with pytest.raises(hf.HufieldError):
         hf.hufield_plan_set_tile(plan, 3)
+
+
+@pytest.mark.parametrize("shape,cfg,levels,nr,nt,noise", [((1024, 1024), inputs.C1, (0.0, 0.5), 64, 36, "real"),
+                                                          ((256, 256, 256), inputs.C2, (0.0,), 128, 1, "real"),
+                                                          ((512, 512), inputs.C1, (0.0,), 64, 36, "kspace")],
+                         ids=["2d-1024", "3d-256", "2d-512-kspace"])
+def test_tile_orders_give_the_same_results(hf, shape, cfg, levels, nr, nt, noise):
+    # contiguous chunks and interleaved tiles transform the same columns; only
+    # the order of the Parseval and bin sums changes, so every order matches the
+    # oracle and the fields agree to an ulp of their normalisation
+    gf, of = filters(hf, **inputs.filter_kwargs(cfg))
+    plan = hf.Plan(shape, kspace=noise == "kspace")
+    hf.hufield_plan_set_bins(plan, nr, nt)
+    assert hf.hufield_plan_order(plan) == 0
+    want = oracle.pipeline(shape, of, 4, 0, levels=levels, nr=nr, ntheta=nt, noise=noise)
+    ref = None
+    for tile, order in ((0, 1), (0, 2), (2, 1), (2, 2), (0, 0)):
+        hf.hufield_plan_set_tile(plan, tile)
+        hf.hufield_plan_set_order(plan, order)
+        assert hf.hufield_plan_order(plan) == order
+        got = run_pipeline(hf, plan, gf, shape, 4, 0, levels, nr, nt)
+        compare(got, want, levels, int(np.prod(shape)))
+        if ref is None:
+            ref = got
+        else:
+            np.testing.assert_allclose(got["f"], ref["f"], rtol=3e-7, atol=3e-7 * np.abs(ref["f"]).max())
+            np.testing.assert_allclose(got["sums_m"], ref["sums_m"], rtol=1e-5, atol=1e-9 * ref["sums_m"].max())
+            np.testing.assert_allclose(got["sums_f"], ref["sums_f"], rtol=1e-5, atol=1e-9 * ref["sums_f"].max())
+            np.testing.assert_array_equal(got["counts_m"], ref["counts_m"])
+    with pytest.raises(hf.HufieldError):
+        hf.hufield_plan_set_order(plan, 3)
