@@ -57,6 +57,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same ten rounds with the round keys given: keys[2r], keys[2r + 1] =
+// (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85).  A launch whose threads share one
+// key passes them as kernel parameters, read as operands of the XORs, instead
+// of bumping the key in every thread.
+__device__ __forceinline__ uint4 philox4x32_10_keyed(uint4 c, const uint32_t (&keys)[20]) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ keys[2 * round], lo1, hi0 ^ c.w ^ keys[2 * round + 1], lo0);
+    }
+    return c;
+}
+
 // Words of the noise block j of field (seed, field_idx).
 __device__ __forceinline__ uint4 noise_block(uint64_t seed, uint32_t field_idx, uint64_t j) {
     return philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), field_idx, 0u), (uint32_t)seed,

@@ -31,12 +31,25 @@ KernelInfo cols_kernel_filter(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_bins(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_kspace(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_filter_batch(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_filter_pair(int log2l, bool big);
+KernelInfo cols_kernel_bins_pair(int log2l, bool big);
+KernelInfo cols_kernel_kspace_pair(int log2l, bool big);
+KernelInfo cols_kernel_filter_batch_pair(int log2l, bool big);
 
 KernelInfo r2c_kernel(int log2m, bool big, int src) {
     return (src == kSrcNoise || src == kSrcNoiseBatch) ? r2c_kernel_noise(log2m, big, src)
                                                        : r2c_kernel_src(log2m, big, src);
 }
-KernelInfo cols_kernel(int log2l, bool big, int mode, int dir) {
+KernelInfo cols_kernel(int log2l, bool big, int mode, int dir, bool pair) {
+    if (pair) {
+        switch (mode) {
+            case kModeFilter: return cols_kernel_filter_pair(log2l, big);
+            case kModeBins: return cols_kernel_bins_pair(log2l, big);
+            case kModeKspace: return cols_kernel_kspace_pair(log2l, big);
+            case kModeFilterBatch: return cols_kernel_filter_batch_pair(log2l, big);
+            default: return {};
+        }
+    }
     switch (mode) {
         case kModePlain: return cols_kernel_plain(log2l, big, mode, dir);
         case kModeFilter: return cols_kernel_filter(log2l, big, mode, dir);
@@ -401,11 +414,15 @@ bool col_big(const hufield_plan* p, int log2l, long long B, long long a_spec) {
 
 // Column kernels: tiles of TB columns x L rows, double-buffered in shared
 // memory; TB >= 2 keeps a TMA box row at 16 bytes or more.  At most
-// p->col_cap[mode] CTAs per SM (kColCapDefault unless autotuned).
+// p->col_cap[mode] CTAs per SM (kColCapDefault unless autotuned).  radial:
+// the binning modes' bins are radial only, so a pairable tile takes the paired
+// staging order (the layout build_bin_table gives such a tile's table).
 bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, long long a_spec,
-                size_t extra_smem, KernelInfo& k, Launch& L) {
+                size_t extra_smem, KernelInfo& k, Launch& L, bool radial = false) {
     const bool big = col_big(p, log2l, B, a_spec);
     k = cols_kernel(log2l, big, mode, dir);
+    if (k.fn && radial && mode != kModePlain && pairable_tile(elems_for(log2l), k.threads))
+        k = cols_kernel(log2l, big, mode, dir, true);
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
     L.smem = k.fixed_smem + extra_smem;
@@ -726,6 +743,10 @@ int forward_rows_and_mid(hufield_plan* p, int src, const void* y, uint64_t seed,
     ra.nrows = nrows;
     ra.seed = seed;
     ra.field_idx = field_idx;
+    for (int r = 0; r < 10; ++r) {  // Philox round keys of the seed
+        ra.keys[2 * r] = (uint32_t)seed + (uint32_t)r * 0x9E3779B9u;
+        ra.keys[2 * r + 1] = (uint32_t)(seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
     ra.tw = p->tw;
     Launch L;
     const KernelInfo k = pick_row(p->logM, nrows, r2c_kernel, src);
@@ -773,7 +794,7 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
                                                        : 0);
     Launch L;
     KernelInfo k;
-    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, 1, extra, k, L)) return HUFIELD_ERR_CUDA;
+    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, 1, extra, k, L, bp.ntheta == 1)) return HUFIELD_ERR_CUDA;
     set_tiles(p, ca, k.log2_lines, kz < 0 ? (1ll << p->logM) : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     const int kind = (mode == kModeFilter || mode == kModeKspace || mode == kModeFilterBatch) ? kPassFilter

@@ -47,6 +47,7 @@ struct RowArgs {
     const unsigned* fidx;
     int log2_rows_field;
     long long nrows_valid;  // kSrcNoiseBatch: rows at or past this (the last tile's tail) are not written
+    unsigned int keys[20];  // kSrcNoise: the Philox round keys of seed (philox4x32_10_keyed)
 };
 
 struct C2RArgs {
@@ -382,7 +383,8 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks_r2c(LOG
             const long long gq = row0 * (M / 2) + q;  // global block index
             float4 x;
             if constexpr (SRC == kSrcNoise) {
-                x = box_muller(noise_block(a.seed, a.field_idx, (unsigned long long)gq));
+                x = box_muller(philox4x32_10_keyed(
+                    make_uint4((uint32_t)gq, (uint32_t)((unsigned long long)gq >> 32), a.field_idx, 0u), a.keys));
             } else if constexpr (SRC == kSrcNoiseBatch) {
                 // a row holds M / 2 blocks of four reals; the last tile may run past the fields
                 if ((gq >> (LOG2M - 1)) < a.nrows_valid) {
@@ -808,7 +810,11 @@ struct ColGeo {
         (size_t)nbuf * tile_elems * 8 + (size_t)plan_twiddle_slots<LOG2L>() * 8 + (size_t)nbuf * 8;
 };
 
-template <int LOG2L, int LOGTB, int MODE, int DIR>
+// PAIR: the staging of the filter and bins modes in the paired order (radial
+// bins only, pairable tiles; see stage_o), chosen by the host with the bin
+// table's layout.  Each layout is its own kernel: one that holds both staging
+// loops needs more registers than either (the 512^3 filter pass spilled).
+template <int LOG2L, int LOGTB, int MODE, int DIR, bool PAIR>
 __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(MODE, Geo<LOG2L, LOGTB, false>::T))
     k_cols(const __grid_constant__ ColArgs a) {
     using CG = ColGeo<LOG2L, LOGTB, MODE>;
@@ -827,6 +833,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     // paired staging needs 16 values per thread (L >= 16); left out of the
     // 512-thread tiles, where the second binning variant costs spills
     constexpr bool kPairable = kAcc && pairable_tile(E, T);
+    static_assert(!PAIR || kPairable, "paired staging on a pairable tile of a binning mode only");
     constexpr bool kLoad = MODE != kModeKspace;
     static_assert(TB >= 2, "k-space mode pairs rely on two columns per tile");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -976,37 +983,40 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
             }
         }
         // the bins of the E modes this thread will own after the staging
-        // (tile order: element (b, l) at b L + l, thread t owns t E .. t E + E - 1)
+        // (tile order: element (b, l) at b L + l, thread t owns t E .. t E + E - 1),
+        // loaded once the forward FFT is done so that they hold no registers through it
         uint32_t binw[E / 2 > 0 ? E / 2 : 1];
-        if constexpr (kAcc) {
-            if (nb > 0) {
-                // E entries per thread (E/2 pair bins when paired, see stage_o)
-                const int per = (kPairable && a.bp.ntheta == 1) ? E / 2 : E;
-                const unsigned short* src = a.bintab + tcol * (tile_elems / E * per) + t * per;
-                if (per == E / 2 && E >= 16) {
+        auto load_binw = [&]() {
+            if constexpr (kAcc) {
+                if (nb > 0) {
+                    // E entries per thread (E/2 pair bins when paired, see stage_o)
+                    constexpr int per = PAIR ? E / 2 : E;
+                    const unsigned short* src = a.bintab + tcol * (tile_elems / E * per) + t * per;
+                    if constexpr (per == E / 2 && E >= 16) {
 #pragma unroll
-                    for (int q = 0; q < E / 16; ++q) {
-                        const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
-                        binw[4 * q] = w4.x;
-                        binw[4 * q + 1] = w4.y;
-                        binw[4 * q + 2] = w4.z;
-                        binw[4 * q + 3] = w4.w;
+                        for (int q = 0; q < E / 16; ++q) {
+                            const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
+                            binw[4 * q] = w4.x;
+                            binw[4 * q + 1] = w4.y;
+                            binw[4 * q + 2] = w4.z;
+                            binw[4 * q + 3] = w4.w;
+                        }
+                    } else if constexpr (E >= 8) {
+#pragma unroll
+                        for (int q = 0; q < E / 8; ++q) {
+                            const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
+                            binw[4 * q] = w4.x;
+                            binw[4 * q + 1] = w4.y;
+                            binw[4 * q + 2] = w4.z;
+                            binw[4 * q + 3] = w4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < E / 2; ++q) binw[q] = __ldg(reinterpret_cast<const uint32_t*>(src) + q);
                     }
-                } else if constexpr (E >= 8) {
-#pragma unroll
-                    for (int q = 0; q < E / 8; ++q) {
-                        const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(src) + q);
-                        binw[4 * q] = w4.x;
-                        binw[4 * q + 1] = w4.y;
-                        binw[4 * q + 2] = w4.z;
-                        binw[4 * q + 3] = w4.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < E / 2; ++q) binw[q] = __ldg(reinterpret_cast<const uint32_t*>(src) + q);
                 }
             }
-        }
+        };
         float2 v[E];
         if constexpr (MODE == kModePlain && DIR > 0) {
             for_each_element<G, PI::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
@@ -1020,6 +1030,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                 for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int l) { v[e] = buf[(l << LOGTB) + b]; });
                 fft<G, -1, false>(v, buf, twf, t);
             }
+            load_binw();
             if constexpr (MODE == kModePlain) {
                 __syncthreads();
                 for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) { buf[(l << LOGTB) + b] = v[e]; });
@@ -1069,42 +1080,67 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                 static_assert(T - 1 + ((T - 1) >> 5) * PAD0 < TS0, "staging slots are one-to-one");
                 static_assert(T - 1 + ((T - 1) >> 5) * PAD1 < TS1, "staging slots are one-to-one");
                 static_assert(E * TS0 <= 2 * tile_elems && E * TS1 <= 2 * tile_elems, "staging fits the tile buffer");
-                // radial bins only: n0 and -n0 share every bin (see stage_o)
-                const bool paired = kPairable && a.bp.ntheta == 1;
-                const int TS = paired ? TS1 : TS0, PAD = paired ? PAD1 : PAD0;
                 float pacc = 0.0f;
                 if (nb > 0 || kFilt) {
                     float* ps = reinterpret_cast<float*>(buf);
                     __syncthreads();  // the FFT's last exchange is read
-                    for_each_element<G, PF::last_radix()>(t, [&](int e, int b, int l) {
-                        if constexpr (kFilt) {
-                            float h = 0.0f;
-                            const bool live = !nyq_col && l != L / 2;
-                            if (!fpr.rotated) {
-                                // log2 S >= the larger term: from u_zero on A is 0 exactly.
-                                // The warp skips the amplitude when none of its
-                                // lanes needs it (every thread of the CTA runs this loop).
-                                constexpr unsigned kWarp = T >= 32 ? 0xffffffffu : (1u << T) - 1u;
-                                const float t0 = tab0[l];
-                                const bool need = live && fmaxf(t0, u_col) < fpr.u_zero;
-                                if (__any_sync(kWarp, need)) {
-                                    const float hv = amplitude_from_log2s(fpr, log2_sum2(t0, u_col));
-                                    h = need ? hv : 0.0f;
+                    // Element e of the FFT's output layout sits at l = j + r L/R
+                    // (r = e mod R, j < L/R), so l < L/2 exactly when r < R/2: the
+                    // paired order's m and side follow from r without comparing l.
+                    constexpr int R = PF::last_radix();
+                    constexpr bool P = PAIR;  // radial bins only: n0 and -n0 share every bin
+                    constexpr int TSP = P ? TS1 : TS0, PADP = P ? PAD1 : PAD0;
+                    {
+                        for_each_element<G, R>(t, [&](int e, int b, int l) {
+                            if constexpr (kFilt) {
+                                float h = 0.0f;
+                                const bool live = !nyq_col && l != L / 2;
+                                if (!fpr.rotated) {
+                                    // log2 S >= the larger term: from u_zero on A is 0 exactly.
+                                    // The warp skips the amplitude when none of its
+                                    // lanes needs it (every thread of the CTA runs this loop).
+                                    constexpr unsigned kWarp = T >= 32 ? 0xffffffffu : (1u << T) - 1u;
+                                    const float t0 = tab0[l];
+                                    const bool need = live && fmaxf(t0, u_col) < fpr.u_zero;
+                                    if (__any_sync(kWarp, need)) {
+                                        const float hv = amplitude_from_log2s(fpr, log2_sum2(t0, u_col));
+                                        h = need ? hv : 0.0f;
+                                    }
+                                } else if (live) {
+                                    const float x =
+                                        (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                                    h = filter_amplitude(fpr, x, y, z, a.ndim);
                                 }
-                            } else if (live) {
-                                const float x =
-                                    (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
-                                h = filter_amplitude(fpr, x, y, z, a.ndim);
+                                v[e] = cscale(v[e], h);
                             }
-                            v[e] = cscale(v[e], h);
-                        }
-                        const float pw = wcol * cabs2(v[e]);
-                        pacc += pw;
-                        const int owner = stage_o(b, l, LOG2L, E, paired);
-                        // the Nyquist n0 = -L/2 is dropped from the bins: it stages as 0 next to n0 = 0
-                        ps[stage_i(l, LOG2L, E, paired) * TS + owner + (owner >> 5) * PAD] =
-                            (paired && l == L / 2) ? 0.0f : pw;
-                    });
+                            const float pw = wcol * cabs2(v[e]);
+                            pacc += pw;
+                            int owner, slot_i;
+                            float val = pw;
+                            if constexpr (P) {
+                                // stage_o / stage_i of the paired order
+                                const int r = e & (R - 1);
+                                const int j = l - r * (L / R);
+                                int m;
+                                if (r < R / 2) {
+                                    m = l;
+                                } else if (r > R / 2) {
+                                    m = (R - r) * (L / R) - j;
+                                } else {
+                                    // l = L/2 + j; the Nyquist n0 = -L/2 (j = 0) is dropped from
+                                    // the bins: it stages as 0 next to n0 = 0
+                                    m = j == 0 ? 0 : L / 2 - j;
+                                    if (j == 0) val = 0.0f;
+                                }
+                                owner = b * (L / 16) + (m >> 3);
+                                slot_i = 2 * (m & 7) + (r < R / 2 ? 0 : 1);
+                            } else {
+                                owner = ((b << LOG2L) + l) / E;
+                                slot_i = l & (E - 1);
+                            }
+                            ps[slot_i * TSP + owner + (owner >> 5) * PADP] = val;
+                        });
+                    }
                     __syncthreads();
                     if (nb > 0) {
                         // runs of equal bins (E values, or E/2 pairs), one atomic per run
@@ -1113,10 +1149,11 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                             constexpr bool P = decltype(pair)::value;
                             int cur_bin = -1;
                             float acc = 0.0f;
+                            constexpr int TSP = P ? TS1 : TS0, PADP = P ? PAD1 : PAD0;
 #pragma unroll
                             for (int q = 0; q < K; ++q) {
-                                float pw = ps[(P ? 2 * q : q) * TS + t + (t >> 5) * PAD];
-                                if constexpr (P) pw += ps[(2 * q + 1) * TS + t + (t >> 5) * PAD];
+                                float pw = ps[(P ? 2 * q : q) * TSP + t + (t >> 5) * PADP];
+                                if constexpr (P) pw += ps[(2 * q + 1) * TSP + t + (t >> 5) * PADP];
                                 const int raw = (int)((binw[q >> 1] >> (16 * (q & 1))) & 0xffffu);
                                 const int bin = raw == 0xffff ? -1 : raw;
                                 if (bin != cur_bin) {
@@ -1128,15 +1165,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                             }
                             if (cur_bin >= 0 && acc != 0.0f) atomicAdd(fbin + cur_bin, acc);
                         };
-                        if constexpr (kPairable) {
-                            if (paired) {
-                                binning(std::integral_constant<int, E / 2>{}, std::true_type{});
-                            } else {
-                                binning(std::integral_constant<int, E>{}, std::false_type{});
-                            }
-                        } else {
-                            binning(std::integral_constant<int, E>{}, std::false_type{});
-                        }
+                        binning(std::integral_constant<int, PAIR ? E / 2 : E>{}, std::bool_constant<PAIR>{});
                     }
                 }
                 if constexpr (kFilt) {
