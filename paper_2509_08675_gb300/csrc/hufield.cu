@@ -31,29 +31,35 @@ KernelInfo cols_kernel_filter(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_bins(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_kspace(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_filter_batch(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_filter_rot(int log2l, bool big, int mode, int dir);
+KernelInfo cols_kernel_kspace_rot(int log2l, bool big, int mode, int dir);
 KernelInfo cols_kernel_filter_pair(int log2l, bool big);
+KernelInfo cols_kernel_filter_pair_rot(int log2l, bool big);
 KernelInfo cols_kernel_bins_pair(int log2l, bool big);
 KernelInfo cols_kernel_kspace_pair(int log2l, bool big);
+KernelInfo cols_kernel_kspace_pair_rot(int log2l, bool big);
 KernelInfo cols_kernel_filter_batch_pair(int log2l, bool big);
 
 KernelInfo r2c_kernel(int log2m, bool big, int src) {
     return (src == kSrcNoise || src == kSrcNoiseBatch) ? r2c_kernel_noise(log2m, big, src)
                                                        : r2c_kernel_src(log2m, big, src);
 }
-KernelInfo cols_kernel(int log2l, bool big, int mode, int dir, bool pair) {
+KernelInfo cols_kernel(int log2l, bool big, int mode, int dir, bool pair, bool rot) {
     if (pair) {
         switch (mode) {
-            case kModeFilter: return cols_kernel_filter_pair(log2l, big);
+            case kModeFilter: return rot ? cols_kernel_filter_pair_rot(log2l, big) : cols_kernel_filter_pair(log2l, big);
             case kModeBins: return cols_kernel_bins_pair(log2l, big);
-            case kModeKspace: return cols_kernel_kspace_pair(log2l, big);
+            case kModeKspace: return rot ? cols_kernel_kspace_pair_rot(log2l, big) : cols_kernel_kspace_pair(log2l, big);
             case kModeFilterBatch: return cols_kernel_filter_batch_pair(log2l, big);
             default: return {};
         }
     }
     switch (mode) {
         case kModePlain: return cols_kernel_plain(log2l, big, mode, dir);
-        case kModeFilter: return cols_kernel_filter(log2l, big, mode, dir);
-        case kModeKspace: return cols_kernel_kspace(log2l, big, mode, dir);
+        case kModeFilter: return rot ? cols_kernel_filter_rot(log2l, big, mode, dir)
+                                     : cols_kernel_filter(log2l, big, mode, dir);
+        case kModeKspace: return rot ? cols_kernel_kspace_rot(log2l, big, mode, dir)
+                                     : cols_kernel_kspace(log2l, big, mode, dir);
         case kModeFilterBatch: return cols_kernel_filter_batch(log2l, big, mode, dir);
         default: return cols_kernel_bins(log2l, big, mode, dir);
     }
@@ -416,13 +422,15 @@ bool col_big(const hufield_plan* p, int log2l, long long B, long long a_spec) {
 // memory; TB >= 2 keeps a TMA box row at 16 bytes or more.  At most
 // p->col_cap[mode] CTAs per SM (kColCapDefault unless autotuned).  radial:
 // the binning modes' bins are radial only, so a pairable tile takes the paired
-// staging order (the layout build_bin_table gives such a tile's table).
+// staging order (the layout build_bin_table gives such a tile's table).  rot:
+// the filter and k-space modes' filter has a rotated norm (their kernels fix
+// the norm at compile time).
 bool col_launch(const hufield_plan* p, int log2l, int mode, int dir, long long B, long long A, long long a_spec,
-                size_t extra_smem, KernelInfo& k, Launch& L, bool radial = false) {
+                size_t extra_smem, KernelInfo& k, Launch& L, bool radial = false, bool rot = false) {
     const bool big = col_big(p, log2l, B, a_spec);
-    k = cols_kernel(log2l, big, mode, dir);
+    k = cols_kernel(log2l, big, mode, dir, false, rot);
     if (k.fn && radial && mode != kModePlain && pairable_tile(elems_for(log2l), k.threads))
-        k = cols_kernel(log2l, big, mode, dir, true);
+        k = cols_kernel(log2l, big, mode, dir, true, rot);
     if (!k.fn || B < (1ll << k.log2_lines)) return false;
     L.block = k.threads;
     L.smem = k.fixed_smem + extra_smem;
@@ -794,7 +802,8 @@ int axis0_pass(hufield_plan* p, int mode, float2* data, long long nbatch, const 
                                                        : 0);
     Launch L;
     KernelInfo k;
-    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, 1, extra, k, L, bp.ntheta == 1)) return HUFIELD_ERR_CUDA;
+    if (!col_launch(p, p->log2n[0], mode, -1, ca.B, ca.A, 1, extra, k, L, bp.ntheta == 1, fp && fp->rotated))
+        return HUFIELD_ERR_CUDA;
     set_tiles(p, ca, k.log2_lines, kz < 0 ? (1ll << p->logM) : kz, L);
     if (!col_map(p, &ca.map, data, ca.B, p->log2n[0], ca.A, ca.bstride, k.log2_lines)) return HUFIELD_ERR_CUDA;
     const int kind = (mode == kModeFilter || mode == kModeKspace || mode == kModeFilterBatch) ? kPassFilter

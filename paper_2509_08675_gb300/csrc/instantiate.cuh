@@ -22,26 +22,47 @@ KernelInfo c2r_info() {
             map_bits_packed(LOG2M, LOGTR, OUTDT == kOutBatch)};
 }
 
-template <int LOG2L, int LOGTB, int MODE, int DIR, bool PAIR = false>
+template <int LOG2L, int LOGTB, int MODE, int DIR, bool PAIR = false, int ROT = 2>
 KernelInfo cols_info() {
     using CG = ColGeo<LOG2L, LOGTB, MODE>;
-    return {reinterpret_cast<const void*>(&k_cols<LOG2L, LOGTB, MODE, DIR, PAIR>), CG::G::T, LOGTB, CG::fixed_bytes};
+    return {reinterpret_cast<const void*>(&k_cols<LOG2L, LOGTB, MODE, DIR, PAIR, ROT>), CG::G::T, LOGTB,
+            CG::fixed_bytes};
+}
+
+// Every length's wide and two-column tiles of one mode, direction and norm
+// (the plain staging order).  The wide tile's columns: 256 up to L = 16,
+// 4096 / L from 32 to 512, 8192 / L from 1024 (col_logtb).
+template <int MODE, int DIR, int ROT = 2>
+KernelInfo cols_table(int log2l, bool big) {
+    switch (log2l) {
+        case 3: return big ? cols_info<3, 8, MODE, DIR, false, ROT>() : cols_info<3, 1, MODE, DIR, false, ROT>();
+        case 4: return big ? cols_info<4, 8, MODE, DIR, false, ROT>() : cols_info<4, 1, MODE, DIR, false, ROT>();
+        case 5: return big ? cols_info<5, 7, MODE, DIR, false, ROT>() : cols_info<5, 1, MODE, DIR, false, ROT>();
+        case 6: return big ? cols_info<6, 6, MODE, DIR, false, ROT>() : cols_info<6, 1, MODE, DIR, false, ROT>();
+        case 7: return big ? cols_info<7, 5, MODE, DIR, false, ROT>() : cols_info<7, 1, MODE, DIR, false, ROT>();
+        case 8: return big ? cols_info<8, 4, MODE, DIR, false, ROT>() : cols_info<8, 1, MODE, DIR, false, ROT>();
+        case 9: return big ? cols_info<9, 3, MODE, DIR, false, ROT>() : cols_info<9, 1, MODE, DIR, false, ROT>();
+        case 10: return big ? cols_info<10, 3, MODE, DIR, false, ROT>() : cols_info<10, 1, MODE, DIR, false, ROT>();
+        case 11: return big ? cols_info<11, 2, MODE, DIR, false, ROT>() : cols_info<11, 1, MODE, DIR, false, ROT>();
+        case 12: return cols_info<12, 1, MODE, DIR, false, ROT>();
+        default: return {};
+    }
 }
 
 // The paired-staging variants (PAIR = true) of a binning mode on every
 // pairable tile: 16 values per thread and at most 256 threads, i.e. lengths
 // 16 to 512 in the wide tile and 16 to 2048 in the two-column one.
-template <int MODE>
+template <int MODE, int ROT = 2>
 KernelInfo cols_pair_table(int log2l, bool big) {
     switch (log2l) {
-        case 4: return big ? cols_info<4, 8, MODE, -1, true>() : cols_info<4, 1, MODE, -1, true>();
-        case 5: return big ? cols_info<5, 7, MODE, -1, true>() : cols_info<5, 1, MODE, -1, true>();
-        case 6: return big ? cols_info<6, 6, MODE, -1, true>() : cols_info<6, 1, MODE, -1, true>();
-        case 7: return big ? cols_info<7, 5, MODE, -1, true>() : cols_info<7, 1, MODE, -1, true>();
-        case 8: return big ? cols_info<8, 4, MODE, -1, true>() : cols_info<8, 1, MODE, -1, true>();
-        case 9: return big ? cols_info<9, 3, MODE, -1, true>() : cols_info<9, 1, MODE, -1, true>();
-        case 10: return big ? KernelInfo{} : cols_info<10, 1, MODE, -1, true>();
-        case 11: return big ? KernelInfo{} : cols_info<11, 1, MODE, -1, true>();
+        case 4: return big ? cols_info<4, 8, MODE, -1, true, ROT>() : cols_info<4, 1, MODE, -1, true, ROT>();
+        case 5: return big ? cols_info<5, 7, MODE, -1, true, ROT>() : cols_info<5, 1, MODE, -1, true, ROT>();
+        case 6: return big ? cols_info<6, 6, MODE, -1, true, ROT>() : cols_info<6, 1, MODE, -1, true, ROT>();
+        case 7: return big ? cols_info<7, 5, MODE, -1, true, ROT>() : cols_info<7, 1, MODE, -1, true, ROT>();
+        case 8: return big ? cols_info<8, 4, MODE, -1, true, ROT>() : cols_info<8, 1, MODE, -1, true, ROT>();
+        case 9: return big ? cols_info<9, 3, MODE, -1, true, ROT>() : cols_info<9, 1, MODE, -1, true, ROT>();
+        case 10: return big ? KernelInfo{} : cols_info<10, 1, MODE, -1, true, ROT>();
+        case 11: return big ? KernelInfo{} : cols_info<11, 1, MODE, -1, true, ROT>();
         default: return {};
     }
 }

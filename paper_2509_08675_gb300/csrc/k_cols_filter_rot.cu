@@ -1,0 +1,12 @@
+// Strided-axis kernels with the fused filter, Parseval sum and field bins:
+// rotated norm.
+#include "instantiate.cuh"
+
+namespace hf {
+
+KernelInfo cols_kernel_filter_rot(int log2l, bool big, int mode, int dir) {
+    if (mode != kModeFilter || dir != -1) return {};
+    return cols_table<kModeFilter, -1, 1>(log2l, big);
+}
+
+}  // namespace hf

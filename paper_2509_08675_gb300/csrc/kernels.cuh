@@ -814,7 +814,10 @@ struct ColGeo {
 // bins only, pairable tiles; see stage_o), chosen by the host with the bin
 // table's layout.  Each layout is its own kernel: one that holds both staging
 // loops needs more registers than either (the 512^3 filter pass spilled).
-template <int LOG2L, int LOGTB, int MODE, int DIR, bool PAIR>
+// ROT: the filter's norm, separable (0) or rotated (1), fixed at compile time
+// for the filter and k-space modes (the host picks the kernel from the
+// filter); 2 reads it from the filter at run time (batches of filters).
+template <int LOG2L, int LOGTB, int MODE, int DIR, bool PAIR, int ROT>
 __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(MODE, Geo<LOG2L, LOGTB, false>::T))
     k_cols(const __grid_constant__ ColArgs a) {
     using CG = ColGeo<LOG2L, LOGTB, MODE>;
@@ -834,6 +837,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
     // 512-thread tiles, where the second binning variant costs spills
     constexpr bool kPairable = kAcc && pairable_tile(E, T);
     static_assert(!PAIR || kPairable, "paired staging on a pairable tile of a binning mode only");
+    static_assert(ROT == 2 || MODE == kModeFilter || MODE == kModeKspace, "a fixed norm for single filters only");
     constexpr bool kLoad = MODE != kModeKspace;
     static_assert(TB >= 2, "k-space mode pairs rely on two columns per tile");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -857,9 +861,11 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
         fpp = &a.fp;
     }
     const FilterParams& fpr = *fpp;
+    // the norm is rotated (not separable per axis)
+    auto rotated = [&]() -> bool { return ROT == 2 ? fpr.rotated != 0 : ROT == 1; };
     // the filter's per-row terms p log2 |kappa_0 / a_0| (separable case)
     auto fill_tab0 = [&]() {
-        if (!fpr.rotated) {
+        if (!rotated()) {
             for (int l = t; l < L; l += T) {
                 const float x = (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
                 tab0[l] = plog2_exact(fabsf(x) * fpr.inv_a[0], fpr.p);
@@ -1055,7 +1061,7 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                     nyq_col = a.ndim == 3 && n1 == -(1 << (a.log2n[1] - 1));
                     y = (float)n1 * __int_as_float((127 + 1 - a.log2n[1]) << 23);
                     z = a.ndim == 3 ? (float)n2 * __int_as_float((127 + 1 - a.log2n[2]) << 23) : 0.0f;
-                    if (!fpr.rotated) {  // separable case: the column's terms of the sum
+                    if (!rotated()) {  // separable case: the column's terms of the sum
                         u_col = plog2_exact(fabsf(y) * fpr.inv_a[1], fpr.p);
                         if (a.ndim == 3) {
                             const float u2 = plog2_exact(fabsf(z) * fpr.inv_a[2], fpr.p);
@@ -1092,10 +1098,13 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                     constexpr int TSP = P ? TS1 : TS0, PADP = P ? PAD1 : PAD0;
                     {
                         for_each_element<G, R>(t, [&](int e, int b, int l) {
+                            const int r = e & (R - 1);    // compile-time digit
+                            const int j = l - r * (L / R);  // per butterfly
                             if constexpr (kFilt) {
                                 float h = 0.0f;
-                                const bool live = !nyq_col && l != L / 2;
-                                if (!fpr.rotated) {
+                                // the Nyquist row n0 = -L/2 (l = L/2: digit R/2, j = 0) has A = 0
+                                const bool live = !nyq_col && !(r == R / 2 && j == 0);
+                                if (!rotated()) {
                                     // log2 S >= the larger term: from u_zero on A is 0 exactly.
                                     // The warp skips the amplitude when none of its
                                     // lanes needs it (every thread of the CTA runs this loop).
@@ -1107,8 +1116,8 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                                         h = need ? hv : 0.0f;
                                     }
                                 } else if (live) {
-                                    const float x =
-                                        (float)signed_index(l, LOG2L) * __int_as_float((127 + 1 - LOG2L) << 23);
+                                    const int n0 = r < R / 2 ? l : l - L;  // signed index of l
+                                    const float x = (float)n0 * __int_as_float((127 + 1 - LOG2L) << 23);
                                     h = filter_amplitude(fpr, x, y, z, a.ndim);
                                 }
                                 v[e] = cscale(v[e], h);
@@ -1119,8 +1128,6 @@ __global__ void __launch_bounds__(Geo<LOG2L, LOGTB, false>::T, min_blocks_cols(M
                             float val = pw;
                             if constexpr (P) {
                                 // stage_o / stage_i of the paired order
-                                const int r = e & (R - 1);
-                                const int j = l - r * (L / R);
                                 int m;
                                 if (r < R / 2) {
                                     m = l;

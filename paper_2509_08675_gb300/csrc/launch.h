@@ -27,7 +27,8 @@ constexpr int col_logtb(int log2l, bool big) {
 KernelInfo r2c_kernel(int log2m, bool big, int src);
 KernelInfo c2r_kernel(int log2m, bool big, int out_dtype);
 // pair: the variant staged in the paired order of radial bins (binning modes
-// on pairable tiles; see k_cols)
-KernelInfo cols_kernel(int log2l, bool big, int mode, int dir, bool pair = false);
+// on pairable tiles); rot: the filter and k-space modes' variant for a rotated
+// norm (see k_cols)
+KernelInfo cols_kernel(int log2l, bool big, int mode, int dir, bool pair = false, bool rot = false);
 
 }  // namespace hf
