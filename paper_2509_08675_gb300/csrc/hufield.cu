@@ -928,7 +928,9 @@ int run_field(hufield_plan* p, const hufield_filter* f, uint64_t seed, uint32_t 
     ca.wait_budget = p->wait_budget;
     ca.inject_skip = p->inject_timeout ? 1 : 0;
     Launch L;
-    const KernelInfo k = pick_row(p->logM, ca.nrows, c2r_kernel, out_dtype == HUFIELD_BF16 ? 1 : 0);
+    // variant: the output type, plus 4 for a single sign-map level (its own kernels)
+    const KernelInfo k =
+        pick_row(p->logM, ca.nrows, c2r_kernel, (out_dtype == HUFIELD_BF16 ? 1 : 0) | (ca.nlev == 1 ? 4 : 0));
     if (!row_launch(p, k, ca.nrows, L)) return HUFIELD_ERR_CUDA;
     // one-bit maps of short rows are ORed into words that must start clear
     if (out_maps && ca.map_bits && !k.map_bits_packed && nlev > 0)

@@ -14,10 +14,10 @@ KernelInfo r2c_info() {
             (size_t)G::TB * G::L * 8 + (size_t)G::L * 8 + (size_t)TwTables<LOG2M, false>::size() * 8};
 }
 
-template <int LOG2M, int LOGTR, int OUTDT>
+template <int LOG2M, int LOGTR, int OUTDT, bool ONE>
 KernelInfo c2r_info() {
     using G = Geo<LOG2M, LOGTR, true>;
-    return {reinterpret_cast<const void*>(&k_c2r<LOG2M, LOGTR, OUTDT>), G::T, LOGTR,
+    return {reinterpret_cast<const void*>(&k_c2r<LOG2M, LOGTR, OUTDT, ONE>), G::T, LOGTR,
             (size_t)2 * G::TB * G::L * 8 + (size_t)G::L * 8 + (size_t)plan_twiddle_slots<LOG2M>() * 8 + 16,
             map_bits_packed(LOG2M, LOGTR, OUTDT == kOutBatch)};
 }
@@ -27,6 +27,25 @@ KernelInfo cols_info() {
     using CG = ColGeo<LOG2L, LOGTB, MODE>;
     return {reinterpret_cast<const void*>(&k_cols<LOG2L, LOGTB, MODE, DIR, PAIR, ROT>), CG::G::T, LOGTB,
             CG::fixed_bytes};
+}
+
+// Every row length's wide and one-row tiles of the c2r kernel for one output
+// type and level count (ONE: a single sign-map level).
+template <int OUTDT, bool ONE>
+KernelInfo c2r_table(int log2m, bool big) {
+    switch (log2m) {
+        case 2: return big ? c2r_info<2, 8, OUTDT, ONE>() : c2r_info<2, 0, OUTDT, ONE>();
+        case 3: return big ? c2r_info<3, 8, OUTDT, ONE>() : c2r_info<3, 0, OUTDT, ONE>();
+        case 4: return big ? c2r_info<4, 8, OUTDT, ONE>() : c2r_info<4, 0, OUTDT, ONE>();
+        case 5: return big ? c2r_info<5, 7, OUTDT, ONE>() : c2r_info<5, 0, OUTDT, ONE>();
+        case 6: return big ? c2r_info<6, 6, OUTDT, ONE>() : c2r_info<6, 0, OUTDT, ONE>();
+        case 7: return big ? c2r_info<7, 5, OUTDT, ONE>() : c2r_info<7, 0, OUTDT, ONE>();
+        case 8: return big ? c2r_info<8, 4, OUTDT, ONE>() : c2r_info<8, 0, OUTDT, ONE>();
+        case 9: return big ? c2r_info<9, 3, OUTDT, ONE>() : c2r_info<9, 0, OUTDT, ONE>();
+        case 10: return big ? c2r_info<10, 2, OUTDT, ONE>() : c2r_info<10, 0, OUTDT, ONE>();
+        case 11: return big ? c2r_info<11, 1, OUTDT, ONE>() : c2r_info<11, 0, OUTDT, ONE>();
+        default: return {};
+    }
 }
 
 // Every length's wide and two-column tiles of one mode, direction and norm

@@ -431,8 +431,18 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks_r2c(LOG
 // shared-memory buffers, the next tile in flight while the current one is
 // transformed; the current buffer then serves as the FFT exchange area.
 // ---------------------------------------------------------------------------
-template <int LOG2M, int LOGTR, int OUTDT>
-__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG2M, LOGTR, true>::T))
+// ONE: a single sign-map level, known at compile time (the host picks it for
+// nlev = 1; batches always have one level per field): the field's registers
+// are free once its map is formed, so single-field rows of up to 256 points
+// fit three 256-thread CTAs per SM at 80 registers without spills (the
+// 512-point rows would spill there and keep two).
+constexpr int min_blocks_c2r(int log2m, int T, bool one, int outdt) {
+    return (one && outdt != kOutBatch && log2m <= 8 && T == 256) ? 3 : min_blocks(T);
+}
+
+template <int LOG2M, int LOGTR, int OUTDT, bool ONE>
+__global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T,
+                                  min_blocks_c2r(LOG2M, Geo<LOG2M, LOGTR, true>::T, ONE, OUTDT))
     k_c2r(const __grid_constant__ C2RArgs a) {
     using G = Geo<LOG2M, LOGTR, true>;
     constexpr int M = G::L;
@@ -553,7 +563,8 @@ __global__ void __launch_bounds__(Geo<LOG2M, LOGTR, true>::T, min_blocks(Geo<LOG
                 }
             });
         }
-        for (int lev = 0; lev < a.nlev; ++lev) {
+        const int nlev = ONE ? 1 : a.nlev;
+        for (int lev = 0; lev < nlev; ++lev) {
             float2 u[E];
             if constexpr (OUTDT == kOutBatch) {  // one level per field
                 for_each_element<G, PF::first_radix()>(t, [&](int e, int b, int j) {

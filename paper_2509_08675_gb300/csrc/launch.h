@@ -25,7 +25,8 @@ constexpr int col_logtb(int log2l, bool big) {
 }
 
 KernelInfo r2c_kernel(int log2m, bool big, int src);
-KernelInfo c2r_kernel(int log2m, bool big, int out_dtype);
+// variant: the output type (C2ROut), plus 4 for a single sign-map level
+KernelInfo c2r_kernel(int log2m, bool big, int variant);
 // pair: the variant staged in the paired order of radial bins (binning modes
 // on pairable tiles); rot: the filter and k-space modes' variant for a rotated
 // norm (see k_cols)
