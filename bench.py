@@ -50,11 +50,11 @@ METRIC = "voxels/s for gen+threshold+S(k)"
 # dominant pass from an ncu capture of the current kernels, keyed by
 # (workload, pass); None until captured.
 TRAFFIC = {
-    ("ensemble-2d-4096", "cols_bins"): 232.7e6,  # k_cols<12, 1, 2, -1>, 3 maps of 4096^2, per launch
-    ("3d-512", "c2r"): 1566.8e6,  # k_c2r<8, 4, 0>, 512^3, one-bit maps
-    ("3d-512x8", "c2r"): 1566.8e6,  # the same kernel on the same lattice
-    ("3d-512", "r2c"): 476.3e6,  # k_r2c<8, 4, 0>, 512^3
-    ("3d-512x8", "r2c"): 476.3e6,
+    ("ensemble-2d-4096", "cols_bins"): 232.5e6,  # k_cols<12, 1, 2, -1, 0, 2>, 3 maps of 4096^2, per launch
+    ("3d-512", "c2r"): 1566.0e6,  # k_c2r<8, 4, 0, 1>, 512^3, one-bit map
+    ("3d-512x8", "c2r"): 1566.0e6,  # the same kernel on the same lattice
+    ("3d-512", "r2c"): 475.7e6,  # k_r2c<8, 4, 0>, 512^3
+    ("3d-512x8", "r2c"): 475.7e6,
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 E2E_CHUNK = 4  # fields per ensemble call in the end-to-end leg (--e2e-chunk)
