@@ -107,6 +107,11 @@ def _lib():
             lib.or_inverse_realness.argtypes = [C.c_int, i64p, fp, C.c_uint64, C.c_uint32,
                                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]
             lib.or_threshold.argtypes = [C.c_int64, f64p, C.c_double, i8p]
+            f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
+            lib.or_sd_gain.argtypes = [C.c_int64, f32p, C.c_float]
+            lib.or_sd_gain.restype = C.c_float
+            lib.or_sigma_delta.argtypes = [C.c_int64, C.c_int64, f32p, C.c_float, C.c_float, C.c_int64, i8p,
+                                           C.c_void_p]
             lib.or_angle_table.argtypes = [C.c_int, i64p, i64p]
             lib.or_bin_of.argtypes = [C.c_int, i64p, i64p, C.c_int, C.c_int, i64p, i64p]
             lib.or_bin_of.restype = C.c_int
@@ -224,6 +229,30 @@ def threshold(f: np.ndarray, t: float) -> np.ndarray:
     m = np.zeros(f.size, np.int8)
     _lib().or_threshold(f.size, f.reshape(-1), float(t), m)
     return m.reshape(f.shape)
+
+
+def sd_gain(f: np.ndarray, t: float = 0.0) -> float:
+    """Automatic gain of the noise-shaped binarisation: 1 / max |f - t| in FP32 (0 when f == t)."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    return float(_lib().or_sd_gain(f.size, f.reshape(-1), float(t)))
+
+
+def sigma_delta(f: np.ndarray, t: float = 0.0, gain: float = 0.0, strip: int = 0, return_error: bool = False):
+    """Noise-shaped binarisation of a stored FP32 field (first-order sigma-delta
+    along axis 0 in strips of ``strip`` rows, 0: min(n0, 256)); ``gain`` 0 asks
+    for 1 / max |f - t|.  Returns the +-1 map as int8 (and the error state after
+    each site, FP32, with ``return_error``)."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    n0 = f.shape[0]
+    h = min(n0, 256) if strip == 0 else int(strip)
+    if h < 1 or n0 % h:
+        raise ValueError("strip must divide the length of axis 0")
+    m = np.zeros(f.size, np.int8)
+    err = np.zeros(f.size, np.float32) if return_error else None
+    _lib().or_sigma_delta(n0, f.size // n0, f.reshape(-1), float(t), float(gain), h, m,
+                          err.ctypes.data if return_error else None)
+    m = m.reshape(f.shape)
+    return (m, err.reshape(f.shape)) if return_error else m
 
 
 def angle_table(ntheta: int):

@@ -21,6 +21,8 @@
  *   inverse    f = IDFT(A * F), Eq. (9), real part
  *   normalise  f <- sigma_f (f - <f>) / sqrt(Var f), Eq. (15)
  *   threshold  sign map, Sec. II.B (last paragraph): f >= t -> +1 else -1
+ *   binarise   noise-shaped binarisation (a reading of the future work of
+ *              Sec. IV): sigma-delta modulation along axis 0, in FP32
  *   spectrum   S(n) = |DFT(y)(n)|^2 / N, binned radially (and by angle in 2D)
  *   window     sigma_F^2(R), Eq. (1): variance of the field averaged over a
  *              ball of radius R, from the spectrum
@@ -342,6 +344,58 @@ void or_inverse_realness(int ndim, const int64_t *n, const or_filter *f, uint64_
 /* Sign map, Sec. II.B: f >= t gives +1, else -1. */
 void or_threshold(int64_t N, const double *f, double t, int8_t *m) {
     for (int64_t i = 0; i < N; ++i) m[i] = f[i] >= t ? (int8_t)1 : (int8_t)-1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Noise-shaped binarisation.  Sec. II.B notes that the sign map generally   */
+/* loses the field's hyperuniform scaling, and Sec. IV leaves binarisations  */
+/* that keep it to future work without defining one.  This is the reading    */
+/* built here: first-order sigma-delta modulation (one-dimensional error     */
+/* diffusion) along axis 0, in strips of h consecutive rows.  With           */
+/*   u(x) = clamp(g (f(x) - t), -1, 1),                                      */
+/* each column of each strip runs, for rows r = 0 .. h-1 and e = 0 at the    */
+/* strip's first row,                                                        */
+/*   v = u + e,   m = (v >= 0 ? +1 : -1),   e <- v - m.                     */
+/* Then |e| <= 1 and m - u = e_prev - e: the quantisation error is a first   */
+/* difference along axis 0, so its spectrum carries 4 sin^2(pi n0 / N0),     */
+/* which vanishes as k -> 0, and the map's spectrum near k = 0 follows that  */
+/* of g (f - t).  g = 0 asks for g = 1 / max |f - t| (then |u| <= 1 and no   */
+/* clamping); M = 0 gives u = 0.                                             */
+/*                                                                           */
+/* A floating-point comparison decides each site, so the decision is taken   */
+/* in the precision the GPU kernel uses: every operation below is one FP32   */
+/* operation rounded to nearest (this file is compiled without contraction). */
+/* err, if not NULL, receives e after each site.                             */
+/* ------------------------------------------------------------------------ */
+float or_sd_gain(int64_t N, const float *f, float t) {
+    float M = 0.0f;
+    for (int64_t i = 0; i < N; ++i) {
+        const float a = fabsf(f[i] - t);
+        if (a > M) M = a;
+    }
+    return M > 0.0f ? 1.0f / M : 0.0f;
+}
+
+void or_sigma_delta(int64_t n0, int64_t cols, const float *f, float t, float g, int64_t h, int8_t *m,
+                    float *err) {
+    if (g == 0.0f) g = or_sd_gain(n0 * cols, f, t);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < cols; ++c) {
+        for (int64_t s = 0; s < n0 / h; ++s) {
+            float e = 0.0f;
+            for (int64_t r = 0; r < h; ++r) {
+                const int64_t i = (s * h + r) * cols + c;
+                const float d = f[i] - t;
+                const float y = d * g;
+                const float u = fminf(fmaxf(y, -1.0f), 1.0f);
+                const float v = u + e;
+                const float q = v >= 0.0f ? 1.0f : -1.0f;
+                m[i] = (int8_t)q;
+                e = v - q;
+                if (err) err[i] = e;
+            }
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */
