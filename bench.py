@@ -562,7 +562,7 @@ def main():
     ap.add_argument("--designs", type=int, default=0, help="surrogate: inverse designs (default 500)")
     ap.add_argument("--plain-sample", type=int, default=0, help="surrogate: targets searched by the plain generator")
     ap.add_argument("--fields", type=int, default=0, help="override fields per step (small profiling cases)")
-    ap.add_argument("--also", default="3d-512,3d-512x8,ragged-2000",
+    ap.add_argument("--also", default="3d-512,3d-512x8,ragged-2000,binarise",
                     help="comma-separated workloads timed in the same run ('' for none)")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="fields per ensemble call in the end-to-end leg (default %d)" % E2E_CHUNK)
@@ -615,6 +615,9 @@ def main():
         e2e = measure_e2e(hf, torch, res["plan"], res["filt"], wl, args, *res["bufs"], res["field0"], dist, world)
     also = {}
     for name in [n for n in args.also.split(",") if n and n != args.workload] if world == 1 else []:
+        if name == "binarise":
+            also[name] = binarise_line(hf, torch, args)
+            continue
         if name == "ragged-2000":
             t_r = time.perf_counter()
             r2 = ragged_line(hf, torch, args, cpu=False)
@@ -783,6 +786,50 @@ def measure(hf, torch, wl, name, args, rank, world, dist):
             "gpu_launches": sum(p["launches"] for p in passes.values()) + (args.steps if nf >= 2 else 0),
             "clocks": clk,
             "plan": plan, "filt": filt, "bufs": (out_f, maps, sf, cf, sm, cm, ws), "field0": field0}
+
+
+def binarise_line(hf, torch, args, shapes=("ensemble-2d-4096", "3d-512")):
+    """Noise-shaped binarisation (hufield_binarise) of one generated field of each
+    lattice, maps in the bench's format, automatic gain (the max |f - t| pass, then
+    the sigma-delta pass): device time per call by CUDA events on the launching
+    stream, L2 flushed between calls.  Bytes per voxel: the field read twice, the
+    map written once (4 + 4 + 1/8 with one-bit maps, 4 + 4 + 1 with int8)."""
+    peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    bits = args.maps == "bits"
+    out = {}
+    for name in shapes:
+        wl = WORKLOADS[name]
+        shape = tuple(wl["shape"])
+        N = math.prod(shape)
+        filt = hf.Filter(p=wl["p"], axes=wl["axes"], rot=wl["rot"], k0=wl["k0"], width=wl["width"],
+                         supp=wl["supp"])
+        plan = hf.Plan(shape)
+        hf.hufield_plan_set_maps_format(plan, hf.MAPS_BITS if bits else hf.MAPS_I8)
+        ws = plan.workspace(0, 0)
+        f = torch.empty(shape, dtype=torch.float32, device="cuda")
+        hf.hufield_generate(plan, filt, 7, 0, f, ws, stream=stream)
+        m = torch.empty(N // 32 if bits else N, dtype=torch.int32 if bits else torch.int8, device="cuda")
+        for _ in range(args.warmup):
+            hf.hufield_binarise(plan, f, m, 0.0, 0.0, 0, ws, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            hf.hufield_binarise(plan, f, m, 0.0, 0.0, 0, ws, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        bpv = 8.0 + (0.125 if bits else 1.0)
+        gbs = bpv * N / (ms / 1e3) / 1e9
+        out[name] = {"shape": list(shape), "ms_per_call": round(ms, 5), "voxels_per_s": N / (ms / 1e3),
+                     "bytes_per_voxel": bpv, "GBps": round(gbs, 1), "frac": round(gbs / peak, 4),
+                     "peak_source": peak_kind, "strip": min(shape[0], 256), "launches_per_call": 2}
+        del f, m, ws, plan
+    return out
 
 
 def cufft_comparator(hf, torch, wl, nfields=4):

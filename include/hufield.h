@@ -227,6 +227,39 @@ int hufield_generate(hufield_plan *plan, const hufield_filter *filt, uint64_t se
 int hufield_threshold(hufield_plan *plan, const void *f, int32_t dtype, const float *levels, int32_t nlev,
                       int8_t *out_maps, void *stream);
 
+/* Noise-shaped binarisation of a field: a +-1 map that keeps the field's
+ * suppression of fluctuations near k = 0, which the sign map loses (Sec. II.B,
+ * last paragraph; Sec. IV names such binarisations as future work without
+ * defining one).  This is first-order sigma-delta modulation (one-dimensional
+ * error diffusion) along axis 0, in strips of h rows: with
+ *   u = clamp(g (f - level), -1, 1),
+ * each column of each strip runs, row by row from e = 0,
+ *   v = u + e,  m = (v >= 0 ? +1 : -1),  e <- v - m,
+ * every operation one FP32 operation rounded to nearest.  |e| <= 1, and the
+ * quantisation error m - u is a first difference along axis 0, so its
+ * spectrum carries the factor 4 sin^2(pi n0 / n[0]) and vanishes as k -> 0;
+ * the map's spectrum there follows that of g (f - level), and each column's
+ * mean over a strip that of u to within 1 / h.
+ *   f        device, N values of dtype (HUFIELD_F32 or HUFIELD_BF16), C order,
+ *            256-byte aligned; not modified
+ *   level    the level t (finite)
+ *   gain     g > 0, or 0 for g = 1 / max |f - level| (then |u| <= 1; u = 0
+ *            when f == level everywhere); negative or non-finite: invalid
+ *   strip    rows per strip h: a power of two in [1, n[0]], or 0 for
+ *            min(n[0], 256); strips start from e = 0 and run in parallel
+ *   out_map  device, written in the plan's maps format
+ *            (hufield_plan_set_maps_format): N int8, or N / 8 bytes of
+ *            one-bit words (site i at bit i mod 32 of word i / 32; needs
+ *            N / n[0] >= 32); 4-byte aligned
+ *   ws       the workspace of hufield_generate (hufield_workspace_bytes(plan,
+ *            0, 0)), used for gain = 0 only (the maximum's reduction word);
+ *            may be NULL when gain > 0
+ * Errors: HUFIELD_ERR_INVALID_ARG (pointers, alignment, dtype, level, gain,
+ * strip, one-bit maps with N / n[0] < 32), HUFIELD_ERR_WS_TOO_SMALL,
+ * HUFIELD_ERR_CUDA.  Nothing is enqueued when an argument is refused. */
+int hufield_binarise(hufield_plan *plan, const void *f, int32_t dtype, float level, float gain, int32_t strip,
+                     int8_t *out_map, void *ws, size_t ws_bytes, void *stream);
+
 /* Binned spectral density of a real field y (dtype F32, BF16 or I8):
  * S(n) = |DFT(y)(n)|^2 / N.  nr in [1, 4096], ntheta in [1, 64] (2D only for
  * ntheta > 1), nr * ntheta <= 4096.  accumulate = 0 overwrites sums/counts,

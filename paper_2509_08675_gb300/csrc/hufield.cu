@@ -136,6 +136,118 @@ __global__ void k_threshold(long long nblk, const void* f, Levels lv, int nlev, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Noise-shaped binarisation: first-order sigma-delta modulation along axis 0,
+// in strips of h rows.  u = clamp(g (f - t), -1, 1); each column of each
+// strip runs v = u + e, m = (v >= 0 ? +1 : -1), e <- v - m from e = 0, so the
+// quantisation error m - u is a first difference along axis 0 and its
+// spectrum vanishes as k -> 0.  Every operation is one FP32 operation rounded
+// to nearest (no contraction), so a decision depends only on f, t and g.
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ float4 load_f4(const void* f, long long j) {
+    if constexpr (DT == 0) {
+        return __ldg(reinterpret_cast<const float4*>(f) + j);
+    } else {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(f) + j);
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ float load_f1(const void* f, long long i) {
+    if constexpr (DT == 0) {
+        return __ldg(reinterpret_cast<const float*>(f) + i);
+    } else {
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(f)[i]);
+    }
+}
+
+// max |f - t| as the bit pattern of a non-negative float (which orders like
+// the value): one atomicMax per warp into *out, cleared by the host.
+template <int DT>
+__global__ void __launch_bounds__(256) k_sd_absmax(long long nblk, const void* f, float t, unsigned* out) {
+    float m = 0.0f;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nblk;
+         j += (long long)gridDim.x * blockDim.x) {
+        const float4 x = load_f4<DT>(f, j);
+        const float a = fmaxf(fabsf(__fsub_rn(x.x, t)), fabsf(__fsub_rn(x.y, t)));
+        const float b = fmaxf(fabsf(__fsub_rn(x.z, t)), fabsf(__fsub_rn(x.w, t)));
+        m = fmaxf(m, fmaxf(a, b));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+struct SDArgs {
+    const void* f;
+    long long cols;       // sites per index of axis 0 (N / n0), a power of two
+    int log2cols;
+    int h;                // rows per strip
+    long long nthreads;   // strips x cols: one thread per column of a strip
+    float t, gain;        // level and gain; absmax != nullptr: g = 1 / max |f - t|
+    const unsigned* absmax;
+    int8_t* m;            // map, one int8 per site, or
+    uint32_t* words;      // one bit per site (site i at bit i mod 32 of word i / 32)
+};
+
+// One thread per (strip, column); a warp covers 32 consecutive columns of one
+// row, so every load and store is coalesced.  The rows of a batch of U are
+// loaded before the recurrence runs through them.  One-bit maps (cols >= 32,
+// checked by the host): the warp's 32 decisions of a row are one word.
+template <int DT, bool BITS>
+__global__ void __launch_bounds__(256, 3) k_sigma_delta(const __grid_constant__ SDArgs a) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= a.nthreads) return;  // whole warps: nthreads is a multiple of 32 when BITS
+    const long long c = tid & (a.cols - 1);
+    const long long s = tid >> a.log2cols;
+    float g = a.gain;
+    if (a.absmax) {
+        const float M = __uint_as_float(*a.absmax);
+        g = M > 0.0f ? __frcp_rn(M) : 0.0f;
+    }
+    using T = typename std::conditional<DT == 0, float, __nv_bfloat16>::type;
+    const long long first = s * (long long)a.h * a.cols + c;
+    const T* src = reinterpret_cast<const T*>(a.f) + first;
+    int8_t* dst = BITS ? nullptr : a.m + first;
+    uint32_t* wdst = BITS ? a.words + (first >> 5) : nullptr;
+    const long long wstride = a.cols >> 5;
+    float e = 0.0f;
+    constexpr int U = 16;
+    for (int r0 = 0; r0 < a.h; r0 += U) {
+        const int nr = a.h - r0 < U ? a.h - r0 : U;  // uniform across the grid
+        float x[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (j < nr) {
+                if constexpr (DT == 0) x[j] = __ldg(src);
+                else x[j] = __bfloat162float(*src);
+                src += a.cols;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (j < nr) {
+                const float u = fminf(fmaxf(__fmul_rn(__fsub_rn(x[j], a.t), g), -1.0f), 1.0f);
+                const float v = __fadd_rn(u, e);
+                const bool pos = v >= 0.0f;
+                e = __fsub_rn(v, pos ? 1.0f : -1.0f);
+                if constexpr (BITS) {
+                    const unsigned w = __ballot_sync(0xffffffffu, pos);
+                    if ((threadIdx.x & 31) == 0) *wdst = w;
+                    wdst += wstride;
+                } else {
+                    *dst = pos ? (int8_t)1 : (int8_t)-1;
+                    dst += a.cols;
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_bin_table(const __grid_constant__ TableArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -1368,6 +1480,57 @@ int hufield_threshold(hufield_plan* p, const void* f, int32_t dtype, const float
         k_threshold<0><<<(int)g, 256, 0, s>>>(nblk, f, lv, nlev, p->N, reinterpret_cast<char4*>(out_maps));
     else
         k_threshold<1><<<(int)g, 256, 0, s>>>(nblk, f, lv, nlev, p->N, reinterpret_cast<char4*>(out_maps));
+    HF_CUDA(cudaGetLastError());
+    return HUFIELD_OK;
+}
+
+int hufield_binarise(hufield_plan* p, const void* f, int32_t dtype, float level, float gain, int32_t strip,
+                     int8_t* out_map, void* ws, size_t bytes, void* stream) {
+    if (!p || !f || !out_map || !aligned(f) || !maps_aligned(out_map)) return HUFIELD_ERR_INVALID_ARG;
+    if (dtype != HUFIELD_F32 && dtype != HUFIELD_BF16) return HUFIELD_ERR_INVALID_ARG;
+    if (!isfinite(level) || !isfinite(gain) || !(gain >= 0.0f)) return HUFIELD_ERR_INVALID_ARG;
+    const long long n0 = p->n[0];
+    const long long h = strip == 0 ? std::min<long long>(n0, 256) : (long long)strip;
+    if (h < 1 || h > n0 || (h & (h - 1)) != 0) return HUFIELD_ERR_INVALID_ARG;
+    const long long cols = p->N / n0;
+    const bool bits = p->maps_format == HUFIELD_MAPS_BITS;
+    if (bits && cols < 32) return HUFIELD_ERR_INVALID_ARG;  // a warp's 32 columns form one word
+    cudaStream_t s = (cudaStream_t)stream;
+    SDArgs a{};
+    a.f = f;
+    a.cols = cols;
+    a.log2cols = p->log2n[1] + (p->ndim == 3 ? p->log2n[2] : 0);
+    a.h = (int)h;
+    a.nthreads = (n0 / h) * cols;
+    a.t = level;
+    a.gain = gain;
+    a.m = bits ? nullptr : out_map;
+    a.words = bits ? reinterpret_cast<uint32_t*>(out_map) : nullptr;
+    if (gain == 0.0f) {
+        // automatic gain: max |f - t| into the first word of the workspace's spectrum area
+        Workspace w;
+        const int rc = carve(p, ws, bytes, 0, 0, w);
+        if (rc) return rc;
+        unsigned* word = reinterpret_cast<unsigned*>(w.spec);
+        HF_CUDA(cudaMemsetAsync(word, 0, sizeof(unsigned), s));
+        const long long nblk = p->N / 4;
+        const long long g = std::min<long long>((nblk + 255) / 256, (long long)p->nsm * 8);
+        if (dtype == HUFIELD_F32)
+            k_sd_absmax<0><<<(int)g, 256, 0, s>>>(nblk, f, level, word);
+        else
+            k_sd_absmax<1><<<(int)g, 256, 0, s>>>(nblk, f, level, word);
+        HF_CUDA(cudaGetLastError());
+        a.absmax = word;
+    }
+    const long long grid = (a.nthreads + 255) / 256;
+    if (dtype == HUFIELD_F32 && bits)
+        k_sigma_delta<0, true><<<(unsigned)grid, 256, 0, s>>>(a);
+    else if (dtype == HUFIELD_F32)
+        k_sigma_delta<0, false><<<(unsigned)grid, 256, 0, s>>>(a);
+    else if (bits)
+        k_sigma_delta<1, true><<<(unsigned)grid, 256, 0, s>>>(a);
+    else
+        k_sigma_delta<1, false><<<(unsigned)grid, 256, 0, s>>>(a);
     HF_CUDA(cudaGetLastError());
     return HUFIELD_OK;
 }

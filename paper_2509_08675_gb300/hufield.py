@@ -92,6 +92,7 @@ def _load():
     lib.hufield_forward.argtypes = [vp, u64, u32, vp, sz, vp]
     lib.hufield_generate.argtypes = [vp, fptr, u64, u32, i32, vp, vp, sz, vp]
     lib.hufield_threshold.argtypes = [vp, vp, i32, C.POINTER(C.c_float), i32, vp, vp]
+    lib.hufield_binarise.argtypes = [vp, vp, i32, C.c_float, C.c_float, i32, vp, vp, sz, vp]
     lib.hufield_spectrum.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]
     lib.hufield_spectrum_modes.argtypes = [vp, vp, i32, vp, vp, sz, vp]
     lib.hufield_filter_modes.argtypes = [vp, fptr, vp, vp]
@@ -237,6 +238,15 @@ def hufield_threshold(plan: Plan, f: torch.Tensor, levels, out_maps: torch.Tenso
     lv, n = _levels(levels)
     _check(_lib.hufield_threshold(plan.handle, _ptr(f), _DTYPES[f.dtype], lv, n, _ptr(out_maps), _stream(stream)),
            "hufield_threshold")
+
+
+def hufield_binarise(plan: Plan, f: torch.Tensor, out_map: torch.Tensor, level: float = 0.0, gain: float = 0.0,
+                     strip: int = 0, ws=None, stream=None):
+    """Noise-shaped +-1 map of f (sigma-delta along axis 0, in strips; gain 0:
+    1 / max |f - level|, which needs the workspace of hufield_generate)."""
+    _check(_lib.hufield_binarise(plan.handle, _ptr(f), _DTYPES[f.dtype], float(level), float(gain), int(strip),
+                                 _ptr(out_map), _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream)),
+           "hufield_binarise")
 
 
 def hufield_spectrum(plan: Plan, y: torch.Tensor, nr: int, ntheta: int, accumulate: bool, sums: torch.Tensor,
