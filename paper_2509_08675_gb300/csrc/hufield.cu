@@ -195,8 +195,10 @@ struct SDArgs {
 };
 
 // One thread per (strip, column); a warp covers 32 consecutive columns of one
-// row, so every load and store is coalesced.  The rows of a batch of U are
-// loaded before the recurrence runs through them.  One-bit maps (cols >= 32,
+// row, so every load and store is coalesced.  The pass is bound by load
+// latency (one thread per column gives few threads), so the 32 rows of a batch
+// are loaded before the recurrence runs through them: 32 loads in flight per
+// thread.  Strips shorter than a batch run row by row.  One-bit maps (cols >= 32,
 // checked by the host): the warp's 32 decisions of a row are one word.
 template <int DT, bool BITS>
 __global__ void __launch_bounds__(256, 3) k_sigma_delta(const __grid_constant__ SDArgs a) {
@@ -216,35 +218,38 @@ __global__ void __launch_bounds__(256, 3) k_sigma_delta(const __grid_constant__ 
     uint32_t* wdst = BITS ? a.words + (first >> 5) : nullptr;
     const long long wstride = a.cols >> 5;
     float e = 0.0f;
-    constexpr int U = 16;
-    for (int r0 = 0; r0 < a.h; r0 += U) {
-        const int nr = a.h - r0 < U ? a.h - r0 : U;  // uniform across the grid
-        float x[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            if (j < nr) {
-                if constexpr (DT == 0) x[j] = __ldg(src);
-                else x[j] = __bfloat162float(*src);
-                src += a.cols;
-            }
+    auto step = [&](float x) {
+        const float u = fminf(fmaxf(__fmul_rn(__fsub_rn(x, a.t), g), -1.0f), 1.0f);
+        const float v = __fadd_rn(u, e);
+        const bool pos = v >= 0.0f;
+        e = __fsub_rn(v, pos ? 1.0f : -1.0f);
+        if constexpr (BITS) {
+            const unsigned w = __ballot_sync(0xffffffffu, pos);
+            if ((threadIdx.x & 31) == 0) *wdst = w;
+            wdst += wstride;
+        } else {
+            *dst = pos ? (int8_t)1 : (int8_t)-1;
+            dst += a.cols;
         }
+    };
+    auto load = [&]() {
+        float x;
+        if constexpr (DT == 0) x = __ldg(src);
+        else x = __bfloat162float(*src);
+        src += a.cols;
+        return x;
+    };
+    constexpr int U = 32;
+    if (a.h >= U) {  // h is a power of two: whole batches of U rows
+        for (int r0 = 0; r0 < a.h; r0 += U) {
+            float x[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-            if (j < nr) {
-                const float u = fminf(fmaxf(__fmul_rn(__fsub_rn(x[j], a.t), g), -1.0f), 1.0f);
-                const float v = __fadd_rn(u, e);
-                const bool pos = v >= 0.0f;
-                e = __fsub_rn(v, pos ? 1.0f : -1.0f);
-                if constexpr (BITS) {
-                    const unsigned w = __ballot_sync(0xffffffffu, pos);
-                    if ((threadIdx.x & 31) == 0) *wdst = w;
-                    wdst += wstride;
-                } else {
-                    *dst = pos ? (int8_t)1 : (int8_t)-1;
-                    dst += a.cols;
-                }
-            }
+            for (int j = 0; j < U; ++j) x[j] = load();
+#pragma unroll
+            for (int j = 0; j < U; ++j) step(x[j]);
         }
+    } else {
+        for (int r = 0; r < a.h; ++r) step(load());
     }
 }
 
