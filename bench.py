@@ -108,6 +108,14 @@ def field_bytes(shape, nlev, live, kspace=False, out_bytes=4, map_bytes=1.0):
     return sum(algo[k] for k in keys)
 
 
+def binarise_bytes(shape, map_bytes=0.125, field_bytes=4, auto_gain=True):
+    """Bytes one noise-shaped binarisation call must move: the field read by the
+    sigma-delta pass (and once more by the max |f - t| pass of the automatic
+    gain) and the map written (1/8 byte per site one-bit, 1 int8)."""
+    N = math.prod(shape)
+    return (2 if auto_gain else 1) * field_bytes * N + map_bytes * N
+
+
 def band_live(hf, plan, filt, shape):
     """Fraction of the half spectrum below the filter's band edge (hufield_filter_band_edge)."""
     return hf.hufield_filter_band_edge(plan, filt) / (shape[-1] // 2)
@@ -823,7 +831,7 @@ def binarise_line(hf, torch, args, shapes=("ensemble-2d-4096", "3d-512")):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-        bpv = 8.0 + (0.125 if bits else 1.0)
+        bpv = binarise_bytes(shape, 0.125 if bits else 1.0) / N
         gbs = bpv * N / (ms / 1e3) / 1e9
         out[name] = {"shape": list(shape), "ms_per_call": round(ms, 5), "voxels_per_s": N / (ms / 1e3),
                      "bytes_per_voxel": bpv, "GBps": round(gbs, 1), "frac": round(gbs / peak, 4),

@@ -66,3 +66,11 @@ def test_ragged_draws_are_seeded_and_in_range():
         assert f.supp in (2.0, 4.0, 6.0) and -1.0 <= level <= 1.0 and nr == min(128, shape[0] // 2)
         axes = f.axes[:len(shape)]
         assert all(0.5 <= r <= 2.0 for r in axes[-2:]) and (len(shape) == 2 or axes[0] == 1.0)
+
+
+def test_binarise_bytes():
+    # the field read by the max pass and by the sigma-delta pass, the map written once
+    n = 512 ** 3
+    assert bench.binarise_bytes((512, 512, 512)) / n == pytest.approx(8.125)
+    assert bench.binarise_bytes((4096, 4096), map_bytes=1.0) / 4096 ** 2 == pytest.approx(9.0)
+    assert bench.binarise_bytes((256, 256), auto_gain=False) / 256 ** 2 == pytest.approx(4.125)
