@@ -7,7 +7,10 @@
  * (Eq. 12) and the band envelope (Eq. 13) -> inverse FFT (Eq. 9) ->
  * normalisation to zero mean and variance sigma_f^2 (Eq. 15) -> sign maps at
  * given levels (Sec. II.B, last paragraph) -> binned spectral density S(k) of
- * the field and of every map (the log S panels of Figs. 1-5).
+ * the field and of every map (the log S panels of Figs. 1-5).  Beside the
+ * sign map, hufield_binarise gives a noise-shaped +-1 map that keeps the
+ * field's suppression of S near k = 0 (Sec. IV's binarisations that keep
+ * hyperuniformity, read as sigma-delta modulation along axis 0).
  *
  * Conventions shared by every call
  *   - Lattice: ndim = 2 or 3, C order, axis ndim-1 contiguous; every n[i] is a
@@ -37,8 +40,9 @@
  *   - Every buffer argument named out_*, ws, sums, counts, f or y is a DEVICE
  *     pointer owned by the caller; levels is a HOST pointer.  Device buffers
  *     must be 256-byte aligned, except out_maps of hufield_threshold,
- *     hufield_pipeline and hufield_ensemble, which needs 4 bytes (a map may
- *     start at any field offset of a larger buffer, e.g. a batch item's).
+ *     hufield_pipeline and hufield_ensemble, and out_map of hufield_binarise,
+ *     which need 4 bytes (a map may start at any field offset of a larger
+ *     buffer, e.g. a batch item's).
  *     The library allocates device memory only in
  *     hufield_plan_create (a 32 KB twiddle table) and hufield_plan_set_bins,
  *     never on a hot call.
