@@ -4,7 +4,8 @@ Test infrastructure only: the test suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The product path never
 imports this package.  The arithmetic lives in ``hufield_oracle.c`` (plain C,
 FP64, OpenMP over independent lines); this module compiles it on first use and
-marshals numpy arrays in and out.
+marshals numpy arrays in and out.  Everything is FP64 except the noise-shaped
+binarisation, whose site decisions are taken in FP32 as the kernel takes them.
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """

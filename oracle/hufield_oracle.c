@@ -22,7 +22,9 @@
  *   normalise  f <- sigma_f (f - <f>) / sqrt(Var f), Eq. (15)
  *   threshold  sign map, Sec. II.B (last paragraph): f >= t -> +1 else -1
  *   binarise   noise-shaped binarisation (a reading of the future work of
- *              Sec. IV): sigma-delta modulation along axis 0, in FP32
+ *              Sec. IV): sigma-delta modulation along axis 0, in FP32 (each
+ *              site is a floating-point decision, taken in the kernel's
+ *              precision; everything else here is FP64)
  *   spectrum   S(n) = |DFT(y)(n)|^2 / N, binned radially (and by angle in 2D)
  *   window     sigma_F^2(R), Eq. (1): variance of the field averaged over a
  *              ball of radius R, from the spectrum
