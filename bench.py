@@ -624,7 +624,10 @@ def main():
     also = {}
     for name in [n for n in args.also.split(",") if n and n != args.workload] if world == 1 else []:
         if name == "binarise":
-            also[name] = binarise_line(hf, torch, args)
+            try:  # a context leg: a failure is reported in the line, not in place of it
+                also[name] = binarise_line(hf, torch, args)
+            except Exception as exc:  # noqa: BLE001
+                also[name] = {"error": f"{type(exc).__name__}: {exc}"}
             continue
         if name == "ragged-2000":
             t_r = time.perf_counter()
