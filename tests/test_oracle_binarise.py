@@ -164,3 +164,22 @@ def test_keeps_the_small_k_suppression_the_sign_map_loses():
     assert sign[1:4].min() > 0.3
     assert (sd[1:4] < 0.03 * sign[1:4]).all()
     assert sd[1] < sd[3] < sd[6]
+
+
+def test_keeps_the_small_k_suppression_in_3d():
+    # the same in 3D: eight 64^3 fields (s = 2, band at k0 = 0.4), strips of the whole
+    # axis; the lowest bins stay below 4% of the sign map's.  Their floor (about
+    # E[e^2] / h, h = 64 here) is the strip starts' term
+    shape, nr = (64, 64, 64), 32
+    filt = oracle.Filter(p=2, axes=(1, 1, 1), k0=0.4, width=0.08, supp=2)
+    acc = {"sign": 0.0, "sd": 0.0}
+    for seed in range(8):
+        f = oracle.generate(shape, filt, seed).astype(np.float32)
+        for name, y in (("sign", oracle.threshold(f, 0.0)), ("sd", oracle.sigma_delta(f))):
+            s, c = oracle.spectrum_bins(y, nr)
+            acc[name] = acc[name] + s / c
+    sign, sd = acc["sign"] / 8, acc["sd"] / 8
+    assert sign[1:5].min() > 0.3
+    assert (sd[1:5] < 0.04 * sign[1:5]).all()
+    assert sd[1:5].max() < 0.05
+    assert sd[2] < sd[6] < sd[10]
