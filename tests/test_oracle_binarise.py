@@ -183,3 +183,24 @@ def test_keeps_the_small_k_suppression_in_3d():
     assert (sd[1:5] < 0.04 * sign[1:5]).all()
     assert sd[1:5].max() < 0.05
     assert sd[2] < sd[6] < sd[10]
+
+
+def test_window_variance_keeps_the_fields_class():
+    # Sec. II.A defines hyperuniformity by the window variance of Eq. (1):
+    # sigma^2(R) falls faster than R^-d.  Eight 256^2 fields with s = 2 fall as
+    # R^-(d+1) = R^-3; the sign map's local slope drifts back toward -d = -2, the
+    # noise-shaped map's stays with the field's
+    shape = (256, 256)
+    filt = oracle.Filter(p=2, axes=(1, 1), k0=0.25, width=0.05, supp=2)
+    radii = np.array([8.0, 11.3, 16.0, 22.6, 32.0])
+    acc = {"f": 0.0, "sign": 0.0, "sd": 0.0}
+    for seed in range(8):
+        f = oracle.generate(shape, filt, seed).astype(np.float32)
+        for name, y in (("f", f), ("sign", oracle.threshold(f, 0.0)), ("sd", oracle.sigma_delta(f))):
+            acc[name] = acc[name] + oracle.window_variance(y.astype(np.float64), radii)
+    slope = {k: np.polyfit(np.log(radii), np.log(v), 1)[0] for k, v in acc.items()}
+    local = {k: np.diff(np.log(v)) / np.diff(np.log(radii)) for k, v in acc.items()}
+    assert slope["f"] == pytest.approx(-3.0, abs=0.1)
+    assert slope["sd"] == pytest.approx(slope["f"], abs=0.15)
+    assert local["sd"].max() < -2.8
+    assert local["sign"][-1] > -2.4 and local["sign"][-1] > local["sign"][0]
